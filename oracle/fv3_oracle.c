@@ -1,0 +1,1511 @@
+/*
+ * fv3_oracle.c -- plain, slow FP64 CPU oracle of one FV3 acoustic substep.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path under
+ * paper_2205_04148_gb300/csrc; the two meet only in the seeded inputs.
+ *
+ * What it computes (arxiv 2205.04148, Section II "The FV3 model": the
+ * nonhydrostatic acoustic substep on the gnomonic cubed sphere with a
+ * Lagrangian vertical coordinate; Section IX-B riem_solver_c, a semi-implicit
+ * tridiagonal column solve; Section IX-C fv_tp_2d, 2-D mass-conserving
+ * flux-form transport; Section V-B corner/edge specialisations; Section V-C
+ * halo exchange with an orientation transform between cube faces).
+ *
+ * The paper prints no equation of the method.  Every formula below is the
+ * reading written out in the design notes (readings R1..R15), taken from the
+ * published methods the paper cites (Colella-Woodward PPM, Lin-Rood
+ * splitting, Putman-Lin cubed sphere, Lin 1997 pressure gradient, Chen et al.
+ * semi-implicit column).  Parity with FORTRAN FV3 is therefore unpinned; the
+ * pins in tests/ check this file against closed forms, invariants and brute
+ * force.
+ *
+ * Pinned (tests/test_oracle_*.py): PPM (closed-form swept means of linear and
+ * parabolic profiles, mirror symmetry, monotonicity, 3rd-order convergence),
+ * fv_tp_2d (Courant-1 shift, constant preservation, conservation, bitwise
+ * transpose symmetry, reflection), delnflux (checkerboard and Fourier-mode
+ * amplification), the column solve (Thomas vs dense LU brute force, resting
+ * hydrostatic column, linearity), the grid (total area, symmetries, grid
+ * angle), the halo fill (brute-force geometric matching of cells and rotated
+ * winds), and the whole substep (mass conservation to 1e-14, constant tracer,
+ * rest state, uniform translation, transpose symmetry).
+ * Parity unpinned: agreement of c_sw, update_dz_c, p_grad_c and the wind
+ * update of d_sw with FORTRAN FV3 -- the paper gives neither their equations
+ * nor any field value, so only the invariants above hold them.
+ *
+ * Layout: every field is padded by a halo of h = 3 on each side of a tile,
+ * i fastest.  Index (i, j) of the interior runs over [0, n).  Faces: x-face
+ * (i, j) lies between cells (i-1, j) and (i, j) (i in [0, n]); y-face (i, j)
+ * between cells (i, j-1) and (i, j).  Corners (i, j) in [0, n]^2.
+ * Compiled with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define H 3
+
+typedef struct {
+  int n, nz, nt, cubed;
+  double dx0, radius, omega;
+  int nbt[6][4], nbe[6][4], nbr[6][4]; /* neighbour tile, edge, reversed */
+  long wc, wx;                          /* row widths: cells/y-faces, x-faces/corners */
+  long pc, px, py, pk;                  /* plane sizes */
+  /* metric, per tile, padded planes */
+  double *area, *rarea, *fA;                   /* cells   */
+  double *dx, *rdx, *dyc, *rdyc, *cosy, *siny; /* y-faces */
+  double *dy, *rdy, *dxc, *rdxc, *cosx, *sinx; /* x-faces */
+  double *fC, *rareac;                         /* corners */
+  double da_min;
+} ODom;
+
+typedef struct {
+  double dt;
+  int n_split, nord, hord;
+  double d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air;
+} OParams;
+
+typedef struct {
+  ODom* d;
+  int nq;
+  double *u, *v, *w, *delp, *pt, *delz;
+  double** q;
+  /* intermediates of the last substep (kept for stage-by-stage checks) */
+  double *uc, *vc, *delpc, *ptc, *wc, *delzc, *fx1, *fy1, *pef, *gze;
+  /* flux accumulators over a remapping step */
+  double *amfx, *amfy, *acrx, *acry, *axfx, *ayfx;
+} OState;
+
+/* ------------------------------------------------------------------ */
+/* indexing                                                            */
+/* ------------------------------------------------------------------ */
+static inline long IC(const ODom* d, int j, int i) { return (long)(j + H) * d->wc + (i + H); }
+static inline long IX(const ODom* d, int j, int i) { return (long)(j + H) * d->wx + (i + H); }
+#define IY IC
+#define IK IX
+
+static double* zalloc(long n) { return (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
+static double* nalloc(long n) {
+  double* p = zalloc(n);
+  for (long i = 0; i < n; i++) p[i] = NAN;
+  return p;
+}
+
+/* ------------------------------------------------------------------ */
+/* cubed-sphere geometry (reading R1: equiangular gnomonic grid)       */
+/* ------------------------------------------------------------------ */
+static const double FRAME[6][3][3] = {
+    {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},  {{0, 1, 0}, {-1, 0, 0}, {0, 0, 1}},
+    {{-1, 0, 0}, {0, -1, 0}, {0, 0, 1}}, {{0, -1, 0}, {1, 0, 0}, {0, 0, 1}},
+    {{0, 0, 1}, {0, 1, 0}, {-1, 0, 0}},  {{0, 0, -1}, {0, 1, 0}, {1, 0, 0}}};
+
+static double tanq(double s) {
+  if (s == 1.0) return 1.0;
+  if (s == -1.0) return -1.0;
+  return tan(s * (M_PI / 4.0));
+}
+
+/* point of tile t at index position (X, Y) (corner = integer, centre = +1/2) */
+static void gpoint(const ODom* d, int t, double X, double Y, double p[3]) {
+  double sa = (2.0 * X - d->n) / d->n, sb = (2.0 * Y - d->n) / d->n;
+  double ta = tanq(sa), tb = tanq(sb);
+  double r = 0;
+  for (int c = 0; c < 3; c++) {
+    p[c] = FRAME[t][0][c] + ta * FRAME[t][1][c] + tb * FRAME[t][2][c];
+    r += p[c] * p[c];
+  }
+  r = sqrt(r);
+  for (int c = 0; c < 3; c++) p[c] /= r;
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+
+/* great-circle angle between unit vectors */
+static double gc_angle(const double a[3], const double b[3]) {
+  double c[3];
+  cross3(a, b, c);
+  return atan2(norm3(c), dot3(a, b));
+}
+
+/* spherical excess of the triangle (a, b, c) of unit vectors */
+static double tri_excess(const double a[3], const double b[3], const double c[3]) {
+  double bc[3];
+  cross3(b, c, bc);
+  double num = fabs(dot3(a, bc));
+  double den = 1.0 + dot3(a, b) + dot3(b, c) + dot3(c, a);
+  return 2.0 * atan2(num, den);
+}
+
+/* edge frames in index space: start (units of n), tangent, outward normal */
+static const int EST[4][2] = {{0, 0}, {1, 0}, {0, 0}, {0, 1}};
+static const int ETG[4][2] = {{0, 1}, {0, 1}, {1, 0}, {1, 0}};
+static const int EOU[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+enum { EW = 0, EE = 1, ES = 2, EN = 3 };
+
+static void find_neighbours(ODom* d) {
+  int n = d->n;
+  double P[6][4][2][3];
+  for (int t = 0; t < 6; t++)
+    for (int e = 0; e < 4; e++) {
+      double X0 = n * EST[e][0], Y0 = n * EST[e][1];
+      gpoint(d, t, X0, Y0, P[t][e][0]);
+      gpoint(d, t, X0 + n * ETG[e][0], Y0 + n * ETG[e][1], P[t][e][1]);
+    }
+  for (int t = 0; t < 6; t++)
+    for (int e = 0; e < 4; e++) {
+      d->nbt[t][e] = -1;
+      for (int t2 = 0; t2 < 6; t2++) {
+        if (t2 == t) continue;
+        for (int e2 = 0; e2 < 4; e2++) {
+          double s0[3], s1[3], r0[3], r1[3];
+          for (int c = 0; c < 3; c++) {
+            s0[c] = P[t][e][0][c] - P[t2][e2][0][c];
+            s1[c] = P[t][e][1][c] - P[t2][e2][1][c];
+            r0[c] = P[t][e][0][c] - P[t2][e2][1][c];
+            r1[c] = P[t][e][1][c] - P[t2][e2][0][c];
+          }
+          if (norm3(s0) < 1e-12 && norm3(s1) < 1e-12) {
+            d->nbt[t][e] = t2; d->nbe[t][e] = e2; d->nbr[t][e] = 0;
+          } else if (norm3(r0) < 1e-12 && norm3(r1) < 1e-12) {
+            d->nbt[t][e] = t2; d->nbe[t][e] = e2; d->nbr[t][e] = 1;
+          }
+        }
+      }
+    }
+}
+
+/*
+ * Map a point (X, Y) of tile t across edge e onto the neighbour tile
+ * (reading R2: the halo of a tile is the neighbour's own cells, reached by the
+ * index map that identifies the shared edge; Section V-C).  ex/ey receive the
+ * images of the unit index directions (the basis rotation, entries 0/+-1).
+ */
+static void edge_map(const ODom* d, int t, int e, double X, double Y, int* t2, double* X2, double* Y2,
+                     int ex[2], int ey[2]) {
+  int n = d->n;
+  if (!d->cubed) { /* doubly periodic: wrap */
+    *t2 = t;
+    *X2 = X; *Y2 = Y;
+    if (e == EW) *X2 = X + n;
+    if (e == EE) *X2 = X - n;
+    if (e == ES) *Y2 = Y + n;
+    if (e == EN) *Y2 = Y - n;
+    ex[0] = 1; ex[1] = 0; ey[0] = 0; ey[1] = 1;
+    return;
+  }
+  double rx = X - n * EST[e][0], ry = Y - n * EST[e][1];
+  double p = rx * ETG[e][0] + ry * ETG[e][1];
+  double dd = rx * EOU[e][0] + ry * EOU[e][1];
+  int tt = d->nbt[t][e], e2 = d->nbe[t][e], rev = d->nbr[t][e];
+  double p2 = rev ? n - p : p;
+  *t2 = tt;
+  *X2 = n * EST[e2][0] + p2 * ETG[e2][0] - dd * EOU[e2][0];
+  *Y2 = n * EST[e2][1] + p2 * ETG[e2][1] - dd * EOU[e2][1];
+  int sg = rev ? -1 : 1;
+  /* unit x = ETG[e][0]*tangent + EOU[e][0]*outward ; tangent -> sg*ETG[e2], outward -> -EOU[e2] */
+  for (int c = 0; c < 2; c++) {
+    ex[c] = ETG[e][0] * sg * ETG[e2][c] - EOU[e][0] * EOU[e2][c];
+    ey[c] = ETG[e][1] * sg * ETG[e2][c] - EOU[e][1] * EOU[e2][c];
+  }
+}
+
+static int beyond_edge(int n, double X, double Y) {
+  if (X < 0) return EW;
+  if (X > n) return EE;
+  if (Y < 0) return ES;
+  return EN;
+}
+
+/*
+ * Corner regions (reading R3, the corner specialisations of Section V-B):
+ * a tile corner of the cube has no fourth quadrant.  A sweep along x reads
+ * the missing quadrant as the x-strip (W or E halo) rotated by 90 degrees
+ * about the corner ("x-role"); a sweep along y reads the y-strip rotated the
+ * other way ("y-role").  Returns the source point inside the tile's own strip
+ * and the basis images.
+ */
+static void role_src(int n, int role, double X, double Y, double* Xs, double* Ys, int ex[2], int ey[2]) {
+  int ox = X < 0 ? -1 : 1, oy = Y < 0 ? -1 : 1;
+  double xc = X < 0 ? 0 : n, yc = Y < 0 ? 0 : n;
+  double a = ox * (X - xc), b = oy * (Y - yc);
+  int s = ox * oy;
+  if (role == 0) {
+    *Xs = xc + ox * b; *Ys = yc - oy * a;
+    ex[0] = 0; ex[1] = -s; ey[0] = s; ey[1] = 0;
+  } else {
+    *Xs = xc - ox * b; *Ys = yc + oy * a;
+    ex[0] = 0; ex[1] = s; ey[0] = -s; ey[1] = 0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* halo fills (Section V-C, readings R2, R3)                           */
+/* ------------------------------------------------------------------ */
+/* cell scalar: strips of depth `depth` from neighbours; cubed corners left NaN */
+static void fill_cells(const ODom* d, double* f, int nlev, int depth) {
+  int n = d->n;
+  long pl = d->pc;
+  for (int t = 0; t < d->nt; t++)
+    for (int j = -depth; j < n + depth; j++)
+      for (int i = -depth; i < n + depth; i++) {
+        int inx = (i >= 0 && i < n), iny = (j >= 0 && j < n);
+        if (inx && iny) continue;
+        if (!inx && !iny && d->cubed) {
+          for (int k = 0; k < nlev; k++) f[((long)t * nlev + k) * pl + IC(d, j, i)] = NAN;
+          continue;
+        }
+        double X = i + 0.5, Y = j + 0.5;
+        int t2, ex[2], ey[2];
+        double X2, Y2;
+        if (!d->cubed) { /* periodic: wrap both directions */
+          t2 = t;
+          X2 = X < 0 ? X + n : (X > n ? X - n : X);
+          Y2 = Y < 0 ? Y + n : (Y > n ? Y - n : Y);
+        } else {
+          edge_map(d, t, beyond_edge(n, X, Y), X, Y, &t2, &X2, &Y2, ex, ey);
+        }
+        int i2 = (int)floor(X2), j2 = (int)floor(Y2);
+        for (int k = 0; k < nlev; k++)
+          f[((long)t * nlev + k) * pl + IC(d, j, i)] = f[((long)t2 * nlev + k) * pl + IC(d, j2, i2)];
+      }
+}
+
+/*
+ * face pair: fxf on x-faces, fyf on y-faces.
+ * kind 0: unsigned (lengths); 1: D-grid vector (x-comp on y-faces, y-comp on
+ * x-faces); 2: C-grid vector / face flux (x-comp on x-faces, y-comp on
+ * y-faces); 3: cosine of the grid angle (sign = product of the basis signs).
+ * corners: 0 = NaN, 1 = D-grid corner rule (x-faces y-role, y-faces x-role).
+ */
+static double pair_value(const ODom* d, const double* fxf, const double* fyf, int nlev, int t2, int k, double X2,
+                         double Y2, int comp_on_slot, int kind, int ex[2], int ey[2]) {
+  /* source face type from the mapped midpoint */
+  int srcx = (X2 == floor(X2)); /* integer X -> x-face */
+  int i2 = (int)floor(X2), j2 = (int)floor(Y2);
+  double val = srcx ? fxf[((long)t2 * nlev + k) * d->px + IX(d, j2, i2)]
+                    : fyf[((long)t2 * nlev + k) * d->py + IY(d, j2, i2)];
+  if (kind == 0) return val;
+  if (kind == 3) {
+    int sx = ex[0] + ex[1], sy = ey[0] + ey[1];
+    return sx * sy * val;
+  }
+  int* img = comp_on_slot == 0 ? ex : ey;
+  return (img[0] + img[1]) * val;
+}
+
+static void fill_faces(const ODom* d, double* fxf, double* fyf, int nlev, int depth, int kind, int corners) {
+  int n = d->n;
+  /* pass 1: shared tile-edge faces take the owner's value (lower tile index;
+     on the periodic tile the faces i = 0 / j = 0) */
+  for (int t = 0; t < d->nt; t++) {
+    for (int side = 0; side < 2; side++)
+      for (int j = 0; j < n; j++) { /* x-faces on W/E edges */
+        int i = side ? n : 0, e = side ? EE : EW;
+        double X = i, Y = j + 0.5;
+        int t2, ex[2], ey[2];
+        double X2, Y2;
+        edge_map(d, t, e, X, Y, &t2, &X2, &Y2, ex, ey);
+        int owner_is_other = d->cubed ? (t2 < t) : (side == 1);
+        if (!owner_is_other) continue;
+        int comp = (kind == 1) ? 1 : 0;
+        for (int k = 0; k < nlev; k++)
+          fxf[((long)t * nlev + k) * d->px + IX(d, j, i)] =
+              pair_value(d, fxf, fyf, nlev, t2, k, X2, Y2, comp, kind, ex, ey);
+      }
+    for (int side = 0; side < 2; side++)
+      for (int i = 0; i < n; i++) { /* y-faces on S/N edges */
+        int j = side ? n : 0, e = side ? EN : ES;
+        double X = i + 0.5, Y = j;
+        int t2, ex[2], ey[2];
+        double X2, Y2;
+        edge_map(d, t, e, X, Y, &t2, &X2, &Y2, ex, ey);
+        int owner_is_other = d->cubed ? (t2 < t) : (side == 1);
+        if (!owner_is_other) continue;
+        int comp = (kind == 1) ? 0 : 1;
+        for (int k = 0; k < nlev; k++)
+          fyf[((long)t * nlev + k) * d->py + IY(d, j, i)] =
+              pair_value(d, fxf, fyf, nlev, t2, k, X2, Y2, comp, kind, ex, ey);
+      }
+  }
+  /* pass 2: strips.  x-faces: i in [-depth, n+depth], j in [-depth, n+depth) */
+  for (int t = 0; t < d->nt; t++) {
+    for (int j = -depth; j < n + depth; j++)
+      for (int i = -depth; i <= n + depth; i++) {
+        int inx = (i >= 0 && i <= n), iny = (j >= 0 && j < n);
+        if (inx && iny) continue;
+        double X = i, Y = j + 0.5;
+        int comp = (kind == 1) ? 1 : 0;
+        if (!inx && !iny) continue; /* corner region: pass 3 */
+        int t2, ex[2], ey[2];
+        double X2, Y2;
+        edge_map(d, t, beyond_edge(n, X, Y), X, Y, &t2, &X2, &Y2, ex, ey);
+        for (int k = 0; k < nlev; k++)
+          fxf[((long)t * nlev + k) * d->px + IX(d, j, i)] =
+              pair_value(d, fxf, fyf, nlev, t2, k, X2, Y2, comp, kind, ex, ey);
+      }
+    for (int j = -depth; j <= n + depth; j++)
+      for (int i = -depth; i < n + depth; i++) {
+        int inx = (i >= 0 && i < n), iny = (j >= 0 && j <= n);
+        if (inx && iny) continue;
+        if (!inx && !iny) continue;
+        double X = i + 0.5, Y = j;
+        int comp = (kind == 1) ? 0 : 1;
+        int t2, ex[2], ey[2];
+        double X2, Y2;
+        edge_map(d, t, beyond_edge(n, X, Y), X, Y, &t2, &X2, &Y2, ex, ey);
+        for (int k = 0; k < nlev; k++)
+          fyf[((long)t * nlev + k) * d->py + IY(d, j, i)] =
+              pair_value(d, fxf, fyf, nlev, t2, k, X2, Y2, comp, kind, ex, ey);
+      }
+  }
+  /* pass 3: corner regions */
+  for (int t = 0; t < d->nt; t++) {
+    for (int j = -depth; j < n + depth; j++)
+      for (int i = -depth; i <= n + depth; i++) {
+        int inx = (i >= 0 && i <= n), iny = (j >= 0 && j < n);
+        if (inx || iny) continue;
+        double X = i, Y = j + 0.5;
+        for (int k = 0; k < nlev; k++) {
+          long o = ((long)t * nlev + k) * d->px + IX(d, j, i);
+          if (!d->cubed) { /* wrap */
+            int i2 = i < 0 ? i + n : i - n, j2 = j < 0 ? j + n : j - n;
+            fxf[o] = fxf[((long)t * nlev + k) * d->px + IX(d, j2, i2)];
+          } else if (corners == 1) { /* x-face stores v: y-role */
+            double Xs, Ys;
+            int ex[2], ey[2];
+            role_src(n, 1, X, Y, &Xs, &Ys, ex, ey);
+            fxf[o] = pair_value(d, fxf, fyf, nlev, t, k, Xs, Ys, 1, kind, ex, ey);
+          } else {
+            fxf[o] = NAN;
+          }
+        }
+      }
+    for (int j = -depth; j <= n + depth; j++)
+      for (int i = -depth; i < n + depth; i++) {
+        int inx = (i >= 0 && i < n), iny = (j >= 0 && j <= n);
+        if (inx || iny) continue;
+        double X = i + 0.5, Y = j;
+        for (int k = 0; k < nlev; k++) {
+          long o = ((long)t * nlev + k) * d->py + IY(d, j, i);
+          if (!d->cubed) {
+            int i2 = i < 0 ? i + n : i - n, j2 = j < 0 ? j + n : j - n;
+            fyf[o] = fyf[((long)t * nlev + k) * d->py + IY(d, j2, i2)];
+          } else if (corners == 1) { /* y-face stores u: x-role */
+            double Xs, Ys;
+            int ex[2], ey[2];
+            role_src(n, 0, X, Y, &Xs, &Ys, ex, ey);
+            fyf[o] = pair_value(d, fxf, fyf, nlev, t, k, Xs, Ys, 0, kind, ex, ey);
+          } else {
+            fyf[o] = NAN;
+          }
+        }
+      }
+  }
+}
+
+/* FV3-style copy_corners: fill the corner regions of one cell plane from the
+   tile's own strips, x-role (dir 0) or y-role (dir 1).  No-op when periodic. */
+static void copy_corners(const ODom* d, double* q, int dir) {
+  if (!d->cubed) return;
+  int n = d->n;
+  for (int j = -H; j < n + H; j++)
+    for (int i = -H; i < n + H; i++) {
+      if ((i >= 0 && i < n) || (j >= 0 && j < n)) continue;
+      double Xs, Ys;
+      int ex[2], ey[2];
+      role_src(n, dir, i + 0.5, j + 0.5, &Xs, &Ys, ex, ey);
+      q[IC(d, j, i)] = q[IC(d, (int)floor(Ys), (int)floor(Xs))];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* grid construction (reading R1)                                      */
+/* ------------------------------------------------------------------ */
+static void metric_fill_all(ODom* d) {
+  fill_cells(d, d->area, 1, H);
+  fill_cells(d, d->rarea, 1, H);
+  fill_cells(d, d->fA, 1, H);
+  fill_faces(d, d->dy, d->dx, 1, H, 0, 0);
+  fill_faces(d, d->rdy, d->rdx, 1, H, 0, 0);
+  fill_faces(d, d->dxc, d->dyc, 1, H, 0, 0);
+  fill_faces(d, d->rdxc, d->rdyc, 1, H, 0, 0);
+  fill_faces(d, d->sinx, d->siny, 1, H, 0, 0);
+  fill_faces(d, d->cosx, d->cosy, 1, H, 3, 0);
+}
+
+/* cell centre of (i, j) of tile t; strip positions are resolved to the neighbour */
+static void centre_any(const ODom* d, int t, int i, int j, double p[3]) {
+  int n = d->n;
+  double X = i + 0.5, Y = j + 0.5;
+  if (X < 0 || X > n || Y < 0 || Y > n) {
+    int t2, ex[2], ey[2];
+    double X2, Y2;
+    edge_map(d, t, beyond_edge(n, X, Y), X, Y, &t2, &X2, &Y2, ex, ey);
+    gpoint(d, t2, X2, Y2, p);
+  } else {
+    gpoint(d, t, X, Y, p);
+  }
+}
+
+/* unit tangents of the alpha / beta coordinate lines at (X, Y) */
+static void basis_at(const ODom* d, int t, double X, double Y, double ea[3], double eb[3]) {
+  double p[3];
+  gpoint(d, t, X, Y, p);
+  const double* a = FRAME[t][1];
+  const double* b = FRAME[t][2];
+  double pa = dot3(a, p), pb = dot3(b, p);
+  for (int c = 0; c < 3; c++) {
+    ea[c] = a[c] - pa * p[c];
+    eb[c] = b[c] - pb * p[c];
+  }
+  double ra = norm3(ea), rb = norm3(eb);
+  for (int c = 0; c < 3; c++) { ea[c] /= ra; eb[c] /= rb; }
+}
+
+ODom* orc_dom_create(int cubed, int n, int nz, double dx0, double radius, double omega) {
+  ODom* d = (ODom*)calloc(1, sizeof(ODom));
+  d->n = n; d->nz = nz; d->cubed = cubed; d->nt = cubed ? 6 : 1;
+  d->dx0 = dx0; d->radius = radius; d->omega = omega;
+  d->wc = n + 2 * H; d->wx = n + 1 + 2 * H;
+  d->pc = d->wc * d->wc; d->px = d->wc * d->wx; d->py = d->wx * d->wc; d->pk = d->wx * d->wx;
+  int nt = d->nt;
+  d->area = nalloc(nt * d->pc); d->rarea = nalloc(nt * d->pc); d->fA = nalloc(nt * d->pc);
+  d->dx = nalloc(nt * d->py); d->rdx = nalloc(nt * d->py); d->dyc = nalloc(nt * d->py);
+  d->rdyc = nalloc(nt * d->py); d->cosy = nalloc(nt * d->py); d->siny = nalloc(nt * d->py);
+  d->dy = nalloc(nt * d->px); d->rdy = nalloc(nt * d->px); d->dxc = nalloc(nt * d->px);
+  d->rdxc = nalloc(nt * d->px); d->cosx = nalloc(nt * d->px); d->sinx = nalloc(nt * d->px);
+  d->fC = nalloc(nt * d->pk); d->rareac = nalloc(nt * d->pk);
+  if (!cubed) {
+    double a = dx0 * dx0;
+    for (long o = 0; o < d->pc; o++) { d->area[o] = a; d->rarea[o] = 1.0 / a; d->fA[o] = 0.0; }
+    for (long o = 0; o < d->py; o++) {
+      d->dx[o] = dx0; d->rdx[o] = 1.0 / dx0; d->dyc[o] = dx0; d->rdyc[o] = 1.0 / dx0;
+      d->cosy[o] = 0.0; d->siny[o] = 1.0;
+    }
+    for (long o = 0; o < d->px; o++) {
+      d->dy[o] = dx0; d->rdy[o] = 1.0 / dx0; d->dxc[o] = dx0; d->rdxc[o] = 1.0 / dx0;
+      d->cosx[o] = 0.0; d->sinx[o] = 1.0;
+    }
+    for (long o = 0; o < d->pk; o++) { d->fC[o] = 0.0; d->rareac[o] = 1.0 / a; }
+    d->da_min = a;
+    return d;
+  }
+  find_neighbours(d);
+  double R = radius;
+  for (int t = 0; t < nt; t++) {
+    double* area = d->area + t * d->pc;
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) {
+        double p00[3], p10[3], p11[3], p01[3], c[3];
+        gpoint(d, t, i, j, p00); gpoint(d, t, i + 1, j, p10);
+        gpoint(d, t, i + 1, j + 1, p11); gpoint(d, t, i, j + 1, p01);
+        double A = (tri_excess(p00, p10, p11) + tri_excess(p00, p11, p01)) * R * R;
+        area[IC(d, j, i)] = A;
+        d->rarea[t * d->pc + IC(d, j, i)] = 1.0 / A;
+        gpoint(d, t, i + 0.5, j + 0.5, c);
+        d->fA[t * d->pc + IC(d, j, i)] = 2.0 * omega * c[2];
+      }
+    for (int j = 0; j <= n; j++) /* y-faces */
+      for (int i = 0; i < n; i++) {
+        double pa[3], pb[3], ca[3], cb[3], ea[3], eb[3];
+        gpoint(d, t, i, j, pa); gpoint(d, t, i + 1, j, pb);
+        double L = gc_angle(pa, pb) * R;
+        long o = t * d->py + IY(d, j, i);
+        d->dx[o] = L; d->rdx[o] = 1.0 / L;
+        centre_any(d, t, i, j - 1, ca); centre_any(d, t, i, j, cb);
+        double Lc = gc_angle(ca, cb) * R;
+        d->dyc[o] = Lc; d->rdyc[o] = 1.0 / Lc;
+        basis_at(d, t, i + 0.5, j, ea, eb);
+        double cs = dot3(ea, eb);
+        d->cosy[o] = cs; d->siny[o] = sqrt(1.0 - cs * cs);
+      }
+    for (int j = 0; j < n; j++) /* x-faces */
+      for (int i = 0; i <= n; i++) {
+        double pa[3], pb[3], ca[3], cb[3], ea[3], eb[3];
+        gpoint(d, t, i, j, pa); gpoint(d, t, i, j + 1, pb);
+        double L = gc_angle(pa, pb) * R;
+        long o = t * d->px + IX(d, j, i);
+        d->dy[o] = L; d->rdy[o] = 1.0 / L;
+        centre_any(d, t, i - 1, j, ca); centre_any(d, t, i, j, cb);
+        double Lc = gc_angle(ca, cb) * R;
+        d->dxc[o] = Lc; d->rdxc[o] = 1.0 / Lc;
+        basis_at(d, t, i, j + 0.5, ea, eb);
+        double cs = dot3(ea, eb);
+        d->cosx[o] = cs; d->sinx[o] = sqrt(1.0 - cs * cs);
+      }
+    for (int j = 0; j <= n; j++) /* corners: Coriolis and dual-cell area */
+      for (int i = 0; i <= n; i++) {
+        double p[3];
+        gpoint(d, t, i, j, p);
+        long o = t * d->pk + IK(d, j, i);
+        d->fC[o] = 2.0 * omega * p[2];
+        int tc = (i == 0 || i == n) && (j == 0 || j == n);
+        double A;
+        if (tc) { /* cube corner: triangle of own, x-strip and y-strip centres */
+          int io = (i == 0) ? 0 : n - 1, jo = (j == 0) ? 0 : n - 1;
+          int ix = (i == 0) ? -1 : n, jy = (j == 0) ? -1 : n;
+          double c0[3], c1[3], c2[3];
+          centre_any(d, t, io, jo, c0); centre_any(d, t, ix, jo, c1); centre_any(d, t, io, jy, c2);
+          A = tri_excess(c0, c1, c2) * R * R;
+        } else {
+          double c00[3], c10[3], c11[3], c01[3];
+          centre_any(d, t, i - 1, j - 1, c00); centre_any(d, t, i, j - 1, c10);
+          centre_any(d, t, i, j, c11); centre_any(d, t, i - 1, j, c01);
+          A = (tri_excess(c00, c10, c11) + tri_excess(c00, c11, c01)) * R * R;
+        }
+        d->rareac[o] = 1.0 / A;
+      }
+  }
+  metric_fill_all(d);
+  double m = INFINITY;
+  for (int t = 0; t < nt; t++)
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) m = fmin(m, d->area[t * d->pc + IC(d, j, i)]);
+  d->da_min = m;
+  return d;
+}
+
+void orc_dom_free(ODom* d) {
+  if (!d) return;
+  double* arr[] = {d->area, d->rarea, d->fA, d->dx, d->rdx, d->dyc, d->rdyc, d->cosy, d->siny,
+                   d->dy, d->rdy, d->dxc, d->rdxc, d->cosx, d->sinx, d->fC, d->rareac};
+  for (size_t i = 0; i < sizeof(arr) / sizeof(arr[0]); i++) free(arr[i]);
+  free(d);
+}
+
+int orc_dom_info(const ODom* d, int* out) {
+  out[0] = d->n; out[1] = d->nz; out[2] = d->nt; out[3] = d->cubed; out[4] = H;
+  for (int t = 0; t < d->nt && d->cubed; t++)
+    for (int e = 0; e < 4; e++) {
+      out[5 + (t * 4 + e) * 3 + 0] = d->nbt[t][e];
+      out[5 + (t * 4 + e) * 3 + 1] = d->nbe[t][e];
+      out[5 + (t * 4 + e) * 3 + 2] = d->nbr[t][e];
+    }
+  return 0;
+}
+
+double orc_da_min(const ODom* d) { return d->da_min; }
+
+/* export a padded metric plane set (all tiles) by name */
+int orc_get_metric(const ODom* d, const char* name, double* out) {
+  struct { const char* nm; const double* p; long pl; } tab[] = {
+      {"area", d->area, d->pc}, {"rarea", d->rarea, d->pc}, {"fA", d->fA, d->pc},
+      {"dx", d->dx, d->py}, {"rdx", d->rdx, d->py}, {"dyc", d->dyc, d->py}, {"rdyc", d->rdyc, d->py},
+      {"cosy", d->cosy, d->py}, {"siny", d->siny, d->py},
+      {"dy", d->dy, d->px}, {"rdy", d->rdy, d->px}, {"dxc", d->dxc, d->px}, {"rdxc", d->rdxc, d->px},
+      {"cosx", d->cosx, d->px}, {"sinx", d->sinx, d->px},
+      {"fC", d->fC, d->pk}, {"rareac", d->rareac, d->pk}};
+  for (size_t i = 0; i < sizeof(tab) / sizeof(tab[0]); i++)
+    if (!strcmp(tab[i].nm, name)) {
+      memcpy(out, tab[i].p, sizeof(double) * tab[i].pl * d->nt);
+      return (int)tab[i].pl;
+    }
+  return -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1-D PPM (reading R4: Colella-Woodward, uniform-grid form)           */
+/* ------------------------------------------------------------------ */
+/* edge value between cells q0 (left) and q1 (right); qm/qp the outer cells */
+static double ppm_edge(double qm, double q0, double q1, double qp) {
+  double al = 7.0 / 12.0 * (q0 + q1) - 1.0 / 12.0 * (qm + qp);
+  double lo = fmin(q0, q1), hi = fmax(q0, q1);
+  if (al < lo) al = lo;
+  if (al > hi) al = hi;
+  return al;
+}
+
+/* monotone limiter on the cell's left/right deviations */
+static void ppm_limit(double* bl, double* br) {
+  if (*bl * *br >= 0.0) {
+    *bl = 0.0;
+    *br = 0.0;
+  } else if (fabs(*bl) > 2.0 * fabs(*br)) {
+    *bl = -2.0 * *br;
+  } else if (fabs(*br) > 2.0 * fabs(*bl)) {
+    *br = -2.0 * *bl;
+  }
+}
+
+/* face value at the face between q[-s] and q[0] for Courant number c; reads
+   q[-3s .. 2s] */
+static double ppm_face(const double* q, long s, double c) {
+  if (c > 0.0) {
+    double qc = q[-s];
+    double bl = ppm_edge(q[-3 * s], q[-2 * s], q[-s], q[0]) - qc;
+    double br = ppm_edge(q[-2 * s], q[-s], q[0], q[s]) - qc;
+    ppm_limit(&bl, &br);
+    return qc + (1.0 - c) * (br - c * (bl + br));
+  } else {
+    double qc = q[0];
+    double bl = ppm_edge(q[-2 * s], q[-s], q[0], q[s]) - qc;
+    double br = ppm_edge(q[-s], q[0], q[s], q[2 * s]) - qc;
+    ppm_limit(&bl, &br);
+    return qc + (1.0 + c) * (bl + c * (bl + br));
+  }
+}
+
+/* exported for the pins: face value from the six cells q6[0..5] = q_{i-3..i+2} */
+double orc_ppm_face(const double* q6, double c) { return ppm_face(q6 + 3, 1, c); }
+
+/* ------------------------------------------------------------------ */
+/* fv_tp_2d (Section IX-C; reading R5: Lin-Rood split, averaged orders) */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  double *qx, *qy, *qi, *qj, *fx, *fx2, *fy, *fy2; /* work planes */
+} Work;
+
+static Work work_new(const ODom* d) {
+  Work w;
+  w.qx = zalloc(d->pc); w.qy = zalloc(d->pc); w.qi = zalloc(d->pc); w.qj = zalloc(d->pc);
+  w.fx = zalloc(d->px); w.fx2 = zalloc(d->px); w.fy = zalloc(d->py); w.fy2 = zalloc(d->py);
+  return w;
+}
+static void work_free(Work* w) {
+  free(w->qx); free(w->qy); free(w->qi); free(w->qj);
+  free(w->fx); free(w->fx2); free(w->fy); free(w->fy2);
+}
+
+/*
+ * One tile plane.  q: cell plane with strips filled (corners NaN on the cube).
+ * Output fluxes on the tile's faces: Fx on x-faces [0,n] x [0,n), Fy on
+ * y-faces [0,n) x [0,n].  mfx/mfy (or NULL) replace the area fluxes in the
+ * final flux.
+ */
+static void fv_tp_2d_plane(const ODom* d, int t, const double* q, const double* crx, const double* cry,
+                           const double* xfx, const double* yfx, const double* mfx, const double* mfy, double* Fx,
+                           double* Fy, Work* w) {
+  int n = d->n;
+  const double* area = d->area + t * d->pc;
+  long sc = d->wc;
+  memcpy(w->qx, q, sizeof(double) * d->pc);
+  memcpy(w->qy, q, sizeof(double) * d->pc);
+  copy_corners(d, w->qx, 0);
+  copy_corners(d, w->qy, 1);
+  /* 1. y-sweep on the plain field; inner y-update in every column */
+  for (int j = 0; j <= n; j++)
+    for (int i = -H; i < n + H; i++) w->fy2[IY(d, j, i)] = ppm_face(&w->qy[IC(d, j, i)], sc, cry[IY(d, j, i)]);
+  for (int j = 0; j < n; j++)
+    for (int i = -H; i < n + H; i++) {
+      long c = IC(d, j, i);
+      double num = q[c] * area[c] + w->fy2[IY(d, j, i)] * yfx[IY(d, j, i)] -
+                   w->fy2[IY(d, j + 1, i)] * yfx[IY(d, j + 1, i)];
+      double den = area[c] + yfx[IY(d, j, i)] - yfx[IY(d, j + 1, i)];
+      w->qi[c] = num / den;
+    }
+  /* 2. outer x-sweep of the y-updated field */
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) w->fx[IX(d, j, i)] = ppm_face(&w->qi[IC(d, j, i)], 1, crx[IX(d, j, i)]);
+  /* 3. x-sweep on the plain field; inner x-update in every row */
+  for (int j = -H; j < n + H; j++)
+    for (int i = 0; i <= n; i++) w->fx2[IX(d, j, i)] = ppm_face(&w->qx[IC(d, j, i)], 1, crx[IX(d, j, i)]);
+  for (int j = -H; j < n + H; j++)
+    for (int i = 0; i < n; i++) {
+      long c = IC(d, j, i);
+      double num = q[c] * area[c] + w->fx2[IX(d, j, i)] * xfx[IX(d, j, i)] -
+                   w->fx2[IX(d, j, i + 1)] * xfx[IX(d, j, i + 1)];
+      double den = area[c] + xfx[IX(d, j, i)] - xfx[IX(d, j, i + 1)];
+      w->qj[c] = num / den;
+    }
+  /* 4. outer y-sweep of the x-updated field */
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) w->fy[IY(d, j, i)] = ppm_face(&w->qj[IC(d, j, i)], sc, cry[IY(d, j, i)]);
+  /* 5. average of both orders times the mass (or area) flux */
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) {
+      long o = IX(d, j, i);
+      Fx[o] = 0.5 * (w->fx[o] + w->fx2[o]) * (mfx ? mfx[o] : xfx[o]);
+    }
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) {
+      long o = IY(d, j, i);
+      Fy[o] = 0.5 * (w->fy[o] + w->fy2[o]) * (mfy ? mfy[o] : yfx[o]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* delnflux, nord = 1 (reading R6: del-4 damping as a flux correction) */
+/* ------------------------------------------------------------------ */
+static void delnflux_plane(const ODom* d, int t, const double* q, double damp, const double* wdelp, double* Fx,
+                           double* Fy, Work* w) {
+  int n = d->n;
+  const double *dy = d->dy + t * d->px, *rdxc = d->rdxc + t * d->px;
+  const double *dx = d->dx + t * d->py, *rdyc = d->rdyc + t * d->py;
+  const double* rarea = d->rarea + t * d->pc;
+  double* L = w->qi; /* reuse */
+  memcpy(w->qx, q, sizeof(double) * d->pc);
+  memcpy(w->qy, q, sizeof(double) * d->pc);
+  copy_corners(d, w->qx, 0);
+  copy_corners(d, w->qy, 1);
+  const double *qx = w->qx, *qy = w->qy;
+  for (int j = -1; j <= n; j++)
+    for (int i = -1; i <= n; i++) {
+      int ring = (i < 0 || i >= n) + (j < 0 || j >= n);
+      if (ring == 2) continue; /* corners of the ring are not needed */
+      double lx = (qx[IC(d, j, i + 1)] - qx[IC(d, j, i)]) * dy[IX(d, j, i + 1)] * rdxc[IX(d, j, i + 1)] -
+                  (qx[IC(d, j, i)] - qx[IC(d, j, i - 1)]) * dy[IX(d, j, i)] * rdxc[IX(d, j, i)];
+      double ly = (qy[IC(d, j + 1, i)] - qy[IC(d, j, i)]) * dx[IY(d, j + 1, i)] * rdyc[IY(d, j + 1, i)] -
+                  (qy[IC(d, j, i)] - qy[IC(d, j - 1, i)]) * dx[IY(d, j, i)] * rdyc[IY(d, j, i)];
+      L[IC(d, j, i)] = (lx + ly) * rarea[IC(d, j, i)];
+    }
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) {
+      long o = IX(d, j, i);
+      double f = damp * (L[IC(d, j, i)] - L[IC(d, j, i - 1)]) * dy[o] * rdxc[o];
+      if (wdelp) f *= 0.5 * (wdelp[IC(d, j, i - 1)] + wdelp[IC(d, j, i)]);
+      Fx[o] += f;
+    }
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) {
+      long o = IY(d, j, i);
+      double f = damp * (L[IC(d, j, i)] - L[IC(d, j - 1, i)]) * dx[o] * rdyc[o];
+      if (wdelp) f *= 0.5 * (wdelp[IC(d, j - 1, i)] + wdelp[IC(d, j, i)]);
+      Fy[o] += f;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* state                                                               */
+/* ------------------------------------------------------------------ */
+OState* orc_state_create(ODom* d, int nq) {
+  OState* s = (OState*)calloc(1, sizeof(OState));
+  s->d = d; s->nq = nq;
+  long nc = (long)d->nt * d->nz * d->pc, nx = (long)d->nt * d->nz * d->px, ny = (long)d->nt * d->nz * d->py;
+  long ni = (long)d->nt * (d->nz + 1) * d->pc;
+  s->u = nalloc(ny); s->v = nalloc(nx); s->w = nalloc(nc); s->delp = nalloc(nc); s->pt = nalloc(nc);
+  s->delz = nalloc(nc);
+  s->q = (double**)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double*));
+  for (int m = 0; m < nq; m++) s->q[m] = nalloc(nc);
+  s->uc = nalloc(nx); s->vc = nalloc(ny); s->delpc = nalloc(nc); s->ptc = nalloc(nc); s->wc = nalloc(nc);
+  s->delzc = nalloc(nc); s->fx1 = nalloc(nx); s->fy1 = nalloc(ny); s->pef = nalloc(ni); s->gze = nalloc(ni);
+  s->amfx = zalloc(nx); s->amfy = zalloc(ny); s->acrx = zalloc(nx); s->acry = zalloc(ny);
+  s->axfx = zalloc(nx); s->ayfx = zalloc(ny);
+  return s;
+}
+
+void orc_state_free(OState* s) {
+  if (!s) return;
+  double* arr[] = {s->u, s->v, s->w, s->delp, s->pt, s->delz, s->uc, s->vc, s->delpc, s->ptc, s->wc,
+                   s->delzc, s->fx1, s->fy1, s->pef, s->gze, s->amfx, s->amfy, s->acrx, s->acry,
+                   s->axfx, s->ayfx};
+  for (size_t i = 0; i < sizeof(arr) / sizeof(arr[0]); i++) free(arr[i]);
+  for (int m = 0; m < s->nq; m++) free(s->q[m]);
+  free(s->q);
+  free(s);
+}
+
+/* field kinds: 0 cell, 1 x-face, 2 y-face, 3 interface (cells, nz+1 levels) */
+static double* field_ptr(OState* s, const char* name, int* kind, int* nlev) {
+  ODom* d = s->d;
+  *nlev = d->nz;
+  struct { const char* nm; double* p; int k; } tab[] = {
+      {"u", s->u, 2}, {"v", s->v, 1}, {"w", s->w, 0}, {"delp", s->delp, 0}, {"pt", s->pt, 0},
+      {"delz", s->delz, 0}, {"uc", s->uc, 1}, {"vc", s->vc, 2}, {"delpc", s->delpc, 0}, {"ptc", s->ptc, 0},
+      {"wc", s->wc, 0}, {"delzc", s->delzc, 0}, {"fx1", s->fx1, 1}, {"fy1", s->fy1, 2}, {"pef", s->pef, 3},
+      {"gz", s->gze, 3}, {"mfx", s->amfx, 1}, {"mfy", s->amfy, 2}, {"crx", s->acrx, 1}, {"cry", s->acry, 2},
+      {"xfx", s->axfx, 1}, {"yfx", s->ayfx, 2}};
+  for (size_t i = 0; i < sizeof(tab) / sizeof(tab[0]); i++)
+    if (!strcmp(tab[i].nm, name)) {
+      *kind = tab[i].k;
+      if (tab[i].k == 3) { *kind = 0; *nlev = d->nz + 1; }
+      return tab[i].p;
+    }
+  if (name[0] == 'q') {
+    int m = atoi(name + 1);
+    if (m >= 0 && m < s->nq) { *kind = 0; return s->q[m]; }
+  }
+  return NULL;
+}
+
+/* copy between a dense interior array and the padded field (dir 0: set, 1: get) */
+int orc_state_io(OState* s, const char* name, double* dense, int dir) {
+  ODom* d = s->d;
+  int kind, nlev;
+  double* f = field_ptr(s, name, &kind, &nlev);
+  if (!f) return -1;
+  int n = d->n;
+  int ni = n + (kind == 1), nj = n + (kind == 2);
+  long pl = kind == 0 ? d->pc : kind == 1 ? d->px : d->py;
+  long q = 0;
+  for (int t = 0; t < d->nt; t++)
+    for (int k = 0; k < nlev; k++)
+      for (int j = 0; j < nj; j++)
+        for (int i = 0; i < ni; i++, q++) {
+          long o = ((long)t * nlev + k) * pl + (kind == 1 ? IX(d, j, i) : IC(d, j, i));
+          if (dir == 0) f[o] = dense[q]; else dense[q] = f[o];
+        }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* c_sw (reading R7)                                                   */
+/* ------------------------------------------------------------------ */
+static void c_sw(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double dt2 = 0.5 * P->dt;
+  double* uc0 = zalloc(d->px);
+  double* vc0 = zalloc(d->py);
+  double* ut = zalloc(d->px);
+  double* vt = zalloc(d->py);
+  double* ke = zalloc(d->pc);
+  double* vort = zalloc(d->pk);
+  for (int t = 0; t < d->nt; t++) {
+    const double *dy = d->dy + t * d->px, *sinx = d->sinx + t * d->px, *cosx = d->cosx + t * d->px,
+                 *dxc = d->dxc + t * d->px, *rdxc = d->rdxc + t * d->px;
+    const double *dx = d->dx + t * d->py, *siny = d->siny + t * d->py, *cosy = d->cosy + t * d->py,
+                 *dyc = d->dyc + t * d->py, *rdyc = d->rdyc + t * d->py;
+    const double *rarea = d->rarea + t * d->pc, *fC = d->fC + t * d->pk, *rareac = d->rareac + t * d->pk;
+    for (int k = 0; k < nz; k++) {
+      long oc = ((long)t * nz + k) * d->pc, ox = ((long)t * nz + k) * d->px, oy = ((long)t * nz + k) * d->py;
+      const double *u = s->u + oy, *v = s->v + ox;
+      const double *delp = s->delp + oc, *pt = s->pt + oc, *w = s->w + oc;
+      /* 1-2. C-grid winds from the D-grid by 4-point averages; contravariant */
+      for (int j = -1; j <= n; j++)
+        for (int i = -1; i <= n + 1; i++) {
+          long o = IX(d, j, i);
+          uc0[o] = 0.25 * (u[IY(d, j, i - 1)] + u[IY(d, j, i)] + u[IY(d, j + 1, i - 1)] + u[IY(d, j + 1, i)]);
+          ut[o] = (uc0[o] - cosx[o] * v[o]) / (sinx[o] * sinx[o]);
+        }
+      for (int j = -1; j <= n + 1; j++)
+        for (int i = -1; i <= n; i++) {
+          long o = IY(d, j, i);
+          vc0[o] = 0.25 * (v[IX(d, j - 1, i)] + v[IX(d, j - 1, i + 1)] + v[IX(d, j, i)] + v[IX(d, j, i + 1)]);
+          vt[o] = (vc0[o] - cosy[o] * u[o]) / (siny[o] * siny[o]);
+        }
+      /* 3. upwind half-step of delp, pt, w */
+      double* fx1 = s->fx1 + ox;
+      double* fy1 = s->fy1 + oy;
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) {
+          long o = IX(d, j, i);
+          fx1[o] = dt2 * ut[o] * dy[o] * sinx[o];
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) {
+          long o = IY(d, j, i);
+          fy1[o] = dt2 * vt[o] * dx[o] * siny[o];
+        }
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          long c = IC(d, j, i);
+          double fm[4], fp[4], fw[4];
+          /* faces: W, E (x), S, N (y); flux positive in +x / +y */
+          long fcs[4] = {IX(d, j, i), IX(d, j, i + 1), IY(d, j, i), IY(d, j + 1, i)};
+          long lo[4] = {IC(d, j, i - 1), IC(d, j, i), IC(d, j - 1, i), IC(d, j, i)};
+          long hi[4] = {IC(d, j, i), IC(d, j, i + 1), IC(d, j, i), IC(d, j + 1, i)};
+          for (int f = 0; f < 4; f++) {
+            double F = f < 2 ? fx1[fcs[f]] : fy1[fcs[f]];
+            long up = F > 0.0 ? lo[f] : hi[f];
+            fm[f] = F * delp[up];
+            fp[f] = fm[f] * pt[up];
+            fw[f] = fm[f] * w[up];
+          }
+          double dpc = delp[c] + (fm[0] - fm[1] + fm[2] - fm[3]) * rarea[c];
+          s->delpc[oc + c] = dpc;
+          s->ptc[oc + c] = (pt[c] * delp[c] + (fp[0] - fp[1] + fp[2] - fp[3]) * rarea[c]) / dpc;
+          s->wc[oc + c] = (w[c] * delp[c] + (fw[0] - fw[1] + fw[2] - fw[3]) * rarea[c]) / dpc;
+        }
+      /* 4. kinetic energy at cells and absolute vorticity at corners */
+      for (int j = -1; j <= n; j++)
+        for (int i = -1; i <= n; i++) {
+          double ua = 0.5 * (ut[IX(d, j, i)] + ut[IX(d, j, i + 1)]);
+          double va = 0.5 * (vt[IY(d, j, i)] + vt[IY(d, j + 1, i)]);
+          ke[IC(d, j, i)] = 0.5 * dt2 * (ua * ua + va * va);
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i <= n; i++) {
+          long o = IK(d, j, i);
+          double ts = uc0[IX(d, j - 1, i)] * dxc[IX(d, j - 1, i)];
+          double te = vc0[IY(d, j, i)] * dyc[IY(d, j, i)];
+          double tn = uc0[IX(d, j, i)] * dxc[IX(d, j, i)];
+          double tw = vc0[IY(d, j, i - 1)] * dyc[IY(d, j, i - 1)];
+          int tc = d->cubed && (i == 0 || i == n) && (j == 0 || j == n);
+          if (tc) { /* cube corner: triangle, the W/E-strip term is absent */
+            if (i == 0) tw = 0.0; else te = 0.0;
+          }
+          vort[o] = (ts + te - tn - tw) * rareac[o] + fC[o];
+        }
+      /* 5. vorticity flux and kinetic-energy gradient on the C-grid winds */
+      double* ucn = s->uc + ox;
+      double* vcn = s->vc + oy;
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) {
+          long o = IX(d, j, i);
+          ucn[o] = uc0[o] + dt2 * 0.5 * (vort[IK(d, j, i)] + vort[IK(d, j + 1, i)]) * v[o] +
+                   (ke[IC(d, j, i - 1)] - ke[IC(d, j, i)]) * rdxc[o];
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) {
+          long o = IY(d, j, i);
+          vcn[o] = vc0[o] - dt2 * 0.5 * (vort[IK(d, j, i)] + vort[IK(d, j, i + 1)]) * u[o] +
+                   (ke[IC(d, j - 1, i)] - ke[IC(d, j, i)]) * rdyc[o];
+        }
+    }
+  }
+  free(uc0); free(vc0); free(ut); free(vt); free(ke); free(vort);
+}
+
+/* ------------------------------------------------------------------ */
+/* update_dz_c (reading R8)                                            */
+/* ------------------------------------------------------------------ */
+static void update_dz_c(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double g = P->grav;
+  double* gz = zalloc((long)(nz + 1) * d->pc);
+  double* gzn = zalloc((long)(nz + 1) * d->pc);
+  for (int t = 0; t < d->nt; t++) {
+    const double* area = d->area + t * d->pc;
+    /* interface geopotential from the surface (0) up, interior and ring 1 */
+    for (int j = -1; j <= n; j++)
+      for (int i = -1; i <= n; i++) {
+        int ring = (i < 0 || i >= n) + (j < 0 || j >= n);
+        if (ring == 2) continue;
+        long c = IC(d, j, i);
+        gz[(long)nz * d->pc + c] = 0.0;
+        for (int k = nz - 1; k >= 0; k--)
+          gz[(long)k * d->pc + c] = gz[(long)(k + 1) * d->pc + c] - g * s->delz[((long)t * nz + k) * d->pc + c];
+      }
+    for (int K = 0; K < nz; K++) {
+      const double* g0 = gz + (long)K * d->pc;
+      const double *fxa = s->fx1 + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->px,
+                   *fxb = s->fx1 + ((long)t * nz + K) * d->px;
+      const double *fya = s->fy1 + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->py,
+                   *fyb = s->fy1 + ((long)t * nz + K) * d->py;
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          long c = IC(d, j, i);
+          long fcs[4] = {IX(d, j, i), IX(d, j, i + 1), IY(d, j, i), IY(d, j + 1, i)};
+          long lo[4] = {IC(d, j, i - 1), IC(d, j, i), IC(d, j - 1, i), IC(d, j, i)};
+          long hi[4] = {IC(d, j, i), IC(d, j, i + 1), IC(d, j, i), IC(d, j + 1, i)};
+          double F[4], G[4];
+          for (int f = 0; f < 4; f++) {
+            double a = f < 2 ? fxa[fcs[f]] : fya[fcs[f]];
+            double b = f < 2 ? fxb[fcs[f]] : fyb[fcs[f]];
+            F[f] = K == 0 ? b : 0.5 * (a + b);
+            G[f] = F[f] * (F[f] > 0.0 ? g0[lo[f]] : g0[hi[f]]);
+          }
+          gzn[(long)K * d->pc + c] = (g0[c] * area[c] + G[0] - G[1] + G[2] - G[3]) /
+                                     (area[c] + F[0] - F[1] + F[2] - F[3]);
+        }
+    }
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) {
+        long c = IC(d, j, i);
+        gzn[(long)nz * d->pc + c] = 0.0;
+        for (int k = 0; k < nz; k++) {
+          double dz = (gzn[(long)(k + 1) * d->pc + c] - gzn[(long)k * d->pc + c]) / g;
+          s->delzc[((long)t * nz + k) * d->pc + c] = fmin(dz, -P->dz_min);
+        }
+      }
+  }
+  free(gz); free(gzn);
+}
+
+/* ------------------------------------------------------------------ */
+/* riem_solver_c (Section IX-B; reading R9)                            */
+/* ------------------------------------------------------------------ */
+/* tridiagonal: a lower, b diagonal, c upper, d rhs; Thomas without pivoting */
+void orc_thomas(int m, const double* a, const double* b, const double* c, const double* rhs, double* x) {
+  double* cp = zalloc(m);
+  double* dp = zalloc(m);
+  cp[0] = c[0] / b[0];
+  dp[0] = rhs[0] / b[0];
+  for (int k = 1; k < m; k++) {
+    double den = b[k] - a[k] * cp[k - 1];
+    cp[k] = c[k] / den;
+    dp[k] = (rhs[k] - a[k] * dp[k - 1]) / den;
+  }
+  x[m - 1] = dp[m - 1];
+  for (int k = m - 2; k >= 0; k--) x[k] = dp[k] - cp[k] * x[k + 1];
+  free(cp); free(dp);
+}
+
+/* dense LU with partial pivoting (brute-force check of the column solve) */
+void orc_dense_lu(int m, const double* A0, const double* b0, double* x) {
+  double* A = zalloc((long)m * m);
+  double* b = zalloc(m);
+  memcpy(A, A0, sizeof(double) * m * m);
+  memcpy(b, b0, sizeof(double) * m);
+  for (int col = 0; col < m; col++) {
+    int piv = col;
+    for (int r = col + 1; r < m; r++)
+      if (fabs(A[r * m + col]) > fabs(A[piv * m + col])) piv = r;
+    if (piv != col) {
+      for (int c = 0; c < m; c++) { double tmp = A[col * m + c]; A[col * m + c] = A[piv * m + c]; A[piv * m + c] = tmp; }
+      double tmp = b[col]; b[col] = b[piv]; b[piv] = tmp;
+    }
+    for (int r = col + 1; r < m; r++) {
+      double f = A[r * m + col] / A[col * m + col];
+      for (int c = col; c < m; c++) A[r * m + c] -= f * A[col * m + c];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int r = m - 1; r >= 0; r--) {
+    double sacc = b[r];
+    for (int c = r + 1; c < m; c++) sacc -= A[r * m + c] * x[c];
+    x[r] = sacc / A[r * m + r];
+  }
+  free(A); free(b);
+}
+
+/*
+ * One column.  Inputs per layer k (0 = top): delpc, ptc, wc, delzc.  dt is the
+ * solver's time step (dt/2 of the substep).  Outputs: pef[nz+1] interface
+ * total pressure, gz[nz+1] interface geopotential (0 at the surface).  If
+ * sys != NULL the tridiagonal system (a, b, c, rhs; 4*nz) is returned too and
+ * use_lu selects the dense solver for the brute-force pin.
+ */
+void orc_riem_column(int nz, const double* delpc, const double* ptc, const double* wc, const double* delzc,
+                     double dt, double ptop, double grav, double rdgas, double cp_air, double a_imp, double* pef,
+                     double* gzo, double* sys, int use_lu, double* wsol) {
+  double kappa = rdgas / cp_air, gama = 1.0 / (1.0 - kappa);
+  double *pe = zalloc(nz + 1), *pp = zalloc(nz), *C = zalloc(nz), *p = zalloc(nz);
+  double *a = zalloc(nz), *b = zalloc(nz), *c = zalloc(nz), *r = zalloc(nz), *W = zalloc(nz + 1);
+  pe[0] = ptop;
+  for (int k = 0; k < nz; k++) pe[k + 1] = pe[k] + delpc[k];
+  for (int k = 0; k < nz; k++) {
+    p[k] = -delpc[k] * rdgas * ptc[k] / (grav * delzc[k]);
+    double ph = delpc[k] / log(pe[k + 1] / pe[k]);
+    pp[k] = p[k] - ph;
+    C[k] = a_imp * dt * gama * p[k] / (-delzc[k]);
+  }
+  for (int K = 0; K < nz; K++) {
+    double m = K == 0 ? 0.5 * delpc[0] / grav : 0.5 * (delpc[K - 1] + delpc[K]) / grav;
+    double wn = K == 0 ? wc[0] : 0.5 * (wc[K - 1] + wc[K]);
+    double Cu = K > 0 ? C[K - 1] : 0.0; /* layer above the interface */
+    double Cd = C[K];                   /* layer below */
+    a[K] = -Cu;
+    b[K] = m / dt + Cu + Cd;
+    c[K] = K < nz - 1 ? -Cd : 0.0;
+    r[K] = m / dt * wn + pp[K] - (K > 0 ? pp[K - 1] : 0.0);
+  }
+  if (sys)
+    for (int K = 0; K < nz; K++) { sys[K] = a[K]; sys[nz + K] = b[K]; sys[2 * nz + K] = c[K]; sys[3 * nz + K] = r[K]; }
+  if (use_lu) {
+    double* A = zalloc((long)nz * nz);
+    for (int K = 0; K < nz; K++) {
+      A[K * nz + K] = b[K];
+      if (K > 0) A[K * nz + K - 1] = a[K];
+      if (K < nz - 1) A[K * nz + K + 1] = c[K];
+    }
+    orc_dense_lu(nz, A, r, W);
+    free(A);
+  } else {
+    orc_thomas(nz, a, b, c, r, W);
+  }
+  W[nz] = 0.0;
+  if (wsol) for (int K = 0; K <= nz; K++) wsol[K] = W[K];
+  double* ppn = zalloc(nz);
+  double* dzn = zalloc(nz);
+  for (int k = 0; k < nz; k++) {
+    dzn[k] = delzc[k] + dt * (W[k + 1] - W[k]);
+    ppn[k] = pp[k] + C[k] * (W[k + 1] - W[k]) / a_imp;
+  }
+  pef[0] = ptop;
+  for (int K = 1; K < nz; K++) pef[K] = pe[K] + 0.5 * (ppn[K - 1] + ppn[K]);
+  pef[nz] = pe[nz] + ppn[nz - 1];
+  gzo[nz] = 0.0;
+  for (int K = nz - 1; K >= 0; K--) gzo[K] = gzo[K + 1] - grav * dzn[K];
+  free(pe); free(pp); free(C); free(p); free(a); free(b); free(c); free(r); free(W); free(ppn); free(dzn);
+}
+
+static void riem_solver_c(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double *dp = zalloc(nz), *pt = zalloc(nz), *w = zalloc(nz), *dz = zalloc(nz), *pef = zalloc(nz + 1),
+         *gz = zalloc(nz + 1);
+  for (int t = 0; t < d->nt; t++)
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) {
+        long c = IC(d, j, i);
+        for (int k = 0; k < nz; k++) {
+          long o = ((long)t * nz + k) * d->pc + c;
+          dp[k] = s->delpc[o]; pt[k] = s->ptc[o]; w[k] = s->wc[o]; dz[k] = s->delzc[o];
+        }
+        orc_riem_column(nz, dp, pt, w, dz, 0.5 * P->dt, P->ptop, P->grav, P->rdgas, P->cp_air, P->a_imp, pef,
+                        gz, NULL, 0, NULL);
+        for (int K = 0; K <= nz; K++) {
+          long o = ((long)t * (nz + 1) + K) * d->pc + c;
+          s->pef[o] = pef[K];
+          s->gze[o] = gz[K];
+        }
+      }
+  free(dp); free(pt); free(w); free(dz); free(pef); free(gz);
+}
+
+/* ------------------------------------------------------------------ */
+/* p_grad_c (reading R10: Lin 1997 contour integral)                   */
+/* ------------------------------------------------------------------ */
+static double pgrad(double gA0, double gA1, double gB0, double gB1, double pA0, double pA1, double pB0,
+                    double pB1) {
+  return ((gA1 - gB0) * (pB1 - pA0) + (gA0 - gB1) * (pA1 - pB0)) / (pA1 - pA0 + pB1 - pB0);
+}
+
+static void p_grad_c(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double dt2 = 0.5 * P->dt;
+  for (int t = 0; t < d->nt; t++) {
+    const double* rdxc = d->rdxc + t * d->px;
+    const double* rdyc = d->rdyc + t * d->py;
+    for (int k = 0; k < nz; k++) {
+      const double *p0 = s->pef + ((long)t * (nz + 1) + k) * d->pc, *p1 = p0 + d->pc;
+      const double *g0 = s->gze + ((long)t * (nz + 1) + k) * d->pc, *g1 = g0 + d->pc;
+      double* uc = s->uc + ((long)t * nz + k) * d->px;
+      double* vc = s->vc + ((long)t * nz + k) * d->py;
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) {
+          long A = IC(d, j, i - 1), B = IC(d, j, i), o = IX(d, j, i);
+          uc[o] += dt2 * rdxc[o] * pgrad(g0[A], g1[A], g0[B], g1[B], p0[A], p1[A], p0[B], p1[B]);
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) {
+          long A = IC(d, j - 1, i), B = IC(d, j, i), o = IY(d, j, i);
+          vc[o] += dt2 * rdyc[o] * pgrad(g0[A], g1[A], g0[B], g1[B], p0[A], p1[A], p0[B], p1[B]);
+        }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* d_sw (reading R11)                                                  */
+/* ------------------------------------------------------------------ */
+static void d_sw(OState* s, const OParams* P, int accumulate) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double dt = P->dt;
+  double damp = pow(P->d4_bg * d->da_min, P->nord + 1);
+  Work w = work_new(d);
+  double *ut = zalloc(d->px), *vt = zalloc(d->py), *crx = zalloc(d->px), *cry = zalloc(d->py);
+  double *xfx = zalloc(d->px), *yfx = zalloc(d->py), *mfx = zalloc(d->px), *mfy = zalloc(d->py);
+  double *Fx = zalloc(d->px), *Fy = zalloc(d->py), *vort = nalloc(d->pc), *ke = zalloc(d->pk);
+  long nc = (long)d->nt * nz * d->pc, nx = (long)d->nt * nz * d->px, ny = (long)d->nt * nz * d->py;
+  double *u_n = nalloc(ny), *v_n = nalloc(nx), *w_n = nalloc(nc), *dp_n = nalloc(nc), *pt_n = nalloc(nc);
+  for (int t = 0; t < d->nt; t++) {
+    const double *dy = d->dy + t * d->px, *sinx = d->sinx + t * d->px, *cosx = d->cosx + t * d->px,
+                 *rdxc = d->rdxc + t * d->px, *rdy = d->rdy + t * d->px;
+    const double *dx = d->dx + t * d->py, *siny = d->siny + t * d->py, *cosy = d->cosy + t * d->py,
+                 *rdyc = d->rdyc + t * d->py, *rdx = d->rdx + t * d->py;
+    const double *rarea = d->rarea + t * d->pc, *fA = d->fA + t * d->pc;
+    for (int k = 0; k < nz; k++) {
+      long oc = ((long)t * nz + k) * d->pc, ox = ((long)t * nz + k) * d->px, oy = ((long)t * nz + k) * d->py;
+      const double *u = s->u + oy, *v = s->v + ox, *uc = s->uc + ox, *vc = s->vc + oy;
+      const double *delp = s->delp + oc, *pt = s->pt + oc, *wv = s->w + oc;
+      /* 1. Courant numbers and area fluxes from the C-grid winds */
+      for (int j = -H; j < n + H; j++)
+        for (int i = 0; i <= n; i++) {
+          long o = IX(d, j, i);
+          ut[o] = (uc[o] - cosx[o] * v[o]) / (sinx[o] * sinx[o]);
+          xfx[o] = dt * ut[o] * dy[o] * sinx[o];
+          crx[o] = dt * ut[o] * sinx[o] * rdxc[o];
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = -H; i < n + H; i++) {
+          long o = IY(d, j, i);
+          vt[o] = (vc[o] - cosy[o] * u[o]) / (siny[o] * siny[o]);
+          yfx[o] = dt * vt[o] * dx[o] * siny[o];
+          cry[o] = dt * vt[o] * siny[o] * rdyc[o];
+        }
+      /* 2. mass: transport + damping -> mass fluxes, new delp */
+      fv_tp_2d_plane(d, t, delp, crx, cry, xfx, yfx, NULL, NULL, mfx, mfy, &w);
+      delnflux_plane(d, t, delp, damp, NULL, mfx, mfy, &w);
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          long c = IC(d, j, i);
+          dp_n[oc + c] = delp[c] + (mfx[IX(d, j, i)] - mfx[IX(d, j, i + 1)] + mfy[IY(d, j, i)] -
+                                    mfy[IY(d, j + 1, i)]) * rarea[c];
+        }
+      /* 3. pt and w with the mass fluxes, mass-weighted damping */
+      for (int fld = 0; fld < 2; fld++) {
+        const double* q = fld == 0 ? pt : wv;
+        double* qn = fld == 0 ? pt_n : w_n;
+        fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w);
+        delnflux_plane(d, t, q, damp, delp, Fx, Fy, &w);
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i < n; i++) {
+            long c = IC(d, j, i);
+            qn[oc + c] = (q[c] * delp[c] + (Fx[IX(d, j, i)] - Fx[IX(d, j, i + 1)] + Fy[IY(d, j, i)] -
+                                            Fy[IY(d, j + 1, i)]) * rarea[c]) / dp_n[oc + c];
+          }
+      }
+      /* 4. kinetic energy at corners from upwind-PPM corner winds */
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i <= n; i++) {
+          double ub_adv = 0.5 * (uc[IX(d, j - 1, i)] + uc[IX(d, j, i)]);
+          double vb_adv = 0.5 * (vc[IY(d, j, i - 1)] + vc[IY(d, j, i)]);
+          double cu = dt * ub_adv * (ub_adv > 0.0 ? rdx[IY(d, j, i - 1)] : rdx[IY(d, j, i)]);
+          double cv = dt * vb_adv * (vb_adv > 0.0 ? rdy[IX(d, j - 1, i)] : rdy[IX(d, j, i)]);
+          double ub = ppm_face(&u[IY(d, j, i)], 1, cu);
+          double vb = ppm_face(&v[IX(d, j, i)], d->wx, cv);
+          ke[IK(d, j, i)] = 0.5 * dt * (ub * ub_adv + vb * vb_adv);
+        }
+      /* 5. cell-centre absolute vorticity from the edge circulation */
+      for (int j = -H; j < n + H; j++)
+        for (int i = -H; i < n + H; i++) {
+          int inx = (i >= 0 && i < n), iny = (j >= 0 && j < n);
+          if (d->cubed && !inx && !iny) { vort[IC(d, j, i)] = NAN; continue; }
+          vort[IC(d, j, i)] = (u[IY(d, j, i)] * dx[IY(d, j, i)] - u[IY(d, j + 1, i)] * dx[IY(d, j + 1, i)] +
+                               v[IX(d, j, i + 1)] * dy[IX(d, j, i + 1)] - v[IX(d, j, i)] * dy[IX(d, j, i)]) *
+                                  rarea[IC(d, j, i)] + fA[IC(d, j, i)];
+        }
+      fv_tp_2d_plane(d, t, vort, crx, cry, xfx, yfx, NULL, NULL, Fx, Fy, &w);
+      delnflux_plane(d, t, vort, damp, NULL, Fx, Fy, &w);
+      /* 6. new D-grid winds: vorticity flux plus kinetic-energy gradient */
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) {
+          long o = IY(d, j, i);
+          u_n[oy + o] = u[o] + (Fy[o] + ke[IK(d, j, i)] - ke[IK(d, j, i + 1)]) * rdx[o];
+        }
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) {
+          long o = IX(d, j, i);
+          v_n[ox + o] = v[o] + (-Fx[o] + ke[IK(d, j, i)] - ke[IK(d, j + 1, i)]) * rdy[o];
+        }
+      if (accumulate) {
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i <= n; i++) {
+            long o = IX(d, j, i);
+            s->amfx[ox + o] += mfx[o]; s->acrx[ox + o] += crx[o]; s->axfx[ox + o] += xfx[o];
+          }
+        for (int j = 0; j <= n; j++)
+          for (int i = 0; i < n; i++) {
+            long o = IY(d, j, i);
+            s->amfy[oy + o] += mfy[o]; s->acry[oy + o] += cry[o]; s->ayfx[oy + o] += yfx[o];
+          }
+      }
+    }
+  }
+  /* interior results replace the state (halos are refilled by the next step) */
+  for (int t = 0; t < d->nt; t++)
+    for (int k = 0; k < nz; k++) {
+      long oc = ((long)t * nz + k) * d->pc, ox = ((long)t * nz + k) * d->px, oy = ((long)t * nz + k) * d->py;
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          long c = oc + IC(d, j, i);
+          s->delp[c] = dp_n[c]; s->pt[c] = pt_n[c]; s->w[c] = w_n[c];
+        }
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) s->u[oy + IY(d, j, i)] = u_n[oy + IY(d, j, i)];
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) s->v[ox + IX(d, j, i)] = v_n[ox + IX(d, j, i)];
+    }
+  work_free(&w);
+  free(ut); free(vt); free(crx); free(cry); free(xfx); free(yfx); free(mfx); free(mfy); free(Fx); free(Fy);
+  free(vort); free(ke); free(u_n); free(v_n); free(w_n); free(dp_n); free(pt_n);
+}
+
+/* ------------------------------------------------------------------ */
+/* the acoustic substep (Section II: the innermost loop, with halo     */
+/* exchanges at several execution points)                             */
+/* ------------------------------------------------------------------ */
+static void fill_prognostics(OState* s) {
+  ODom* d = s->d;
+  fill_faces(d, s->v, s->u, d->nz, H, 1, 1);
+  fill_cells(d, s->w, d->nz, H);
+  fill_cells(d, s->delp, d->nz, H);
+  fill_cells(d, s->pt, d->nz, H);
+  fill_cells(d, s->delz, d->nz, H);
+}
+
+int orc_substep(OState* s, const OParams* P, int stop_after, int accumulate) {
+  ODom* d = s->d;
+  fill_prognostics(s);
+  if (stop_after == 0) return 0;
+  c_sw(s, P);
+  if (stop_after == 1) return 0;
+  update_dz_c(s, P);
+  if (stop_after == 2) return 0;
+  riem_solver_c(s, P);
+  if (stop_after == 3) return 0;
+  fill_cells(d, s->pef, d->nz + 1, 1);
+  fill_cells(d, s->gze, d->nz + 1, 1);
+  p_grad_c(s, P);
+  if (stop_after == 4) return 0;
+  fill_faces(d, s->uc, s->vc, d->nz, H, 2, 0);
+  d_sw(s, P, accumulate);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* tracer_2d (reading R12) and the remapping-step driver               */
+/* ------------------------------------------------------------------ */
+static void tracer_2d(OState* s, const double* dp_start) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  fill_faces(d, s->amfx, s->amfy, nz, H, 2, 0);
+  fill_faces(d, s->acrx, s->acry, nz, H, 2, 0);
+  fill_faces(d, s->axfx, s->ayfx, nz, H, 2, 0);
+  double cmax = 0.0;
+  for (int t = 0; t < d->nt; t++)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          cmax = fmax(cmax, fabs(s->acrx[((long)t * nz + k) * d->px + IX(d, j, i)]));
+          cmax = fmax(cmax, fabs(s->acry[((long)t * nz + k) * d->py + IY(d, j, i)]));
+        }
+  int nsplt = (int)ceil(cmax);
+  if (nsplt < 1) nsplt = 1;
+  double fr = 1.0 / nsplt;
+  Work w = work_new(d);
+  double *crx = zalloc(d->px), *cry = zalloc(d->py), *xfx = zalloc(d->px), *yfx = zalloc(d->py);
+  double *mfx = zalloc(d->px), *mfy = zalloc(d->py), *Fx = zalloc(d->px), *Fy = zalloc(d->py);
+  long nc = (long)d->nt * nz * d->pc;
+  double* dp0 = zalloc(nc);
+  double* dp1 = zalloc(nc);
+  memcpy(dp0, dp_start, sizeof(double) * nc);
+  for (int it = 0; it < nsplt; it++) {
+    for (int m = 0; m < s->nq; m++) fill_cells(d, s->q[m], nz, H);
+    for (int t = 0; t < d->nt; t++) {
+      const double* rarea = d->rarea + t * d->pc;
+      for (int k = 0; k < nz; k++) {
+        long oc = ((long)t * nz + k) * d->pc, ox = ((long)t * nz + k) * d->px, oy = ((long)t * nz + k) * d->py;
+        for (long o = 0; o < d->px; o++) {
+          crx[o] = s->acrx[ox + o] * fr; xfx[o] = s->axfx[ox + o] * fr; mfx[o] = s->amfx[ox + o] * fr;
+        }
+        for (long o = 0; o < d->py; o++) {
+          cry[o] = s->acry[oy + o] * fr; yfx[o] = s->ayfx[oy + o] * fr; mfy[o] = s->amfy[oy + o] * fr;
+        }
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i < n; i++) {
+            long c = IC(d, j, i);
+            dp1[oc + c] = dp0[oc + c] + (mfx[IX(d, j, i)] - mfx[IX(d, j, i + 1)] + mfy[IY(d, j, i)] -
+                                         mfy[IY(d, j + 1, i)]) * rarea[c];
+          }
+        for (int m = 0; m < s->nq; m++) {
+          double* q = s->q[m] + oc;
+          fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w);
+          for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+              long c = IC(d, j, i);
+              w.qj[c] = (q[c] * dp0[oc + c] + (Fx[IX(d, j, i)] - Fx[IX(d, j, i + 1)] + Fy[IY(d, j, i)] -
+                                               Fy[IY(d, j + 1, i)]) * rarea[c]) / dp1[oc + c];
+            }
+          for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) q[IC(d, j, i)] = w.qj[IC(d, j, i)];
+        }
+      }
+    }
+    memcpy(dp0, dp1, sizeof(double) * nc);
+  }
+  work_free(&w);
+  free(crx); free(cry); free(xfx); free(yfx); free(mfx); free(mfy); free(Fx); free(Fy); free(dp0); free(dp1);
+}
+
+int orc_run_dyn(OState* s, const OParams* P, int n_steps) {
+  ODom* d = s->d;
+  long nc = (long)d->nt * d->nz * d->pc;
+  long nx = (long)d->nt * d->nz * d->px, ny = (long)d->nt * d->nz * d->py;
+  double* dp_start = zalloc(nc);
+  for (int st = 0; st < n_steps; st++) {
+    memcpy(dp_start, s->delp, sizeof(double) * nc);
+    memset(s->amfx, 0, sizeof(double) * nx); memset(s->acrx, 0, sizeof(double) * nx);
+    memset(s->axfx, 0, sizeof(double) * nx); memset(s->amfy, 0, sizeof(double) * ny);
+    memset(s->acry, 0, sizeof(double) * ny); memset(s->ayfx, 0, sizeof(double) * ny);
+    for (int it = 0; it < P->n_split; it++) orc_substep(s, P, -1, 1);
+    if (s->nq > 0) tracer_2d(s, dp_start);
+  }
+  free(dp_start);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* global mass (reading R13): sum of delp * area, Neumaier compensated */
+/* ------------------------------------------------------------------ */
+double orc_mass_sum(OState* s) {
+  ODom* d = s->d;
+  double sum = 0.0, comp = 0.0;
+  for (int t = 0; t < d->nt; t++)
+    for (int k = 0; k < d->nz; k++)
+      for (int j = 0; j < d->n; j++)
+        for (int i = 0; i < d->n; i++) {
+          double x = s->delp[((long)t * d->nz + k) * d->pc + IC(d, j, i)] * d->area[t * d->pc + IC(d, j, i)];
+          double tt = sum + x;
+          if (fabs(sum) >= fabs(x)) comp += (sum - tt) + x; else comp += (x - tt) + sum;
+          sum = tt;
+        }
+  return sum + comp;
+}
+
+/* ------------------------------------------------------------------ */
+/* exported single-plane helpers for the pins                          */
+/* ------------------------------------------------------------------ */
+/* fv_tp_2d on level 0 of tile t of a state-less domain, dense inputs:
+   q [n][n]; crx, xfx [n][n+1]; cry, yfx [n+1][n] (interior faces, filled
+   periodically / by the cube halo), fluxes out: Fx [n][n+1], Fy [n+1][n]. */
+int orc_fv_tp_2d_dense(ODom* d, int t, const double* q, const double* crx, const double* cry, const double* xfx,
+                       const double* yfx, double* Fx_out, double* Fy_out) {
+  int n = d->n, nt = d->nt;
+  double *Q = nalloc(nt * d->pc), *CX = nalloc(nt * d->px), *CY = nalloc(nt * d->py);
+  double *XF = nalloc(nt * d->px), *YF = nalloc(nt * d->py);
+  double *Fx = zalloc(d->px), *Fy = zalloc(d->py);
+  for (int tt = 0; tt < nt; tt++)
+    for (int j = 0; j <= n; j++)
+      for (int i = 0; i <= n; i++) {
+        long dq = ((long)tt * n + j) * n + i;
+        if (j < n && i < n) Q[tt * d->pc + IC(d, j, i)] = q[dq];
+        if (j < n) {
+          long o = ((long)tt * n + j) * (n + 1) + i;
+          CX[tt * d->px + IX(d, j, i)] = crx[o]; XF[tt * d->px + IX(d, j, i)] = xfx[o];
+        }
+        if (i < n) {
+          long o = ((long)tt * (n + 1) + j) * n + i;
+          CY[tt * d->py + IY(d, j, i)] = cry[o]; YF[tt * d->py + IY(d, j, i)] = yfx[o];
+        }
+      }
+  fill_cells(d, Q, 1, H);
+  fill_faces(d, CX, CY, 1, H, 2, 0);
+  fill_faces(d, XF, YF, 1, H, 2, 0);
+  Work w = work_new(d);
+  fv_tp_2d_plane(d, t, Q + t * d->pc, CX + t * d->px, CY + t * d->py, XF + t * d->px, YF + t * d->py, NULL, NULL,
+                 Fx, Fy, &w);
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) Fx_out[(long)j * (n + 1) + i] = Fx[IX(d, j, i)];
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) Fy_out[(long)j * n + i] = Fy[IY(d, j, i)];
+  work_free(&w);
+  free(Q); free(CX); free(CY); free(XF); free(YF); free(Fx); free(Fy);
+  return 0;
+}
+
+/* delnflux fluxes of a dense level-0 field of tile t (unweighted) */
+int orc_delnflux_dense(ODom* d, int t, const double* q, double damp, double* Fx_out, double* Fy_out) {
+  int n = d->n, nt = d->nt;
+  double* Q = nalloc(nt * d->pc);
+  double *Fx = zalloc(d->px), *Fy = zalloc(d->py);
+  for (int tt = 0; tt < nt; tt++)
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) Q[tt * d->pc + IC(d, j, i)] = q[((long)tt * n + j) * n + i];
+  fill_cells(d, Q, 1, H);
+  Work w = work_new(d);
+  delnflux_plane(d, t, Q + t * d->pc, damp, NULL, Fx, Fy, &w);
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) Fx_out[(long)j * (n + 1) + i] = Fx[IX(d, j, i)];
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) Fy_out[(long)j * n + i] = Fy[IY(d, j, i)];
+  work_free(&w);
+  free(Q); free(Fx); free(Fy);
+  return 0;
+}
+
+/* halo fill exports (whole padded arrays, all tiles, one level) */
+int orc_fill_cells(ODom* d, double* f, int nlev, int depth) { fill_cells(d, f, nlev, depth); return 0; }
+int orc_fill_faces(ODom* d, double* fxf, double* fyf, int nlev, int kind, int corners) {
+  fill_faces(d, fxf, fyf, nlev, H, kind, corners);
+  return 0;
+}
+int orc_copy_corners(ODom* d, double* q, int dir) { copy_corners(d, q, dir); return 0; }
+int orc_plane_sizes(const ODom* d, long* out) {
+  out[0] = d->pc; out[1] = d->px; out[2] = d->py; out[3] = d->pk; out[4] = d->wc; out[5] = d->wx;
+  return 0;
+}
+int orc_gpoint(const ODom* d, int t, double X, double Y, double* p) { gpoint(d, t, X, Y, p); return 0; }
