@@ -1,0 +1,199 @@
+/*
+ * fv3.h -- C-ABI of the GB300 FV3 acoustic-substep library (libfv3.so).
+ *
+ * What it computes: the nonhydrostatic acoustic substep of the FV3 dynamical
+ * core on a doubly-periodic tile or on the six-tile gnomonic cubed sphere
+ * (arxiv 2205.04148, Section II: the innermost loop, integrating on
+ * Lagrangian surfaces, with halo exchanges at several execution points;
+ * Section IX-B: riem_solver_c; Section IX-C: fv_tp_2d; Section V-C: halo
+ * exchange with the orientation transform between cube faces).  The paper
+ * gives no equation; the discretisation is the one documented with the
+ * library (readings R1-R13: PPM transport with a monotone limiter, Lin-Rood
+ * splitting, del-4 damping, a semi-implicit tridiagonal column solve, the
+ * contour-integral C-grid pressure gradient).
+ *
+ * Conventions
+ *  - Fields live on the device in the library layout: every member (ensemble
+ *    state) has nt tiles (1 periodic, 6 cube) of n x n cells and nz levels
+ *    with a halo of 3; each plane has `rows` rows of `pitch` elements and
+ *    element (i, j) of the interior sits at (j + 3) * pitch + ox + i (i, j may
+ *    be -3 .. n + 3).  A 3-D field is [tile][level][plane]; the fields of all
+ *    members are concatenated at member offsets.  Query the layout with
+ *    fv3_get_layout, the element count of a field with fv3_field_elems.
+ *  - Staggering (D-grid): u, the x-wind, on y-faces (i in [0,n), j in [0,n]);
+ *    v, the y-wind, on x-faces (i in [0,n], j in [0,n)); w, delp, pt, delz and
+ *    tracers at cell centres.  pt is temperature (K), delp the layer pressure
+ *    thickness (Pa), delz the (negative) layer height thickness (m), k = 0 the
+ *    model top.  Faces on a tile edge are stored by both tiles; the tile with
+ *    the lower index owns them (periodic: faces i = 0, j = 0).
+ *  - Element type: double (FV3_FP64) or float (FV3_FP32, "FP32-bulk": all
+ *    stencils in FP32, the column solve and global sums in FP64), fixed at
+ *    fv3_init_grid.
+ *  - Ownership: the caller allocates and owns the state buffers (device
+ *    memory, base address aligned to 128 bytes) and the streams; the library
+ *    owns the metric terms, halo plans, intermediates, solver scratch and
+ *    CUDA graphs, released by fv3_destroy.
+ *  - Streams: every call is stream-ordered on `stream` (a cudaStream_t; 0 is
+ *    the legacy default stream) and does not synchronise unless stated.
+ *  - Errors: no call aborts.  Every call validates its arguments and returns a
+ *    status; fv3_last_error returns a message for the last failure of a
+ *    context.  Conditions detected by kernels (Courant number >= 1, too many
+ *    tracer subcycles) are latched in a device status word and reported by
+ *    fv3_check_status.
+ */
+#ifndef FV3_H
+#define FV3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fv3_ctx fv3_ctx;
+typedef void* fv3_stream; /* cudaStream_t */
+
+typedef enum {
+  FV3_OK = 0,
+  FV3_ERR_ARG = -1,         /* null pointer or value out of range */
+  FV3_ERR_SHAPE = -2,       /* sizes inconsistent with the context */
+  FV3_ERR_ALIGN = -3,       /* buffer base not 128-byte aligned */
+  FV3_ERR_CUDA = -4,        /* a CUDA call failed (message in fv3_last_error) */
+  FV3_ERR_NONFINITE = -5,   /* non-finite value found */
+  FV3_ERR_CFL = -6,         /* a Courant number reached 1 */
+  FV3_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
+  FV3_ERR_UNSUPPORTED = -8  /* option not built */
+} fv3_status;
+
+enum { FV3_GRID_PERIODIC = 0, FV3_GRID_CUBED = 1 };
+enum { FV3_FP64 = 0, FV3_FP32 = 1 };
+/* field kinds: cell levels, x-face levels, y-face levels, cell interfaces (nz+1) */
+enum { FV3_KIND_CELL = 0, FV3_KIND_XFACE = 1, FV3_KIND_YFACE = 2, FV3_KIND_IFACE = 3 };
+/* fv3_halo_fill field mask bits */
+enum {
+  FV3_HALO_WIND = 1,  /* u, v (D-grid vector pair, rotated across cube edges) */
+  FV3_HALO_W = 2,
+  FV3_HALO_DELP = 4,
+  FV3_HALO_PT = 8,
+  FV3_HALO_DELZ = 16,
+  FV3_HALO_TRACERS = 32
+};
+
+typedef struct {
+  int grid_type;         /* FV3_GRID_PERIODIC or FV3_GRID_CUBED */
+  int npx;               /* cells per tile edge (all members, if member_npx is NULL); >= 8 */
+  int npz;               /* vertical levels; >= 2 */
+  int n_members;         /* independent states advanced together; >= 1 */
+  const int* member_npx; /* host array [n_members] of per-member npx, or NULL */
+  int precision;         /* FV3_FP64 or FV3_FP32 */
+  double dx;             /* periodic grid spacing (m) */
+  double radius;         /* sphere radius (m), cube only */
+  double omega;          /* rotation rate (1/s), cube only */
+} fv3_grid_desc;
+
+typedef struct {
+  void *u, *v, *w, *delp, *pt, *delz; /* device, library layout, all members */
+  void* const* q;                     /* host array of nq device tracer fields */
+  int nq;                             /* 0 .. 16 */
+} fv3_state;
+
+typedef struct {
+  double dt;     /* acoustic substep (s) */
+  int n_split;   /* substeps per remapping step (fv3_run_dyn) */
+  int nord;      /* damping order: 1 (del-4) */
+  int hord;      /* edge reconstruction: 0 monotone PPM */
+  double d4_bg;  /* damping coefficient (0.12) */
+  double a_imp;  /* implicit weight of the column solve (1 = fully implicit) */
+  double dz_min; /* minimum layer thickness (m) */
+  double ptop;   /* model-top pressure (Pa) */
+  double grav, rdgas, cp_air;
+} fv3_params;
+
+typedef struct {
+  int n, nz, ntiles;    /* cells per tile edge, levels, tiles */
+  int pitch, rows, ox;  /* plane geometry (elements) */
+  long long plane;      /* elements per plane */
+  long long offset3;    /* member offset in CELL / XFACE / YFACE fields */
+  long long offseti;    /* member offset in IFACE fields */
+} fv3_layout;
+
+/* Build the grid (metric terms in FP64, Section II), the halo plans (Section
+ * V-C) and all internal buffers.  *out receives the context.  Returns
+ * FV3_ERR_ARG / FV3_ERR_SHAPE for bad descriptors, FV3_ERR_CUDA when device
+ * memory cannot be had. */
+fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* desc, fv3_stream stream);
+
+/* Release every library-owned resource of ctx (NULL is allowed). */
+void fv3_destroy(fv3_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none; a static string if ctx is NULL). */
+const char* fv3_last_error(const fv3_ctx* ctx);
+
+/* Elements (of fv3_elem_size bytes) of one field of `kind`, all members. */
+size_t fv3_field_elems(const fv3_ctx* ctx, int kind);
+size_t fv3_elem_size(const fv3_ctx* ctx);
+
+/* Plane geometry and offsets of member `member`. */
+fv3_status fv3_get_layout(const fv3_ctx* ctx, int member, fv3_layout* out);
+
+/* Copy a dense array of member `member` into (import) or out of (export) a
+ * field in the library layout.  Dense layout [tile][level][nj][ni] with
+ * (ni, nj) = (n, n) cells, (n+1, n) x-faces, (n, n+1) y-faces, levels nz (nz+1
+ * for IFACE).  dense_is_host: the dense array is host memory (copied through
+ * a staging buffer; host exports return after the copy completed);
+ * dense_is_double: dense elements are double (else float). */
+fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, int dense_is_host, int dense_is_double,
+                      int member, fv3_stream stream);
+fv3_status fv3_export(fv3_ctx* ctx, int kind, const void* field, void* dense, int dense_is_host, int dense_is_double,
+                      int member, fv3_stream stream);
+
+/* Fill the halos (strips of 3, owner copies of shared tile-edge faces, cube
+ * corner slots) of the fields selected by `field_mask` (FV3_HALO_*), all
+ * members: Section V-C, on the device. */
+fv3_status fv3_halo_fill(fv3_ctx* ctx, const fv3_state* state, unsigned field_mask, fv3_stream stream);
+
+/* One acoustic substep (Section II): halo fill, c_sw, update_dz_c,
+ * riem_solver_c, p_grad_c, C-grid halo fill, d_sw with fv_tp_2d and del-4
+ * damping.  u, v, w, delp, pt are advanced in place (delz and tracers are
+ * inputs only). */
+fv3_status fv3_acoustic_substep(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream);
+
+/* n_steps remapping steps (Section II): each is params->n_split acoustic
+ * substeps with accumulated mass fluxes and Courant numbers, then tracer
+ * transport (tracer_2d) of the state's nq tracers.  The step is captured once
+ * as a CUDA graph (per state pointers and parameters) and replayed. */
+fv3_status fv3_run_dyn(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int n_steps,
+                       fv3_stream stream);
+
+/* Global mass sum(delp * area) per member in FP64 (Neumaier-compensated, fixed
+ * order).  out_per_member: host array [n_members]; returns after the sum is
+ * on the host. */
+fv3_status fv3_mass_sum(fv3_ctx* ctx, const fv3_state* state, double* out_per_member, fv3_stream stream);
+
+/* Synchronise `stream` and report (then clear) the kernel status word:
+ * FV3_ERR_CFL, FV3_ERR_UNSUPPORTED (tracer subcycles beyond 4) or FV3_OK. */
+fv3_status fv3_check_status(fv3_ctx* ctx, fv3_stream stream);
+
+/* ---- test exports (same conventions) ---- */
+
+/* Dense copy of one FP64 metric term of `member` into host memory: cells
+ * (area, rarea, fA) [nt][n][n]; y-faces (dx, rdx, dyc, rdyc, cosy, siny)
+ * [nt][n+1][n]; x-faces (dy, rdy, dxc, rdxc, cosx, sinx) [nt][n][n+1];
+ * corners (fC, rareac) [nt][n+1][n+1]. */
+fv3_status fv3_get_metric(fv3_ctx* ctx, const char* name, int member, double* dense_host);
+
+/* Run the substep only up to stage `stop_after` (0 halo fill, 1 c_sw, 2
+ * update_dz_c, 3 riem_solver_c, 4 p_grad_c, 5 everything) without advancing
+ * the state, then copy an intermediate of member `member` to host (dense,
+ * double): uc, fx1 (x-faces), vc, fy1 (y-faces), delpc, ptc, wc, delzc
+ * (cells), pef, gz (interfaces). */
+fv3_status fv3_stage(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int stop_after,
+                     fv3_stream stream);
+fv3_status fv3_get_intermediate(fv3_ctx* ctx, const char* name, int member, double* dense_host, fv3_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV3_H */

@@ -1,0 +1,1133 @@
+// fv3_kernels.cu -- sm_103a kernels of one FV3 acoustic substep.
+//
+// arxiv 2205.04148, Section II (the acoustic substep: c_sw, riem_solver_c,
+// p_grad_c, d_sw with halo exchanges between them), Section IX-B
+// (riem_solver_c: semi-implicit tridiagonal column solve), Section IX-C
+// (fv_tp_2d: 2-D mass-conserving flux-form transport), Section V-B (corner and
+// edge specialisations), Section VII-A (I-contiguous layout, horizontal
+// stencils with I on threadIdx.x, vertical solvers with K inside a thread;
+// consecutive statements fused into one kernel with redundant computation of
+// the halo they need).
+//
+// The paper prints no equation; the formulas are the design readings R1-R13
+// (Colella-Woodward PPM with a monotone limiter, Lin-Rood inner/outer
+// splitting, del-4 damping fluxes, Lin 1997 contour pressure gradient, a
+// Chen-et-al.-style semi-implicit column).  Every kernel is templated on the
+// arithmetic type R: double for the FP64 path, float for the FP32-bulk path
+// (whose column solve still runs in double).
+//
+// Horizontal kernels: one CTA = one 2-D block (BX x BY cells) of one tile of
+// one member, looping over a chunk of levels.  The block and its halo of 3
+// live in shared memory; every phase is a 2-D loop over the range it must
+// produce, separated by barriers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fv3_kernels.cuh"
+
+namespace fv3 {
+
+template <typename R>
+__device__ __forceinline__ R qnan();
+template <>
+__device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+template <>
+__device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+
+// ------------------------------------------------------------------------
+// PPM (reading R4)
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R ppm_edge(R qm, R q0, R q1, R qp) {
+  R al = R(7.0 / 12.0) * (q0 + q1) - R(1.0 / 12.0) * (qm + qp);
+  return fmin(fmax(al, fmin(q0, q1)), fmax(q0, q1));
+}
+
+// face value at the face left of q[0] (between q[-s] and q[0]) for Courant
+// number c; the upwind cell is picked first so the warp does one evaluation.
+template <typename R>
+__device__ __forceinline__ R ppm_face(const R* q, int s, R c) {
+  const R* p = (c > R(0)) ? q - s : q;
+  const R qu = p[0];
+  R bl = ppm_edge(p[-2 * s], p[-s], p[0], p[s]) - qu;
+  R br = ppm_edge(p[-s], p[0], p[s], p[2 * s]) - qu;
+  if (bl * br >= R(0)) {
+    bl = R(0);
+    br = R(0);
+  } else if (fabs(bl) > R(2) * fabs(br)) {
+    bl = R(-2) * br;
+  } else if (fabs(br) > R(2) * fabs(bl)) {
+    br = R(-2) * bl;
+  }
+  const R ac = fabs(c);
+  const R x = (c > R(0)) ? br : bl;
+  return qu + (R(1) - ac) * (x - ac * (bl + br));
+}
+
+// ------------------------------------------------------------------------
+// per-tile metric view: element (i, j) at p[j * pitch + i]
+// ------------------------------------------------------------------------
+template <typename R>
+struct TM {
+  const R *area, *rarea, *fA, *dx, *rdx, *dyc, *rdyc, *cosy, *siny, *rsin2y, *dy, *rdy, *dxc, *rdxc, *cosx, *sinx,
+      *rsin2x, *fC, *rareac;
+  int pitch;
+};
+#define MT(name, j, i) __ldg(m.name + (long long)(j) * m.pitch + (i))
+
+template <typename R>
+__device__ __forceinline__ TM<R> tile_metric(const Metric<R>& M, const Geo& g, int t) {
+  const long long o = g.off2 + (long long)t * g.plane + (long long)HALO * g.pitch + g.ox;
+  TM<R> m;
+  m.area = M.area + o; m.rarea = M.rarea + o; m.fA = M.fA + o;
+  m.dx = M.dx + o; m.rdx = M.rdx + o; m.dyc = M.dyc + o; m.rdyc = M.rdyc + o;
+  m.cosy = M.cosy + o; m.siny = M.siny + o; m.rsin2y = M.rsin2y + o;
+  m.dy = M.dy + o; m.rdy = M.rdy + o; m.dxc = M.dxc + o; m.rdxc = M.rdxc + o;
+  m.cosx = M.cosx + o; m.sinx = M.sinx + o; m.rsin2x = M.rsin2x + o;
+  m.fC = M.fC + o; m.rareac = M.rareac + o;
+  m.pitch = g.pitch;
+  return m;
+}
+
+// origin (i = j = 0) of level k of tile t in a [tile][nlev][plane] field
+__device__ __forceinline__ long long fld0(const Geo& g, long long off, int nlev, int t, int k) {
+  return off + ((long long)t * nlev + k) * g.plane + (long long)HALO * g.pitch + g.ox;
+}
+
+// CTA block and its shared-memory frame (halo 3 on every side)
+struct Blk {
+  int x0, x1, y0, y1, SX;
+  __device__ __forceinline__ int L(int i, int j) const { return (j - y0 + 3) * SX + (i - x0 + 3); }
+};
+
+template <typename F>
+__device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
+  for (int j = jlo + (int)threadIdx.y; j < jhi; j += (int)blockDim.y)
+    for (int i = ilo + (int)threadIdx.x; i < ihi; i += (int)blockDim.x) f(i, j);
+}
+
+// Cube corners (reading R3): rewrite the 3x3 missing-quadrant cells of a
+// shared-memory scalar from the block's own strips, turned about the corner:
+// role 0 for sweeps along x (from the W/E strip), 1 along y (S/N strip).
+template <typename R>
+__device__ __forceinline__ void corner_roles(R* Q, const Blk& B, int n, int role) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid >= 36) return;
+  const int c = tid / 9, pa = tid % 3, pb = (tid / 3) % 3;
+  const int ox = (c & 1) ? 1 : -1, oy = (c & 2) ? 1 : -1;
+  const bool here = (ox < 0 ? B.x0 == 0 : B.x1 == n) && (oy < 0 ? B.y0 == 0 : B.y1 == n);
+  if (!here) return;
+  const int i = ox < 0 ? -1 - pa : n + pa;
+  const int j = oy < 0 ? -1 - pb : n + pb;
+  int si, sj;
+  if (role == 0) {
+    si = ox < 0 ? -1 - pb : n + pb;
+    sj = oy < 0 ? pa : n - 1 - pa;
+  } else {
+    si = ox < 0 ? pb : n - 1 - pb;
+    sj = oy < 0 ? -1 - pa : n + pa;
+  }
+  Q[B.L(i, j)] = Q[B.L(si, sj)];
+}
+
+// shared-memory arrays of the transport
+template <typename R>
+struct TS {
+  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP;
+};
+
+// fv_tp_2d (reading R5) + optional delnflux (R6) of the shared-memory scalar
+// Q on the block: fluxes on x-faces [x0, x1] x [y0, y1) -> FXO and y-faces
+// [x0, x1) x [y0, y1] -> FYO.  mfx/mfy: mass fluxes (null: area fluxes).
+// damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
+template <typename R>
+__device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, int n, bool cc, const R* mfx,
+                          const R* mfy, R damp, const R* wdp, R* FXO, R* FYO) {
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  if (cc) corner_roles(Q, B, n, 1);
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
+  });
+  if (damp != R(0))
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.LAP[l] = (Q[l + SX] - Q[l]) * MT(dx, j + 1, i) * MT(rdyc, j + 1, i) -
+                 (Q[l] - Q[l - SX]) * MT(dx, j, i) * MT(rdyc, j, i);
+    });
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * S.RDYd[l];
+  });
+  if (cc) corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
+  __syncthreads();
+  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
+  });
+  if (damp != R(0))
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R lx = (Q[l + 1] - Q[l]) * MT(dy, j, i + 1) * MT(rdxc, j, i + 1) -
+                   (Q[l] - Q[l - 1]) * MT(dy, j, i) * MT(rdxc, j, i);
+      S.LAP[l] = (S.LAP[l] + lx) * MT(rarea, j, i);
+    });
+  __syncthreads();
+  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
+    FXO[l] = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+  });
+  __syncthreads();
+  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * S.RDXd[l];
+  });
+  __syncthreads();
+  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R f = ppm_face(S.QIJ + l, SX, S.CRY[l]);
+    FYO[l] = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+  });
+  if (damp != R(0)) {
+    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * MT(dy, j, i) * MT(rdxc, j, i);
+      if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
+      FXO[l] = FXO[l] + f;
+    });
+    __syncthreads();  // FYO of this thread's faces written above by others
+    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * MT(dx, j, i) * MT(rdyc, j, i);
+      if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
+      FYO[l] = FYO[l] + f;
+    });
+  }
+  __syncthreads();
+}
+
+// Courant numbers and area fluxes (reading R11) into shared memory, plus the
+// reciprocal denominators of the two inner updates.  uc/vc: global, origin of
+// the level.
+template <typename R>
+__device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R>& S, const Blk& B,
+                        const TM<R>& m, const Geo& g, R dt, bool scaled, R fr) {
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const int P = g.pitch;
+  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R ut = (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]) * MT(rsin2x, j, i);
+    S.XFX[l] = dt * ut * MT(dy, j, i) * MT(sinx, j, i);
+    S.CRX[l] = dt * ut * MT(sinx, j, i) * MT(rdxc, j, i);
+  });
+  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R vt = (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]) * MT(rsin2y, j, i);
+    S.YFX[l] = dt * vt * MT(dx, j, i) * MT(siny, j, i);
+    S.CRY[l] = dt * vt * MT(siny, j, i) * MT(rdyc, j, i);
+  });
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+  });
+  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+  });
+  (void)scaled;
+  (void)fr;
+}
+
+// ------------------------------------------------------------------------
+// d_sw (reading R11): one level of a block per loop iteration
+// ------------------------------------------------------------------------
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256) k_d_sw(StepArgs<R> a, int kchunk) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
+  R* sb = reinterpret_cast<R*>(smraw);
+  R *DP = sb, *PT = sb + SA, *W = sb + 2 * SA, *U = sb + 3 * SA, *V = sb + 4 * SA;
+  R *MFX = sb + 5 * SA, *MFY = sb + 6 * SA, *FXO = sb + 7 * SA, *FYO = sb + 8 * SA, *DPN = sb + 9 * SA;
+  R* KE = sb + 10 * SA;
+  TS<R> S;
+  S.CRX = sb + 11 * SA; S.XFX = sb + 12 * SA; S.CRY = sb + 13 * SA; S.YFX = sb + 14 * SA;
+  S.RDXd = sb + 15 * SA; S.RDYd = sb + 16 * SA; S.FY2 = sb + 17 * SA; S.FX2 = sb + 18 * SA;
+  S.QIJ = sb + 19 * SA; S.LAP = sb + 20 * SA;
+  (void)SY;
+
+  const Item it = a.items[blockIdx.x];
+  const Geo g = a.geo[it.m];
+  const int n = g.n, P = g.pitch;
+  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
+  const bool cc = g.cubed && (B.x0 == 0 || B.x1 == n) && (B.y0 == 0 || B.y1 == n);
+  const TM<R> m = tile_metric(a.M, g, it.t);
+  const R dt = (R)a.P.dt;
+  const double dd = a.P.d4_bg * g.da_min;
+  const R damp = (R)(dd * dd);
+  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  for (int k = k0; k < k1; ++k) {
+    const long long o = fld0(g, g.off3, g.nz, it.t, k);
+    const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
+    const R *uc = a.uc + o, *vc = a.vc + o;
+    auto G = [&](int j, int i) { return (long long)j * P + i; };
+    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = G(j, i);
+      DP[l] = dp[q];
+      PT[l] = pt[q];
+      W[l] = w[q];
+    });
+    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+    for2(x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    __syncthreads();
+    courant(uc, vc, V, U, S, B, m, g, dt, false, R(1));
+    if (a.status) {  // Courant-number guard on the block's own faces
+      bool bad = false;
+      for2(x0, x1, y0, y1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        bad |= !(fabs(S.CRX[l]) < R(1)) || !(fabs(S.CRY[l]) < R(1));
+      });
+      if (bad) atomicOr(a.status, ST_CFL);
+    }
+    // mass
+    transport(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY);
+    R* dpo = a.delp_o + o;
+    for2(x0, x1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
+      DPN[l] = d;
+      dpo[G(j, i)] = d;
+    });
+    // pt and w with the mass fluxes and mass-weighted damping
+    for (int fld = 0; fld < 2; ++fld) {
+      R* Q = fld == 0 ? PT : W;
+      R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
+      transport(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+      for2(x0, x1, y0, y1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        out[G(j, i)] =
+            (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) / DPN[l];
+      });
+    }
+    __syncthreads();
+    // cell absolute vorticity (into PT)
+    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
+               V[l] * MT(dy, j, i)) * MT(rarea, j, i) + MT(fA, j, i);
+    });
+    transport(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, FXO, FYO);
+    // kinetic energy at corners from upwind-PPM corner winds
+    for2(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
+      const R va = R(0.5) * (vc[G(j, i - 1)] + vc[G(j, i)]);
+      const R cu = dt * ua * (ua > R(0) ? MT(rdx, j, i - 1) : MT(rdx, j, i));
+      const R cv = dt * va * (va > R(0) ? MT(rdy, j - 1, i) : MT(rdy, j, i));
+      const R ub = ppm_face(U + l, 1, cu);
+      const R vb = ppm_face(V + l, SX, cv);
+      KE[l] = R(0.5) * dt * (ub * ua + vb * va);
+    });
+    __syncthreads();
+    R *uo = a.u_o + o, *vo = a.v_o + o;
+    for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+      const int l = B.L(i, j);
+      uo[G(j, i)] = U[l] + (FYO[l] + KE[l] - KE[l + 1]) * MT(rdx, j, i);
+    });
+    for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      vo[G(j, i)] = V[l] + (-FXO[l] + KE[l] - KE[l + SX]) * MT(rdy, j, i);
+    });
+    if (a.amfx) {
+      for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        const long long q = o + G(j, i);
+        a.amfx[q] += MFX[l];
+        a.acrx[q] += S.CRX[l];
+        a.axfx[q] += S.XFX[l];
+      });
+      for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+        const int l = B.L(i, j);
+        const long long q = o + G(j, i);
+        a.amfy[q] += MFY[l];
+        a.acry[q] += S.CRY[l];
+        a.ayfx[q] += S.YFX[l];
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------
+// c_sw (reading R7)
+// ------------------------------------------------------------------------
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
+  R* sb = reinterpret_cast<R*>(smraw);
+  R *U = sb, *V = sb + SA, *DP = sb + 2 * SA, *PT = sb + 3 * SA, *W = sb + 4 * SA;
+  R *UC0 = sb + 5 * SA, *VC0 = sb + 6 * SA, *UT = sb + 7 * SA, *VT = sb + 8 * SA, *KE = sb + 9 * SA;
+  R *VO = sb + 10 * SA, *FX1 = sb + 11 * SA, *FY1 = sb + 12 * SA;
+  (void)SY;
+  const Item it = a.items[blockIdx.x];
+  const Geo g = a.geo[it.m];
+  const int n = g.n, P = g.pitch;
+  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  const TM<R> m = tile_metric(a.M, g, it.t);
+  const R dt2 = R(0.5 * a.P.dt);
+  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  auto G = [&](int j, int i) { return (long long)j * P + i; };
+  for (int k = k0; k < k1; ++k) {
+    const long long o = fld0(g, g.off3, g.nz, it.t, k);
+    const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
+    for2(x0 - 2, x1 + 2, y0 - 1, y1 + 2, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+    for2(x0 - 1, x1 + 2, y0 - 2, y1 + 2, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = G(j, i);
+      DP[l] = dp[q];
+      PT[l] = pt[q];
+      W[l] = w[q];
+    });
+    __syncthreads();
+    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R c0 = R(0.25) * (U[l - 1] + U[l] + U[l - 1 + SX] + U[l + SX]);
+      UC0[l] = c0;
+      UT[l] = (c0 - MT(cosx, j, i) * V[l]) * MT(rsin2x, j, i);
+    });
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R c0 = R(0.25) * (V[l - SX] + V[l - SX + 1] + V[l] + V[l + 1]);
+      VC0[l] = c0;
+      VT[l] = (c0 - MT(cosy, j, i) * U[l]) * MT(rsin2y, j, i);
+    });
+    __syncthreads();
+    R *fx1 = a.fx1 + o, *fy1 = a.fy1 + o;
+    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R f = dt2 * UT[l] * MT(dy, j, i) * MT(sinx, j, i);
+      FX1[l] = f;
+      if (i < x1 || x1 == n) fx1[G(j, i)] = f;
+    });
+    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R f = dt2 * VT[l] * MT(dx, j, i) * MT(siny, j, i);
+      FY1[l] = f;
+      if (j < y1 || y1 == n) fy1[G(j, i)] = f;
+    });
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R ua = R(0.5) * (UT[l] + UT[l + 1]);
+      const R va = R(0.5) * (VT[l] + VT[l + SX]);
+      KE[l] = R(0.5) * dt2 * (ua * ua + va * va);
+    });
+    for2(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R ts = UC0[l - SX] * MT(dxc, j - 1, i);
+      R te = VC0[l] * MT(dyc, j, i);
+      const R tn = UC0[l] * MT(dxc, j, i);
+      R tw = VC0[l - 1] * MT(dyc, j, i - 1);
+      if (g.cubed && (i == 0 || i == n) && (j == 0 || j == n)) {  // cube corner: triangle
+        if (i == 0) tw = R(0);
+        else te = R(0);
+      }
+      VO[l] = (ts + te - tn - tw) * MT(rareac, j, i) + MT(fC, j, i);
+    });
+    __syncthreads();
+    R *dpc = a.delpc + o, *ptc = a.ptc + o, *wcc = a.wc + o;
+    for2(x0, x1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const int up[4] = {FX1[l] > R(0) ? l - 1 : l, FX1[l + 1] > R(0) ? l : l + 1, FY1[l] > R(0) ? l - SX : l,
+                         FY1[l + SX] > R(0) ? l : l + SX};
+      const R F[4] = {FX1[l], FX1[l + 1], FY1[l], FY1[l + SX]};
+      R fm[4], fp[4], fw[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        fm[f] = F[f] * DP[up[f]];
+        fp[f] = fm[f] * PT[up[f]];
+        fw[f] = fm[f] * W[up[f]];
+      }
+      const R ra = MT(rarea, j, i);
+      const R d = DP[l] + (fm[0] - fm[1] + fm[2] - fm[3]) * ra;
+      dpc[G(j, i)] = d;
+      ptc[G(j, i)] = (PT[l] * DP[l] + (fp[0] - fp[1] + fp[2] - fp[3]) * ra) / d;
+      wcc[G(j, i)] = (W[l] * DP[l] + (fw[0] - fw[1] + fw[2] - fw[3]) * ra) / d;
+    });
+    R *uco = a.uc + o, *vco = a.vc + o;
+    for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      uco[G(j, i)] = UC0[l] + dt2 * R(0.5) * (VO[l] + VO[l + SX]) * V[l] + (KE[l - 1] - KE[l]) * MT(rdxc, j, i);
+    });
+    for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+      const int l = B.L(i, j);
+      vco[G(j, i)] = VC0[l] - dt2 * R(0.5) * (VO[l] + VO[l + 1]) * U[l] + (KE[l - SX] - KE[l]) * MT(rdyc, j, i);
+    });
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------
+// update_dz_c (reading R8): blocks of columns marching up from the surface,
+// the interface geopotential of the block and its ring exchanged in shared
+// memory level by level.  Block: (BXc + 2) x (BYc + 2) threads.
+// ------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int BYc) {
+  __shared__ R GZ[256];
+  const Item it = a.items[blockIdx.x];
+  const Geo g = a.geo[it.m];
+  const int n = g.n, P = g.pitch, nz = g.nz;
+  const int x0 = it.x0, y0 = it.y0, x1 = min(x0 + BXc, n), y1 = min(y0 + BYc, n);
+  const int tx = threadIdx.x, ty = threadIdx.y, TXW = blockDim.x;
+  const int i = x0 - 1 + tx, j = y0 - 1 + ty;
+  const bool ring = (i == x0 - 1 || i == x1) , ringy = (j == y0 - 1 || j == y1);
+  const bool valid = i >= x0 - 1 && i <= x1 && j >= y0 - 1 && j <= y1 && !(ring && ringy);
+  const bool inner = i >= x0 && i < x1 && j >= y0 && j < y1;
+  const TM<R> m = tile_metric(a.M, g, it.t);
+  const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min;
+  const long long q = (long long)j * P + i;
+  R gzr = R(0), gzn_below = R(0);
+  const int l = ty * TXW + tx;
+  for (int K = nz - 1; K >= 0; --K) {
+    const long long o = fld0(g, g.off3, nz, it.t, K);
+    if (valid) {
+      gzr = gzr - grav * a.delz[o + q];
+      GZ[l] = gzr;
+    }
+    __syncthreads();
+    if (inner) {
+      const long long oa = fld0(g, g.off3, nz, it.t, K > 0 ? K - 1 : 0);
+      const R* fxa = a.fx1 + oa;
+      const R* fxb = a.fx1 + o;
+      const R* fya = a.fy1 + oa;
+      const R* fyb = a.fy1 + o;
+      const long long fq[4] = {q, q + 1, q, q + P};
+      const int lo[4] = {l - 1, l, l - TXW, l};
+      const int hi[4] = {l, l + 1, l, l + TXW};
+      R F[4], Gf[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const R A = f < 2 ? fxa[fq[f]] : fya[fq[f]];
+        const R Bv = f < 2 ? fxb[fq[f]] : fyb[fq[f]];
+        F[f] = K == 0 ? Bv : R(0.5) * (A + Bv);
+        Gf[f] = F[f] * (F[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
+      }
+      const R ar = MT(area, j, i);
+      const R gzn = (GZ[l] * ar + Gf[0] - Gf[1] + Gf[2] - Gf[3]) / (ar + F[0] - F[1] + F[2] - F[3]);
+      a.delzc[o + q] = fmin((gzn_below - gzn) / grav, -dzmin);
+      gzn_below = gzn;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------
+// riem_solver_c (Section IX-B, reading R9): one thread per column, FP64 in
+// both precision modes.  Top-down: interface pressure, gas-law pressure and
+// its perturbation, coefficients and the forward Thomas sweep into scratch;
+// bottom-up: back-substitution, new thickness, perturbation pressure, pef and
+// gz.  Scratch layout [5][nz][ncol], coalesced across the warp along i.
+// ------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* rows) {
+  const RowItem r = rows[blockIdx.y];
+  const Geo g = a.geo[r.m];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int nz = g.nz;
+  const long long col = g.colbase + ((long long)r.t * g.n + r.j) * g.n + i;
+  const long long NC = a.ncol;
+  double* s_cp = a.scratch;
+  double* s_dp = a.scratch + (long long)nz * NC;
+  double* s_C = a.scratch + 2LL * nz * NC;
+  double* s_pp = a.scratch + 3LL * nz * NC;
+  double* s_pe = a.scratch + 4LL * nz * NC;
+  const double dt = 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
+  const double kappa = a.P.rdgas / a.P.cp_air, gama = 1.0 / (1.0 - kappa);
+  const long long q = (long long)r.j * g.pitch + i;
+  double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    const long long o = fld0(g, g.off3, nz, r.t, k) + q;
+    const double dpk = (double)a.delpc[o], ptk = (double)a.ptc[o], wck = (double)a.wc[o], dzk = (double)a.delzc[o];
+    const double pen = pe + dpk;
+    const double p = -dpk * rd * ptk / (grav * dzk);
+    const double ph = dpk / log(pen / pe);
+    const double pp = p - ph;
+    const double C = aimp * dt * gama * p / (-dzk);
+    const double mm = k == 0 ? 0.5 * dpk / grav : 0.5 * (dpp + dpk) / grav;
+    const double wn = k == 0 ? wck : 0.5 * (wcp + wck);
+    const double la = -Cp;                    // lower (layer above the interface)
+    const double di = mm / dt + Cp + C;       // diagonal
+    const double up = k < nz - 1 ? -C : 0.0;  // upper
+    const double rhs = mm / dt * wn + pp - ppp;
+    double cpk, dpt;
+    if (k == 0) {
+      cpk = up / di;
+      dpt = rhs / di;
+    } else {
+      const double den = di - la * cpp;
+      cpk = up / den;
+      dpt = (rhs - la * dpv) / den;
+    }
+    const long long sidx = (long long)k * NC + col;
+    s_cp[sidx] = cpk;
+    s_dp[sidx] = dpt;
+    s_C[sidx] = C;
+    s_pp[sidx] = pp;
+    s_pe[sidx] = pe;
+    pe = pen;
+    dpp = dpk;
+    wcp = wck;
+    Cp = C;
+    ppp = pp;
+    cpp = cpk;
+    dpv = dpt;
+  }
+  // bottom-up
+  const double pe_bot = pe;
+  double Wn = 0.0, gzv = 0.0, ppn_below = 0.0;
+  {
+    const long long ob = fld0(g, g.offi, nz + 1, r.t, nz) + q;
+    a.gz[ob] = R(0);
+  }
+  for (int k = nz - 1; k >= 0; --k) {
+    const long long sidx = (long long)k * NC + col;
+    const double Wk = s_dp[sidx] - s_cp[sidx] * Wn;
+    const long long o = fld0(g, g.off3, nz, r.t, k) + q;
+    const double dzk = (double)a.delzc[o];
+    const double dzn = dzk + dt * (Wn - Wk);
+    const double ppn = s_pp[sidx] + s_C[sidx] * (Wn - Wk) / aimp;
+    gzv = gzv - grav * dzn;
+    const long long oi = fld0(g, g.offi, nz + 1, r.t, k) + q;
+    const long long oib = fld0(g, g.offi, nz + 1, r.t, k + 1) + q;
+    a.gz[oi] = (R)gzv;
+    // pef of the interface below layer k
+    double pef;
+    if (k == nz - 1) pef = pe_bot + ppn;
+    else pef = (k + 1 < nz ? 0.0 : 0.0) + s_pe[(long long)(k + 1) * NC + col] + 0.5 * (ppn + ppn_below);
+    a.pef[oib] = (R)pef;
+    ppn_below = ppn;
+    Wn = Wk;
+  }
+  a.pef[fld0(g, g.offi, nz + 1, r.t, 0) + q] = (R)a.P.ptop;
+}
+
+// ------------------------------------------------------------------------
+// p_grad_c (reading R10): one thread per (i, j) updates the x-face and the
+// y-face at (i, j).  Plane list entries (m, t, k).
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R pgrad(R gA0, R gA1, R gB0, R gB1, R pA0, R pA1, R pB0, R pB1) {
+  return ((gA1 - gB0) * (pB1 - pA0) + (gA0 - gB1) * (pA1 - pB0)) / (pA1 - pA0 + pB1 - pB0);
+}
+
+template <typename R>
+__global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = a.geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = g.n;
+  if (i > n || j > n) return;
+  const int t = pl.y, k = pl.z;
+  const TM<R> m = tile_metric(a.M, g, t);
+  const R dt2 = R(0.5 * a.P.dt);
+  const long long o = fld0(g, g.off3, g.nz, t, k);
+  const R* p0 = a.pef + fld0(g, g.offi, g.nz + 1, t, k);
+  const R* p1 = a.pef + fld0(g, g.offi, g.nz + 1, t, k + 1);
+  const R* z0 = a.gz + fld0(g, g.offi, g.nz + 1, t, k);
+  const R* z1 = a.gz + fld0(g, g.offi, g.nz + 1, t, k + 1);
+  const long long B = (long long)j * g.pitch + i;
+  if (j < n) {
+    const long long A = B - 1;
+    a.uc[o + B] += dt2 * MT(rdxc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]);
+  }
+  if (i < n) {
+    const long long A = B - g.pitch;
+    a.vc[o + B] += dt2 * MT(rdyc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]);
+  }
+}
+
+// ------------------------------------------------------------------------
+// halo fill (Section V-C): gather over the resolved plan
+// ------------------------------------------------------------------------
+template <typename R>
+__global__ void k_halo(const HaloBatch b, const Geo* geo) {
+  const HaloField& f = b.f[blockIdx.z];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (e >= f.count || k >= f.nlev) return;
+  const HaloEntry E = f.ent[e];
+  const Geo& g = geo[E.m];
+  const long long mo = f.iface ? g.offi : g.off3;
+  R* dst = (E.flags & 1) ? (R*)f.ya : (R*)f.xa;
+  const R* src = (E.flags & 2) ? (const R*)f.ya : (const R*)f.xa;
+  const long long d = mo + ((long long)E.dt * f.nlev + k) * g.plane + E.dst;
+  R v;
+  if (E.sign == 0) {
+    v = qnan<R>();
+  } else {
+    const R s = src[mo + ((long long)E.st * f.nlev + k) * g.plane + E.src];
+    v = E.sign > 0 ? s : -s;
+  }
+  dst[d] = v;
+}
+
+// ------------------------------------------------------------------------
+// tracer_2d subcycle (reading R12)
+// ------------------------------------------------------------------------
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256) k_tracer(TracerArgs<R> a, int kchunk) {
+  if (a.it >= *a.nsplt) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int SX = BX + 7, SA = SX * (BY + 7);
+  R* sb = reinterpret_cast<R*>(smraw);
+  R *Q = sb, *MFX = sb + SA, *MFY = sb + 2 * SA, *FXO = sb + 3 * SA, *FYO = sb + 4 * SA, *D0 = sb + 5 * SA,
+    *D1 = sb + 6 * SA;
+  TS<R> S;
+  S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
+  S.RDXd = sb + 11 * SA; S.RDYd = sb + 12 * SA; S.FY2 = sb + 13 * SA; S.FX2 = sb + 14 * SA;
+  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA;
+  const Item it = a.items[blockIdx.x];
+  const Geo g = a.geo[it.m];
+  const int n = g.n, P = g.pitch;
+  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
+  const TM<R> m = tile_metric(a.M, g, it.t);
+  const R fr = R(1) / R(*a.nsplt);
+  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  auto G = [&](int j, int i) { return (long long)j * P + i; };
+  for (int k = k0; k < k1; ++k) {
+    const long long o = fld0(g, g.off3, g.nz, it.t, k);
+    for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = o + G(j, i);
+      S.CRX[l] = a.acrx[q] * fr;
+      S.XFX[l] = a.axfx[q] * fr;
+      MFX[l] = a.amfx[q] * fr;
+    });
+    for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = o + G(j, i);
+      S.CRY[l] = a.acry[q] * fr;
+      S.YFX[l] = a.ayfx[q] * fr;
+      MFY[l] = a.amfy[q] * fr;
+    });
+    __syncthreads();
+    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+    });
+    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+    });
+    for2(x0, x1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R d0 = a.dp0[o + G(j, i)];
+      const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
+      D0[l] = d0;
+      D1[l] = d1;
+      a.dp1[o + G(j, i)] = d1;
+    });
+    for (int tq = 0; tq < a.nq; ++tq) {
+      const R* q = a.q[tq] + o;
+      __syncthreads();
+      for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
+      transport(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+      R* qo = a.q_o[tq] + o;
+      for2(x0, x1, y0, y1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) / D1[l];
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// largest |accumulated Courant number| over interior faces -> subcycles
+template <typename R>
+__global__ void k_cmax(const Geo* geo, const int4* planes, const R* acrx, const R* acry, unsigned* cmax_bits) {
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  float c = 0.f;
+  if (i < g.n && j < g.n) {
+    const long long o = fld0(g, g.off3, g.nz, pl.y, pl.z) + (long long)j * g.pitch + i;
+    c = (float)fmax(fabs((double)acrx[o]), fabs((double)acry[o]));
+  }
+  for (int s = 16; s > 0; s >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, s));
+  if ((threadIdx.x & 31) == 0) atomicMax(cmax_bits, __float_as_uint(c));
+}
+
+template <typename R>
+__global__ void k_nsplt(const unsigned* cmax_bits, int* nsplt, int nmax, unsigned* status, const R* dummy) {
+  (void)dummy;
+  const float c = __uint_as_float(*cmax_bits);
+  int s = (int)ceilf(c);
+  if (s < 1) s = 1;
+  if (s > nmax) {
+    atomicOr(status, ST_NSPLT);
+    s = nmax;
+  }
+  *nsplt = s;
+}
+
+// copy [0, n] x [0, n] of every level plane (cells and both face kinds) from
+// src to dst; gated on the subcycle count when gate != null
+template <typename R>
+__global__ void k_copy_planes(const Geo* geo, const int4* planes, const CopyArgs<R> a, const int* gate, int it) {
+  if (gate && it >= *gate) return;
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.n || j > g.n) return;
+  const long long o = fld0(g, g.off3, g.nz, pl.y, pl.z) + (long long)j * g.pitch + i;
+  for (int f = 0; f < a.nf; ++f) a.dst[f][o] = a.src[f][o];
+}
+
+// ------------------------------------------------------------------------
+// global mass (reading R13): sum of delp * area per member, FP64,
+// Neumaier-compensated, fixed order (block partials, then one thread).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void neu_add(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x;
+  else c += (x - t) + s;
+  s = t;
+}
+
+template <typename R>
+__global__ void k_mass_partial(const Geo* geo, const int4* planes, const R* delp, const double* area,
+                               double* partial) {
+  const int4 pl = planes[blockIdx.x];
+  const Geo g = geo[pl.x];
+  __shared__ double ss[256], sc[256];
+  double s = 0.0, c = 0.0;
+  const long long o = fld0(g, g.off3, g.nz, pl.y, pl.z);
+  const long long oa = g.off2 + (long long)pl.y * g.plane + (long long)HALO * g.pitch + g.ox;
+  for (int e = threadIdx.x; e < g.n * g.n; e += blockDim.x) {
+    const int j = e / g.n, i = e % g.n;
+    const long long q = (long long)j * g.pitch + i;
+    neu_add(s, c, (double)delp[o + q] * area[oa + q]);
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, Cc = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      neu_add(S, Cc, ss[t]);
+      Cc += sc[t];
+    }
+    partial[2 * blockIdx.x] = S;
+    partial[2 * blockIdx.x + 1] = Cc;
+  }
+}
+
+__global__ void k_mass_final(const double* partial, const int* first, int nmem, double* out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  double S = 0.0, Cc = 0.0;
+  for (int b = first[m]; b < first[m + 1]; ++b) {
+    neu_add(S, Cc, partial[2 * b]);
+    Cc += partial[2 * b + 1];
+  }
+  out[m] = S + Cc;
+}
+
+// ------------------------------------------------------------------------
+// dense <-> padded layout (argument marshalling for import / export)
+// kind: 0 cells (n x n), 1 x-faces (n x n+1), 2 y-faces (n+1 x n), 3 corners
+// (n+1 x n+1); iface: 0 level fields, 1 interface fields, 2 metric planes
+// ------------------------------------------------------------------------
+template <typename R, typename D>
+__global__ void k_pack(const Geo* geo, int mem, int kind, int nlev, int iface, R* padded, D* dense, int dir) {
+  const Geo g = geo[mem];
+  const int n = g.n, ni = n + (kind == 1 || kind == 3), nj = n + (kind == 2 || kind == 3);
+  const long long total = (long long)g.nt * nlev * nj * ni;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ni);
+    const int j = (int)((e / ni) % nj);
+    const long long tk = e / ((long long)ni * nj);
+    const int k = (int)(tk % nlev), t = (int)(tk / nlev);
+    const long long base = iface == 1 ? g.offi : iface == 2 ? g.off2 : g.off3;
+    const long long o = fld0(g, base, nlev, t, k) + (long long)j * g.pitch + i;
+    if (dir == 0) padded[o] = (R)dense[e];
+    else dense[e] = (D)padded[o];
+  }
+}
+
+
+// ------------------------------------------------------------------------
+// orchestration: the launches of one substep / tracer step / utilities
+// ------------------------------------------------------------------------
+template <typename R>
+Metric<R> metric_of(const Ctx& c);
+template <>
+Metric<double> metric_of<double>(const Ctx& c) { return c.Md; }
+template <>
+Metric<float> metric_of<float>(const Ctx& c) { return c.Mf; }
+
+template <typename K>
+static void set_smem(K kern, size_t bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static size_t blk_smem(const Ctx& c, int arrays) {
+  return (size_t)arrays * (c.BX + 7) * (c.BY + 7) * c.esize;
+}
+
+void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStream_t st) {
+  for (size_t base = 0; base < fields.size(); base += MAX_HALO_FIELDS) {
+    HaloBatch b{};
+    int nf = 0, maxc = 0, maxl = 0;
+    for (size_t i = base; i < fields.size() && nf < MAX_HALO_FIELDS; ++i, ++nf) {
+      b.f[nf] = fields[i];
+      maxc = std::max(maxc, fields[i].count);
+      maxl = std::max(maxl, fields[i].nlev);
+    }
+    if (maxc == 0) continue;
+    dim3 grid((maxc + 255) / 256, maxl, nf);
+    if (c.prec == 0) k_halo<double><<<grid, 256, 0, st>>>(b, c.geo_d);
+    else k_halo<float><<<grid, 256, 0, st>>>(b, c.geo_d);
+  }
+}
+
+static HaloField hf(const Ctx& c, int kind, void* xa, void* ya, int nlev, int iface) {
+  HaloField f{};
+  f.xa = xa;
+  f.ya = ya;
+  f.ent = c.plan_d[kind];
+  f.count = c.plan_n[kind];
+  f.nlev = nlev;
+  f.iface = iface;
+  return f;
+}
+
+void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st) {
+  std::vector<HaloField> F;
+  F.push_back(hf(c, K_DGRID, s.v, s.u, c.nz, 0));
+  F.push_back(hf(c, K_CELL3, s.w, nullptr, c.nz, 0));
+  F.push_back(hf(c, K_CELL3, s.delp, nullptr, c.nz, 0));
+  F.push_back(hf(c, K_CELL3, s.pt, nullptr, c.nz, 0));
+  F.push_back(hf(c, K_CELL3, s.delz, nullptr, c.nz, 0));
+  enqueue_halo_fields(c, F, st);
+}
+
+template <typename R>
+static void substep_t(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool acc,
+                      cudaStream_t st, int stop_after) {
+  StepArgs<R> a{};
+  a.geo = c.geo_d;
+  a.items = c.items_hz;
+  a.M = metric_of<R>(c);
+  a.P = P;
+  a.u = (const R*)in.u; a.v = (const R*)in.v; a.w = (const R*)in.w;
+  a.delp = (const R*)in.delp; a.pt = (const R*)in.pt; a.delz = (const R*)in.delz;
+  a.u_o = (R*)out.u; a.v_o = (R*)out.v; a.w_o = (R*)out.w; a.delp_o = (R*)out.delp; a.pt_o = (R*)out.pt;
+  a.uc = (R*)c.uc; a.vc = (R*)c.vc; a.delpc = (R*)c.delpc; a.ptc = (R*)c.ptc; a.wc = (R*)c.wc;
+  a.delzc = (R*)c.delzc; a.fx1 = (R*)c.fx1; a.fy1 = (R*)c.fy1; a.pef = (R*)c.pef; a.gz = (R*)c.gz;
+  a.scratch = c.scratch;
+  a.ncol = c.ncol;
+  if (acc) {
+    a.amfx = (R*)c.amfx; a.amfy = (R*)c.amfy; a.acrx = (R*)c.acrx; a.acry = (R*)c.acry;
+    a.axfx = (R*)c.axfx; a.ayfx = (R*)c.ayfx;
+  }
+  a.status = c.status;
+  const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
+
+  enqueue_halo_prognostics(c, in, st);
+  if (stop_after <= 0) return;
+  // c_sw
+  {
+    const size_t sm = blk_smem(c, 13);
+    if (c.BX == 32 && c.BY == 8) {
+      set_smem(k_c_sw<R, 32, 8>, sm);
+      k_c_sw<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    } else {
+      set_smem(k_c_sw<R, 32, 16>, sm);
+      k_c_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    }
+  }
+  if (stop_after <= 1) return;
+  // update_dz_c
+  {
+    StepArgs<R> b = a;
+    b.items = c.items_dz;
+    k_update_dz_c<R><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+  }
+  if (stop_after <= 2) return;
+  // riem_solver_c
+  k_riem_c<R><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
+  if (stop_after <= 3) return;
+  // pef, gz one ring into the halo
+  {
+    std::vector<HaloField> F;
+    F.push_back(hf(c, K_CELL1, c.pef, nullptr, c.nz + 1, 1));
+    F.push_back(hf(c, K_CELL1, c.gz, nullptr, c.nz + 1, 1));
+    enqueue_halo_fields(c, F, st);
+  }
+  // p_grad_c
+  {
+    const int nb = (c.max_n + 1 + 15) / 16;
+    k_p_grad_c<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+  }
+  if (stop_after <= 4) return;
+  // C-grid winds into the halo
+  {
+    std::vector<HaloField> F;
+    F.push_back(hf(c, K_CGRID, c.uc, c.vc, c.nz, 0));
+    enqueue_halo_fields(c, F, st);
+  }
+  // d_sw
+  {
+    const size_t sm = blk_smem(c, 21);
+    if (c.BX == 32 && c.BY == 8) {
+      set_smem(k_d_sw<R, 32, 8>, sm);
+      k_d_sw<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    } else {
+      set_smem(k_d_sw<R, 32, 16>, sm);
+      k_d_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    }
+  }
+}
+
+void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                     cudaStream_t st, int stop_after) {
+  if (c.prec == 0) substep_t<double>(c, in, out, P, accumulate, st, stop_after);
+  else substep_t<float>(c, in, out, P, accumulate, st, stop_after);
+}
+
+template <typename R>
+static void copy_planes_t(Ctx& c, const std::vector<std::pair<void*, const void*>>& pairs, const int* gate, int it,
+                          cudaStream_t st) {
+  CopyArgs<R> a{};
+  a.nf = (int)pairs.size();
+  for (int f = 0; f < a.nf; ++f) {
+    a.dst[f] = (R*)pairs[f].first;
+    a.src[f] = (const R*)pairs[f].second;
+  }
+  const int nb = c.max_n + 1;
+  k_copy_planes<R><<<dim3((nb + 31) / 32, (nb + 7) / 8, c.n_planes), dim3(32, 8), 0, st>>>(c.geo_d, c.planes, a,
+                                                                                             gate, it);
+}
+
+static void copy_planes(Ctx& c, const std::vector<std::pair<void*, const void*>>& pairs, const int* gate, int it,
+                        cudaStream_t st) {
+  if (c.prec == 0) copy_planes_t<double>(c, pairs, gate, it, st);
+  else copy_planes_t<float>(c, pairs, gate, it, st);
+}
+
+void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cudaStream_t st) {
+  copy_planes(c, {{dst.u, src.u}, {dst.v, src.v}, {dst.w, src.w}, {dst.delp, src.delp}, {dst.pt, src.pt}}, nullptr,
+              0, st);
+}
+
+void enqueue_zero_acc(Ctx& c, cudaStream_t st) {
+  const size_t b = c.elems3 * c.esize;
+  void* acc[6] = {c.amfx, c.amfy, c.acrx, c.acry, c.axfx, c.ayfx};
+  for (void* p : acc) cudaMemsetAsync(p, 0, b, st);
+}
+
+void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st) {
+  copy_planes(c, {{c.dpstart, delp}}, nullptr, 0, st);
+}
+
+template <typename R>
+static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
+  std::vector<HaloField> F;
+  F.push_back(hf(c, K_CGRID, c.amfx, c.amfy, c.nz, 0));
+  F.push_back(hf(c, K_CGRID, c.acrx, c.acry, c.nz, 0));
+  F.push_back(hf(c, K_CGRID, c.axfx, c.ayfx, c.nz, 0));
+  enqueue_halo_fields(c, F, st);
+  cudaMemsetAsync(c.cmax, 0, sizeof(unsigned), st);
+  {
+    const int nb = (c.max_n + 15) / 16;
+    k_cmax<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(c.geo_d, c.planes, (const R*)c.acrx,
+                                                                 (const R*)c.acry, c.cmax);
+    k_nsplt<R><<<1, 1, 0, st>>>(c.cmax, c.nsplt, NSPLT_MAX, c.status, (const R*)nullptr);
+  }
+  copy_planes(c, {{c.dp0, c.dpstart}}, nullptr, 0, st);
+  TracerArgs<R> a{};
+  a.geo = c.geo_d;
+  a.items = c.items_hz;
+  a.M = metric_of<R>(c);
+  a.nq = s.nq;
+  a.nsplt = c.nsplt;
+  for (int q = 0; q < s.nq; ++q) {
+    a.q[q] = (const R*)s.q[q];
+    a.q_o[q] = (R*)c.qtmp[q];
+  }
+  a.acrx = (const R*)c.acrx; a.acry = (const R*)c.acry; a.axfx = (const R*)c.axfx; a.ayfx = (const R*)c.ayfx;
+  a.amfx = (const R*)c.amfx; a.amfy = (const R*)c.amfy;
+  a.dp0 = (const R*)c.dp0;
+  a.dp1 = (R*)c.dp1;
+  const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
+  const size_t sm = blk_smem(c, 17);
+  for (int it = 0; it < NSPLT_MAX; ++it) {
+    std::vector<HaloField> Q;
+    for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
+    enqueue_halo_fields(c, Q, st);
+    a.it = it;
+    if (c.BX == 32 && c.BY == 8) {
+      set_smem(k_tracer<R, 32, 8>, sm);
+      k_tracer<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    } else {
+      set_smem(k_tracer<R, 32, 16>, sm);
+      k_tracer<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
+    }
+    std::vector<std::pair<void*, const void*>> pairs;
+    for (int q = 0; q < s.nq; ++q) pairs.push_back({s.q[q], c.qtmp[q]});
+    pairs.push_back({c.dp0, c.dp1});
+    copy_planes(c, pairs, c.nsplt, it, st);
+  }
+}
+
+void enqueue_tracers(Ctx& c, const StateView& s, cudaStream_t st) {
+  if (s.nq <= 0) return;
+  if (c.prec == 0) tracers_t<double>(c, s, st);
+  else tracers_t<float>(c, s, st);
+}
+
+void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st) {
+  if (c.prec == 0)
+    k_mass_partial<double><<<c.n_planes, 256, 0, st>>>(c.geo_d, c.planes, (const double*)delp, c.Md.area,
+                                                       c.mass_part);
+  else
+    k_mass_partial<float><<<c.n_planes, 256, 0, st>>>(c.geo_d, c.planes, (const float*)delp, c.Md.area,
+                                                      c.mass_part);
+  k_mass_final<<<(c.nmem + 63) / 64, 64, 0, st>>>(c.mass_part, c.mass_first, c.nmem, c.mass_out);
+}
+
+void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
+                  int dir, cudaStream_t st) {
+  const int blocks = 1024;
+  if (c.prec == 0 || iface == 2) {
+    if (dense_is_double)
+      k_pack<double, double><<<blocks, 256, 0, st>>>(c.geo_d, member, kind, nlev, iface, (double*)padded,
+                                                     (double*)dense, dir);
+    else
+      k_pack<double, float><<<blocks, 256, 0, st>>>(c.geo_d, member, kind, nlev, iface, (double*)padded,
+                                                    (float*)dense, dir);
+  } else {
+    if (dense_is_double)
+      k_pack<float, double><<<blocks, 256, 0, st>>>(c.geo_d, member, kind, nlev, iface, (float*)padded,
+                                                    (double*)dense, dir);
+    else
+      k_pack<float, float><<<blocks, 256, 0, st>>>(c.geo_d, member, kind, nlev, iface, (float*)padded,
+                                                   (float*)dense, dir);
+  }
+}
+
+}  // namespace fv3

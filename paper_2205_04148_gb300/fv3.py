@@ -1,0 +1,284 @@
+"""Thin ctypes binding of the C-ABI in include/fv3.h (argument marshalling only).
+
+Every step of the substep runs in the CUDA kernels of ``_build/libfv3.so``;
+PyTorch only allocates device memory and provides the stream.  The library
+must have been built (``__graft_entry__.build()`` or
+``python paper_2205_04148_gb300/build.py``): loading fails loudly otherwise,
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfv3.so")
+
+FV3_OK = 0
+STATUS = {0: "FV3_OK", -1: "FV3_ERR_ARG", -2: "FV3_ERR_SHAPE", -3: "FV3_ERR_ALIGN", -4: "FV3_ERR_CUDA",
+          -5: "FV3_ERR_NONFINITE", -6: "FV3_ERR_CFL", -7: "FV3_ERR_TIMEOUT", -8: "FV3_ERR_UNSUPPORTED"}
+GRID_PERIODIC, GRID_CUBED = 0, 1
+FP64, FP32 = 0, 1
+KIND_CELL, KIND_XFACE, KIND_YFACE, KIND_IFACE = 0, 1, 2, 3
+HALO_WIND, HALO_W, HALO_DELP, HALO_PT, HALO_DELZ, HALO_TRACERS = 1, 2, 4, 8, 16, 32
+
+# exported symbols declared in include/fv3.h
+SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", "fv3_elem_size",
+           "fv3_get_layout", "fv3_import", "fv3_export", "fv3_halo_fill", "fv3_acoustic_substep",
+           "fv3_run_dyn", "fv3_mass_sum", "fv3_check_status", "fv3_get_metric", "fv3_stage",
+           "fv3_get_intermediate")
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("grid_type", C.c_int), ("npx", C.c_int), ("npz", C.c_int), ("n_members", C.c_int),
+                ("member_npx", C.POINTER(C.c_int)), ("precision", C.c_int), ("dx", C.c_double),
+                ("radius", C.c_double), ("omega", C.c_double)]
+
+
+class State(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("delp", C.c_void_p),
+                ("pt", C.c_void_p), ("delz", C.c_void_p), ("q", C.POINTER(C.c_void_p)), ("nq", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
+                ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double), ("ptop", C.c_double),
+                ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double)]
+
+
+class Layout(C.Structure):
+    _fields_ = [("n", C.c_int), ("nz", C.c_int), ("ntiles", C.c_int), ("pitch", C.c_int), ("rows", C.c_int),
+                ("ox", C.c_int), ("plane", C.c_longlong), ("offset3", C.c_longlong),
+                ("offseti", C.c_longlong)]
+
+
+_lib = None
+
+
+class Fv3Error(RuntimeError):
+    pass
+
+
+def load(path=LIB_PATH):
+    """Load libfv3.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise Fv3Error("libfv3.so not built (%s): run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    vp, st, i, d = C.c_void_p, C.c_int, C.c_int, C.c_double
+    L.fv3_init_grid.restype = st
+    L.fv3_init_grid.argtypes = [C.POINTER(vp), C.POINTER(GridDesc), vp]
+    L.fv3_destroy.restype = None
+    L.fv3_destroy.argtypes = [vp]
+    L.fv3_last_error.restype = C.c_char_p
+    L.fv3_last_error.argtypes = [vp]
+    L.fv3_field_elems.restype = C.c_size_t
+    L.fv3_field_elems.argtypes = [vp, i]
+    L.fv3_elem_size.restype = C.c_size_t
+    L.fv3_elem_size.argtypes = [vp]
+    L.fv3_get_layout.restype = st
+    L.fv3_get_layout.argtypes = [vp, i, C.POINTER(Layout)]
+    for nm in ("fv3_import", "fv3_export"):
+        f = getattr(L, nm)
+        f.restype = st
+        f.argtypes = [vp, i, vp, vp, i, i, i, vp]
+    L.fv3_halo_fill.restype = st
+    L.fv3_halo_fill.argtypes = [vp, C.POINTER(State), C.c_uint, vp]
+    L.fv3_acoustic_substep.restype = st
+    L.fv3_acoustic_substep.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp]
+    L.fv3_run_dyn.restype = st
+    L.fv3_run_dyn.argtypes = [vp, C.POINTER(State), C.POINTER(Params), i, vp]
+    L.fv3_mass_sum.restype = st
+    L.fv3_mass_sum.argtypes = [vp, C.POINTER(State), C.POINTER(d), vp]
+    L.fv3_check_status.restype = st
+    L.fv3_check_status.argtypes = [vp, vp]
+    L.fv3_get_metric.restype = st
+    L.fv3_get_metric.argtypes = [vp, C.c_char_p, i, C.POINTER(d)]
+    L.fv3_stage.restype = st
+    L.fv3_stage.argtypes = [vp, C.POINTER(State), C.POINTER(Params), i, vp]
+    L.fv3_get_intermediate.restype = st
+    L.fv3_get_intermediate.argtypes = [vp, C.c_char_p, i, C.POINTER(d), vp]
+    _lib = L
+    return L
+
+
+def params(**kw):
+    from .inputs import default_params
+    p = default_params()
+    p.update(kw)
+    return Params(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"], p["dz_min"],
+                  p["ptop"], p["grav"], p["rdgas"], p["cp_air"])
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Grid:
+    """A context (fv3_init_grid) plus helpers that allocate state tensors in the
+    library layout and move dense numpy arrays in and out of them."""
+
+    FIELD_KIND = {"u": KIND_YFACE, "v": KIND_XFACE, "w": KIND_CELL, "delp": KIND_CELL, "pt": KIND_CELL,
+                  "delz": KIND_CELL}
+
+    def __init__(self, grid_type, npx, npz, n_members=1, member_npx=None, precision=FP64, dx=1.0e5,
+                 radius=6.3712e6, omega=7.292e-5):
+        self.L = load()
+        self.ptr = C.c_void_p()
+        self._mnpx = None
+        if member_npx is not None:
+            self._mnpx = (C.c_int * len(member_npx))(*member_npx)
+        desc = GridDesc(grid_type, npx, npz, n_members,
+                        C.cast(self._mnpx, C.POINTER(C.c_int)) if self._mnpx else None,
+                        precision, dx, radius, omega)
+        self.check(self.L.fv3_init_grid(C.byref(self.ptr), C.byref(desc), None))
+        self.precision = precision
+        self.n_members = n_members
+        self.npz = npz
+        self.nt = 6 if grid_type == GRID_CUBED else 1
+        self.member_npx = list(member_npx) if member_npx is not None else [npx] * n_members
+
+    def close(self):
+        if self.ptr:
+            self.L.fv3_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != FV3_OK:
+            msg = self.L.fv3_last_error(self.ptr if getattr(self, "ptr", None) else None)
+            raise Fv3Error("%s: %s" % (STATUS.get(rc, rc), msg.decode() if msg else ""))
+
+    # ---- layout ----
+    def elems(self, kind):
+        return int(self.L.fv3_field_elems(self.ptr, kind))
+
+    def layout(self, member=0):
+        lay = Layout()
+        self.check(self.L.fv3_get_layout(self.ptr, member, C.byref(lay)))
+        return lay
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == FP64 else torch.float32
+
+    def alloc(self, kind=KIND_CELL):
+        import torch
+        return torch.zeros(self.elems(kind), dtype=self.torch_dtype, device="cuda")
+
+    def alloc_state(self, nq=0):
+        st = {f: self.alloc(k) for f, k in self.FIELD_KIND.items()}
+        st["q"] = [self.alloc(KIND_CELL) for _ in range(nq)]
+        return st
+
+    def cstate(self, st):
+        q = st.get("q", [])
+        arr = (C.c_void_p * max(1, len(q)))(*[t.data_ptr() for t in q]) if q else None
+        s = State(st["u"].data_ptr(), st["v"].data_ptr(), st["w"].data_ptr(), st["delp"].data_ptr(),
+                  st["pt"].data_ptr(), st["delz"].data_ptr(),
+                  C.cast(arr, C.POINTER(C.c_void_p)) if arr is not None else None, len(q))
+        s._keep = arr
+        return s
+
+    # ---- dense <-> library layout ----
+    def _dense_shape(self, kind, member):
+        n, nt, nz = self.member_npx[member], self.nt, self.npz
+        if kind == KIND_XFACE:
+            return (nt, nz, n, n + 1)
+        if kind == KIND_YFACE:
+            return (nt, nz, n + 1, n)
+        if kind == KIND_IFACE:
+            return (nt, nz + 1, n, n)
+        return (nt, nz, n, n)
+
+    def put(self, field, kind, dense, member=0, stream=None):
+        a = np.ascontiguousarray(dense, dtype=np.float64).reshape(self._dense_shape(kind, member))
+        self.check(self.L.fv3_import(self.ptr, kind, C.c_void_p(field.data_ptr()),
+                                     a.ctypes.data_as(C.c_void_p), 1, 1, member, _stream(stream)))
+        import torch
+        torch.cuda.current_stream().synchronize()
+
+    def get(self, field, kind, member=0, stream=None):
+        a = np.empty(self._dense_shape(kind, member))
+        self.check(self.L.fv3_export(self.ptr, kind, C.c_void_p(field.data_ptr()),
+                                     a.ctypes.data_as(C.c_void_p), 1, 1, member, _stream(stream)))
+        return a
+
+    def load(self, st, dense, member=0):
+        for f, k in self.FIELD_KIND.items():
+            self.put(st[f], k, dense[f], member)
+        for m, q in enumerate(dense.get("q", [])[: len(st.get("q", []))]):
+            self.put(st["q"][m], KIND_CELL, q, member)
+
+    def read(self, st, name, member=0):
+        if name.startswith("q") and name[1:].isdigit():
+            return self.get(st["q"][int(name[1:])], KIND_CELL, member)
+        return self.get(st[name], self.FIELD_KIND[name], member)
+
+    # ---- the substep ----
+    def halo_fill(self, st, mask=63, stream=None):
+        s = self.cstate(st)
+        self.check(self.L.fv3_halo_fill(self.ptr, C.byref(s), mask, _stream(stream)))
+
+    def substep(self, st, prm=None, stream=None):
+        s = self.cstate(st)
+        prm = prm or params()
+        self.check(self.L.fv3_acoustic_substep(self.ptr, C.byref(s), C.byref(prm), _stream(stream)))
+
+    def run_dyn(self, st, prm=None, n_steps=1, stream=None):
+        s = self.cstate(st)
+        prm = prm or params()
+        self.check(self.L.fv3_run_dyn(self.ptr, C.byref(s), C.byref(prm), n_steps, _stream(stream)))
+
+    def stage(self, st, stop_after, prm=None, stream=None):
+        s = self.cstate(st)
+        prm = prm or params()
+        self.check(self.L.fv3_stage(self.ptr, C.byref(s), C.byref(prm), stop_after, _stream(stream)))
+
+    def intermediate(self, name, member=0, stream=None):
+        n, nt, nz = self.member_npx[member], self.nt, self.npz
+        shp = {"uc": (nt, nz, n, n + 1), "fx1": (nt, nz, n, n + 1), "mfx": (nt, nz, n, n + 1),
+               "crx": (nt, nz, n, n + 1), "xfx": (nt, nz, n, n + 1),
+               "vc": (nt, nz, n + 1, n), "fy1": (nt, nz, n + 1, n), "mfy": (nt, nz, n + 1, n),
+               "cry": (nt, nz, n + 1, n), "yfx": (nt, nz, n + 1, n),
+               "pef": (nt, nz + 1, n, n), "gz": (nt, nz + 1, n, n)}.get(name, (nt, nz, n, n))
+        a = np.empty(shp)
+        self.check(self.L.fv3_get_intermediate(self.ptr, name.encode(), member,
+                                               a.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+        return a
+
+    def metric(self, name, member=0):
+        n, nt = self.member_npx[member], self.nt
+        if name in ("area", "rarea", "fA"):
+            shp = (nt, n, n)
+        elif name in ("dx", "rdx", "dyc", "rdyc", "cosy", "siny"):
+            shp = (nt, n + 1, n)
+        elif name in ("dy", "rdy", "dxc", "rdxc", "cosx", "sinx"):
+            shp = (nt, n, n + 1)
+        else:
+            shp = (nt, n + 1, n + 1)
+        a = np.empty(shp)
+        self.check(self.L.fv3_get_metric(self.ptr, name.encode(), member, a.ctypes.data_as(C.POINTER(C.c_double))))
+        return a
+
+    def mass(self, st, stream=None):
+        s = self.cstate(st)
+        out = (C.c_double * self.n_members)()
+        self.check(self.L.fv3_mass_sum(self.ptr, C.byref(s), out, _stream(stream)))
+        return np.array(out[:])
+
+    def check_status(self, stream=None):
+        return self.L.fv3_check_status(self.ptr, _stream(stream))
