@@ -145,6 +145,7 @@ template <typename R>
 __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  __syncthreads();  // Q (and the strips the corner turn reads) complete
   if (cc) corner_roles(Q, B, n, 1);
   __syncthreads();
   for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
