@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the FV3 acoustic substep on GB300 (one JSON line on rank 0).
+
+Workload (default): the six-tile C96 cubed sphere, 80 levels, FP64, 8 passive
+tracers, n_split = 6 acoustic substeps of 20 s per 120 s remapping step.  One
+bench "step" = one remapping step through the C-ABI (fv3_run_dyn: six
+substeps -- halo fills, c_sw, update_dz_c, riem_solver_c, p_grad_c, d_sw with
+fv_tp_2d -- then tracer_2d), replayed from a CUDA graph.  Metric:
+cell-substeps/s = n_split * 6 * npx^2 * npz / (time per step), summed over
+ranks (independent replicas, weak scaling).
+
+Timing: W warm-up steps, then K steps between CUDA events on the launching
+stream, barrier + synchronize on both sides, max over ranks.  The state
+(about 1.1 GB in FP64 with the library's intermediates) is far larger than
+L2, so no flush is needed.  SM clocks are sampled with nvidia-smi during the
+timed region.
+
+--impl reference times the CPU oracle (oracle/, plain C, one thread) on a
+bounded sample of the same workload (a level subset of C96, one acoustic
+substep per step), on the host cores of this machine.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-substeps/s"
+# Algorithmic floating-point operations per cell of one d_sw launch (the
+# dominant kernel), counted from the operations of readings R4-R6 and R11 as
+# written (each add, subtract, multiply, divide = 1): Courant numbers and
+# area fluxes 20, delp transport + damping + update 138, pt and w 146 each,
+# vorticity 9 + transport 106 + damping 26, corner kinetic energy 55, wind
+# update 9.
+DSW_FLOPS_PER_CELL = 655
+# Algorithmic HBM bytes per cell of one d_sw launch: reads u, v, w, delp, pt,
+# uc, vc and writes u, v, w, delp, pt (12 words).
+DSW_WORDS_PER_CELL = 12
+FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--npx", type=int, default=96)
+    p.add_argument("--npz", type=int, default=80)
+    p.add_argument("--nq", type=int, default=8)
+    p.add_argument("--n-split", type=int, default=6)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampler of SM clocks and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.idx = gpu_index
+        self.proc = None
+        self.enabled = enabled
+
+    def start(self):
+        if not self.enabled:
+            return
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(npx, nz_sample, reps=1):
+    """Oracle (plain C, one thread) time of one acoustic substep on C{npx} x
+    nz_sample levels; returns (cell-substeps/s, seconds)."""
+    from oracle import oracle as O
+    from paper_2205_04148_gb300 import inputs as I
+    st = I.cubed_state(npx, nz_sample, seed=0, ntracers=0)
+    d = O.Domain(True, npx, nz_sample)
+    s = O.State(d)
+    s.load(st)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s.substep()
+    dt = (time.perf_counter() - t0) / reps
+    return 6 * npx * npx * nz_sample / dt, dt
+
+
+def reference_arm(a):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    # size the per-step sample so that (K + W) steps take about two minutes
+    rate1, t1 = cpu_oracle_rate(a.npx, 2)
+    per_level = t1 / 2
+    budget = 120.0 / max(1, a.steps + a.warmup)
+    nzs = int(max(1, min(a.npz, budget / per_level)))
+    from oracle import oracle as O
+    from paper_2205_04148_gb300 import inputs as I
+    st = I.cubed_state(a.npx, nzs, seed=0, ntracers=0)
+    d = O.Domain(True, a.npx, nzs)
+    s = O.State(d)
+    s.load(st)
+    for _ in range(a.warmup):
+        s.substep()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        s.substep()
+    dt = (time.perf_counter() - t0) / max(1, a.steps)
+    value = 6 * a.npx * a.npx * nzs / dt
+    sample = "one acoustic substep of C%d x %d levels (of %d) per step, FP64 oracle, 1 thread" % (a.npx, nzs, a.npz)
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "cubed-sphere C%d x %d levels, FP64, n_split %d" % (a.npx, a.npz, a.n_split),
+                      "sample_levels": nzs},
+           "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def ours(a):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as D
+        torch.cuda.set_device(local)
+        D.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as D
+            D.barrier()
+
+    def allmax(x):
+        if ws > 1:
+            import torch.distributed as D
+            t = torch.tensor([x], device="cuda", dtype=torch.float64)
+            D.all_reduce(t, op=D.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    prec = fv3.FP64 if a.precision == "fp64" else fv3.FP32
+    g = fv3.Grid(fv3.GRID_CUBED, a.npx, a.npz, precision=prec)
+    st = I.cubed_state(a.npx, a.npz, seed=rank, ntracers=a.nq)
+    gs = g.alloc_state(a.nq)
+    g.load(gs, st)
+    prm = fv3.params(n_split=a.n_split)
+    cells = 6 * a.npx * a.npx * a.npz
+    L = g.L
+    L.fv3_kernel_launches.restype = C.c_longlong
+    L.fv3_kernel_launches.argtypes = [C.c_void_p]
+    L.fv3_launch_stage.restype = C.c_int
+    L.fv3_launch_stage.argtypes = [C.c_void_p, C.POINTER(fv3.State), C.POINTER(fv3.Params), C.c_int, C.c_int,
+                                   C.c_void_p]
+    L.fv3_calibrate.restype = C.c_int
+    L.fv3_calibrate.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+
+    # --- warm-up and timed region -------------------------------------
+    for _ in range(max(1, a.warmup)):
+        g.run_dyn(gs, prm, 1)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
+    clocks = Clocks(smi_index, enabled=not a.no_clocks)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = L.fv3_kernel_launches(g.ptr)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        g.run_dyn(gs, prm, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = L.fv3_kernel_launches(g.ptr) - l0
+    ms_step = allmax(e0.elapsed_time(e1) / a.steps)
+    value = ws * a.n_split * cells / (ms_step / 1e3)
+    status = g.check_status()
+
+    # --- dominant kernel (d_sw) timed alone, live ----------------------
+    s = g.cstate(gs)
+    g.stage(gs, 4, prm)
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 5, 1, sp))
+    reps = 10
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 6, 2, sp))   # warm
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 6, reps, sp))
+    k1.record(stream)
+    torch.cuda.synchronize()
+    t_dsw = k0.elapsed_time(k1) / reps / 1e3
+    # FP64 multiply-add rate of this GPU, measured live (calibration kernel)
+    work = C.c_double()
+    g.check(L.fv3_calibrate(g.ptr, 0, sp, C.byref(work)))
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(3):
+        g.check(L.fv3_calibrate(g.ptr, 0, sp, C.byref(work)))
+    c1.record(stream)
+    torch.cuda.synchronize()
+    fp64_meas = work.value * 3 / (c0.elapsed_time(c1) / 1e3) / 1e9
+    esize = 8 if prec == fv3.FP64 else 4
+    if prec == fv3.FP64:
+        ach = DSW_FLOPS_PER_CELL * cells / t_dsw / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
+                "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": None, "kernel": "k_d_sw<double>",
+                "ms_per_launch": t_dsw * 1e3, "flops_per_cell": DSW_FLOPS_PER_CELL,
+                "peak_measured_fma": fp64_meas,
+                "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it"}
+    else:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ach = DSW_WORDS_PER_CELL * esize * cells / t_dsw / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3}
+
+    # --- end to end through the C-ABI with host buffers ------------------
+    e2e = None
+    if not a.no_e2e:
+        pin = {}
+        kinds = dict(g.FIELD_KIND)
+        names = list(kinds) + ["q%d" % m for m in range(a.nq)]
+        dense_in = {}
+        for nm in names:
+            src = st[nm] if not nm.startswith("q") else st["q"][int(nm[1:])]
+            t = torch.empty(src.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = src
+            dense_in[nm] = t
+            pin[nm] = torch.empty(src.shape, dtype=torch.float64, pin_memory=True)
+        outs = [nm for nm in names if nm != "delz"]
+        h2d = sum(dense_in[nm].numel() * 8 for nm in names)
+        d2h = sum(pin[nm].numel() * 8 for nm in outs)
+
+        def field(nm):
+            return gs[nm] if not nm.startswith("q") else gs["q"][int(nm[1:])]
+
+        def kind(nm):
+            return kinds.get(nm, fv3.KIND_CELL)
+
+        def one():
+            for nm in names:
+                g.check(L.fv3_import(g.ptr, kind(nm), C.c_void_p(field(nm).data_ptr()),
+                                     C.c_void_p(dense_in[nm].data_ptr()), 1, 1, 0, sp))
+            g.run_dyn(gs, prm, 1)
+            for nm in outs:
+                g.check(L.fv3_export(g.ptr, kind(nm), C.c_void_p(field(nm).data_ptr()),
+                                     C.c_void_p(pin[nm].data_ptr()), 1, 1, 0, sp))
+
+        one()
+        torch.cuda.synchronize()
+        ke = max(3, a.steps // 4)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            one()
+        torch.cuda.synchronize()
+        te = allmax((time.perf_counter() - t0) / ke)
+        e2e = {"value": ws * a.n_split * cells / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3}
+
+    # --- CPU oracle baseline (rank 0, N = 1) -----------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        nzs, reps = a.npz, 3
+        rate, dt = cpu_oracle_rate(a.npx, nzs, reps)
+        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": "%d acoustic substeps of C%d x %d levels, FP64 oracle, 1 thread (%.1f s each)"
+                         % (reps, a.npx, nzs, dt)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if prec == fv3.FP64 else "f32 (column solve f64)",
+               "data": "synthetic",
+               "config": {"workload": "cubed-sphere C%d x %d levels, %s, n_split %d, %d tracers, one remapping "
+                                      "step per bench step" % (a.npx, a.npz, a.precision.upper(), a.n_split, a.nq),
+                          "cells": cells, "substeps_per_step": a.n_split, "l2": "inputs larger than L2",
+                          "parallelism": "replicas" if ws > 1 else "single GPU"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk, "status": status}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as D
+        D.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+    return ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

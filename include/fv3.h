@@ -192,6 +192,24 @@ fv3_status fv3_stage(fv3_ctx* ctx, const fv3_state* state, const fv3_params* par
                      fv3_stream stream);
 fv3_status fv3_get_intermediate(fv3_ctx* ctx, const char* name, int member, double* dense_host, fv3_stream stream);
 
+/* Enqueue only stage `stage` of the substep, `reps` times, on the current
+ * intermediates (0 halo fill, 1 c_sw, 2 update_dz_c, 3 riem_solver_c, 4 pef/gz
+ * halo + p_grad_c, 5 C-grid halo, 6 d_sw); run fv3_stage first so that its
+ * inputs exist.  Used to time one kernel with events on `stream`; the state
+ * is not advanced. */
+fv3_status fv3_launch_stage(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int stage, int reps,
+                            fv3_stream stream);
+
+/* Kernels the library has enqueued on ctx so far (graph replays included). */
+long long fv3_kernel_launches(const fv3_ctx* ctx);
+
+/* Machine calibration (paper Section IX-A: bandwidth test and copy stencil):
+ * what = 0 FP64 multiply-add throughput, 1 FP32 multiply-add throughput, 2
+ * copy stencil over one halo-padded FP64 3-D field of the context.  Enqueues
+ * one launch on `stream` and returns its work (flops, or bytes read + written)
+ * in *work_per_launch; time it with events on the same stream. */
+fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

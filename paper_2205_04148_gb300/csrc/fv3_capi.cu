@@ -485,7 +485,10 @@ extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_para
       c.graph = nullptr;
     }
     CK(x, cudaStreamBeginCapture(x->cap, cudaStreamCaptureModeThreadLocal));
+    const long long before = c.launches;
     enqueue_remap_step(c, in, P, x->cap);
+    c.graph_launches = c.launches - before;
+    c.launches = before;
     cudaGraph_t g = nullptr;
     cudaError_t e1 = cudaStreamEndCapture(x->cap, &g);
     if (e1 != cudaSuccess) return fail(x, FV3_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
@@ -498,6 +501,7 @@ extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_para
     c.graph_key = key;
   }
   for (int k = 0; k < n_steps; ++k) CK(x, cudaGraphLaunch(c.graph, st));
+  c.launches += (long long)n_steps * c.graph_launches;
   return FV3_OK;
 }
 
@@ -558,4 +562,29 @@ extern "C" fv3_status fv3_get_intermediate(fv3_ctx* x, const char* name, int mem
   for (const E& e : tab)
     if (!std::strcmp(e.nm, name)) return fv3_export(x, e.kind, e.p, dense, 1, 1, member, stream);
   return fail(x, FV3_ERR_ARG, std::string("unknown intermediate ") + name);
+}
+
+extern "C" fv3_status fv3_launch_stage(fv3_ctx* x, const fv3_state* s, const fv3_params* p, int stage, int reps,
+                                       fv3_stream stream) {
+  if (!x) return FV3_ERR_ARG;
+  fv3_status r = check_state(x, s, false);
+  if (r != FV3_OK) return r;
+  r = check_params(x, p);
+  if (r != FV3_OK) return r;
+  if (stage < 0 || stage > 6 || reps < 1) return fail(x, FV3_ERR_ARG, "stage 0..6, reps >= 1");
+  Ctx& c = x->c;
+  const StateView in = view(s), nx = internal_view(c, in);
+  for (int k = 0; k < reps; ++k) enqueue_substep(c, in, nx, to_params(p), false, (cudaStream_t)stream, 99, stage);
+  CK(x, cudaGetLastError());
+  return FV3_OK;
+}
+
+extern "C" long long fv3_kernel_launches(const fv3_ctx* x) { return x ? x->c.launches : -1; }
+
+extern "C" fv3_status fv3_calibrate(fv3_ctx* x, int what, fv3_stream stream, double* work_per_launch) {
+  if (!x || !work_per_launch) return FV3_ERR_ARG;
+  if (what < 0 || what > 2) return fail(x, FV3_ERR_ARG, "what: 0 fp64 fma, 1 fp32 fma, 2 fp64 copy stencil");
+  *work_per_launch = enqueue_calibration(x->c, what, (cudaStream_t)stream);
+  CK(x, cudaGetLastError());
+  return FV3_OK;
 }

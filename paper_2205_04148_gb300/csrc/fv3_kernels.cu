@@ -902,6 +902,7 @@ void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStrea
     dim3 grid((maxc + 255) / 256, maxl, nf);
     if (c.prec == 0) k_halo<double><<<grid, 256, 0, st>>>(b, c.geo_d);
     else k_halo<float><<<grid, 256, 0, st>>>(b, c.geo_d);
+    ++c.launches;
   }
 }
 
@@ -928,7 +929,7 @@ void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st) {
 
 template <typename R>
 static void substep_t(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool acc,
-                      cudaStream_t st, int stop_after) {
+                      cudaStream_t st, int stop_after, int only) {
   StepArgs<R> a{};
   a.geo = c.geo_d;
   a.items = c.items_hz;
@@ -947,11 +948,15 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   }
   a.status = c.status;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
-
-  enqueue_halo_prognostics(c, in, st);
-  if (stop_after <= 0) return;
-  // c_sw
-  {
+  // stage ids: 0 halo fill, 1 c_sw, 2 update_dz_c, 3 riem_solver_c,
+  // 4 pef/gz halo + p_grad_c, 5 C-grid halo, 6 d_sw
+  auto run = [&](int stage) {
+    if (only >= 0) return stage == only;
+    const int last = stop_after >= 5 ? 6 : stop_after;
+    return stage <= last;
+  };
+  if (run(0)) enqueue_halo_prognostics(c, in, st);
+  if (run(1)) {  // c_sw
     const size_t sm = blk_smem(c, 13);
     if (c.BX == 32 && c.BY == 8) {
       set_smem(k_c_sw<R, 32, 8>, sm);
@@ -960,39 +965,33 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
       set_smem(k_c_sw<R, 32, 16>, sm);
       k_c_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
     }
+    ++c.launches;
   }
-  if (stop_after <= 1) return;
-  // update_dz_c
-  {
+  if (run(2)) {  // update_dz_c
     StepArgs<R> b = a;
     b.items = c.items_dz;
     k_update_dz_c<R><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    ++c.launches;
   }
-  if (stop_after <= 2) return;
-  // riem_solver_c
-  k_riem_c<R><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
-  if (stop_after <= 3) return;
-  // pef, gz one ring into the halo
-  {
+  if (run(3)) {  // riem_solver_c
+    k_riem_c<R><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
+    ++c.launches;
+  }
+  if (run(4)) {  // pef, gz one ring into the halo, then p_grad_c
     std::vector<HaloField> F;
     F.push_back(hf(c, K_CELL1, c.pef, nullptr, c.nz + 1, 1));
     F.push_back(hf(c, K_CELL1, c.gz, nullptr, c.nz + 1, 1));
     enqueue_halo_fields(c, F, st);
-  }
-  // p_grad_c
-  {
     const int nb = (c.max_n + 1 + 15) / 16;
     k_p_grad_c<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+    ++c.launches;
   }
-  if (stop_after <= 4) return;
-  // C-grid winds into the halo
-  {
+  if (run(5)) {  // C-grid winds into the halo
     std::vector<HaloField> F;
     F.push_back(hf(c, K_CGRID, c.uc, c.vc, c.nz, 0));
     enqueue_halo_fields(c, F, st);
   }
-  // d_sw
-  {
+  if (run(6)) {  // d_sw
     const size_t sm = blk_smem(c, 21);
     if (c.BX == 32 && c.BY == 8) {
       set_smem(k_d_sw<R, 32, 8>, sm);
@@ -1001,13 +1000,14 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
       set_smem(k_d_sw<R, 32, 16>, sm);
       k_d_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
     }
+    ++c.launches;
   }
 }
 
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
-                     cudaStream_t st, int stop_after) {
-  if (c.prec == 0) substep_t<double>(c, in, out, P, accumulate, st, stop_after);
-  else substep_t<float>(c, in, out, P, accumulate, st, stop_after);
+                     cudaStream_t st, int stop_after, int only) {
+  if (c.prec == 0) substep_t<double>(c, in, out, P, accumulate, st, stop_after, only);
+  else substep_t<float>(c, in, out, P, accumulate, st, stop_after, only);
 }
 
 template <typename R>
@@ -1022,6 +1022,7 @@ static void copy_planes_t(Ctx& c, const std::vector<std::pair<void*, const void*
   const int nb = c.max_n + 1;
   k_copy_planes<R><<<dim3((nb + 31) / 32, (nb + 7) / 8, c.n_planes), dim3(32, 8), 0, st>>>(c.geo_d, c.planes, a,
                                                                                              gate, it);
+  ++c.launches;
 }
 
 static void copy_planes(Ctx& c, const std::vector<std::pair<void*, const void*>>& pairs, const int* gate, int it,
@@ -1058,6 +1059,7 @@ static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
     k_cmax<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(c.geo_d, c.planes, (const R*)c.acrx,
                                                                  (const R*)c.acry, c.cmax);
     k_nsplt<R><<<1, 1, 0, st>>>(c.cmax, c.nsplt, NSPLT_MAX, c.status, (const R*)nullptr);
+    c.launches += 2;
   }
   copy_planes(c, {{c.dp0, c.dpstart}}, nullptr, 0, st);
   TracerArgs<R> a{};
@@ -1088,6 +1090,7 @@ static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
       set_smem(k_tracer<R, 32, 16>, sm);
       k_tracer<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
     }
+    ++c.launches;
     std::vector<std::pair<void*, const void*>> pairs;
     for (int q = 0; q < s.nq; ++q) pairs.push_back({s.q[q], c.qtmp[q]});
     pairs.push_back({c.dp0, c.dp1});
@@ -1109,11 +1112,13 @@ void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st) {
     k_mass_partial<float><<<c.n_planes, 256, 0, st>>>(c.geo_d, c.planes, (const float*)delp, c.Md.area,
                                                       c.mass_part);
   k_mass_final<<<(c.nmem + 63) / 64, 64, 0, st>>>(c.mass_part, c.mass_first, c.nmem, c.mass_out);
+  c.launches += 2;
 }
 
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
                   int dir, cudaStream_t st) {
   const int blocks = 1024;
+  ++c.launches;
   if (c.prec == 0 || iface == 2) {
     if (dense_is_double)
       k_pack<double, double><<<blocks, 256, 0, st>>>(c.geo_d, member, kind, nlev, iface, (double*)padded,

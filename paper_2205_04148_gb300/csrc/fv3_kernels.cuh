@@ -112,6 +112,10 @@ struct Ctx {
   double* mass_part = nullptr;
   double* mass_out = nullptr;
   std::vector<void*> owned;  // every device allocation, freed by destroy
+  // kernels enqueued by the library (host count; graph replays add the
+  // number captured in the graph)
+  long long launches = 0;
+  long long graph_launches = 0;
   // graph of one remapping step
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
@@ -131,7 +135,7 @@ struct ParamView {
 // orchestration (fv3_kernels.cu); enqueue_pack: iface 2 = FP64 metric planes
 void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
-                     cudaStream_t st, int stop_after = 99);
+                     cudaStream_t st, int stop_after = 99, int only = -1);
 void enqueue_tracers(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st);
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
@@ -140,5 +144,7 @@ void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStrea
 void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cudaStream_t st);
 void enqueue_zero_acc(Ctx& c, cudaStream_t st);
 void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st);
+// calibration kernels (fv3_calib.cu): returns work per launch (flops or bytes)
+double enqueue_calibration(Ctx& c, int what, cudaStream_t st);
 
 }  // namespace fv3
