@@ -210,6 +210,28 @@ long long fv3_kernel_launches(const fv3_ctx* ctx);
  * in *work_per_launch; time it with events on the same stream. */
 fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work_per_launch);
 
+/* Column solve of riem_solver_c for callers that cannot allocate device
+ * memory (no counterpart in the paper).  Code that runs under a fixed,
+ * pre-reserved memory budget, or inside a host framework that owns the whole
+ * device pool, cannot create a context with fv3_init_grid (which allocates).
+ * This entry point needs no context and calls no allocator: the caller passes
+ * device arrays, level-major (element (k, col) at k * ncol + col), FP64:
+ * inputs delpc, ptc, wc, delzc [nz][ncol]; outputs pef, gz [nz+1][ncol]; only
+ * params->dt (the solve uses dt/2), ptop, grav, rdgas, cp_air and a_imp are
+ * read.  Scratch is one fixed 32 MiB array inside the library's GPU image
+ * (held on every GPU that loads the library until the process exits), so
+ * 5 * nz * ncol must not exceed 4,194,304 (e.g. ncol <= 10485 at nz = 80);
+ * larger sizes return FV3_ERR_SHAPE without launching.  The first call on a
+ * device looks up the scratch address on that device (make that first call
+ * before any stream capture).  All calls share the one scratch array, so
+ * calls that may run at the same time on the GPU (different streams, or
+ * host threads) race and must be ordered by the caller; nothing in the
+ * scratch has to start at zero, every value read is written first in the
+ * same call. */
+fv3_status fv3_riem_solver_c_noalloc(int ncol, int nz, const double* delpc, const double* ptc, const double* wc,
+                                     const double* delzc, double* pef, double* gz, const fv3_params* params,
+                                     fv3_stream stream);
+
 #ifdef __cplusplus
 }
 #endif
