@@ -210,6 +210,19 @@ long long fv3_kernel_launches(const fv3_ctx* ctx);
  * in *work_per_launch; time it with events on the same stream. */
 fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work_per_launch);
 
+/* Block shape (bx x by cells) and level chunk of the horizontal kernels
+ * (c_sw, d_sw, tracer_2d).  Compiled shapes: 32x8, 32x16, 64x8, 16x16;
+ * 1 <= kchunk <= npz.  Drops the cached remapping-step graph. */
+fv3_status fv3_set_tiles(fv3_ctx* ctx, int bx, int by, int kchunk);
+fv3_status fv3_get_tiles(const fv3_ctx* ctx, int* bx, int* by, int* kchunk);
+
+/* Autotuner (the paper's transfer tuning, Section VII-B, as an empirical
+ * search): times c_sw + d_sw on `state` for every compiled block shape and
+ * level chunks 1, 4, 16, keeps the fastest (fv3_set_tiles) and returns its
+ * time per (c_sw + d_sw) in *best_ms (may be NULL).  Synchronises `stream`. */
+fv3_status fv3_autotune(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream,
+                        double* best_ms);
+
 /* Column solve of riem_solver_c for callers that cannot allocate device
  * memory (no counterpart in the paper).  Code that runs under a fixed,
  * pre-reserved memory budget, or inside a host framework that owns the whole

@@ -120,6 +120,17 @@ fv3_status ensure_stage(fv3_ctx* x, size_t bytes) {
   return FV3_OK;
 }
 
+std::vector<Item> block_items(const Ctx& c, int bx, int by) {
+  std::vector<Item> hz;
+  for (int m = 0; m < c.nmem; ++m) {
+    const Geo& g = c.geo[m];
+    for (int t = 0; t < g.nt; ++t)
+      for (int y0 = 0; y0 < g.n; y0 += by)
+        for (int x0 = 0; x0 < g.n; x0 += bx) hz.push_back({m, t, x0, y0});
+  }
+  return hz;
+}
+
 size_t dense_count(const Geo& g, int kind, int nlev) {
   const int n = g.n;
   const int ni = n + (kind == 1 || kind == 3), nj = n + (kind == 2 || kind == 3);
@@ -202,20 +213,22 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
 
   // metric: concatenate members, FP64 and FP32 copies
   {
-    const int NM = 19;
+    const int NM = 21;
     std::vector<double> all[NM];
     for (int q = 0; q < NM; ++q) all[q].assign(c.elems2, NAN);
     for (int m = 0; m < c.nmem; ++m) {
       const HostMetric& M = HM[m];
       const std::vector<double>* src[NM] = {&M.area, &M.rarea, &M.fA, &M.dx, &M.rdx, &M.dyc, &M.rdyc,
                                             &M.cosy, &M.siny, nullptr, &M.dy, &M.rdy, &M.dxc, &M.rdxc,
-                                            &M.cosx, &M.sinx, nullptr, &M.fC, &M.rareac};
+                                            &M.cosx, &M.sinx, nullptr, &M.fC, &M.rareac, nullptr, nullptr};
       const long long o = c.geo[m].off2;
       for (int q = 0; q < NM; ++q)
         if (src[q]) std::copy(src[q]->begin(), src[q]->end(), all[q].begin() + o);
       for (size_t e = 0; e < M.siny.size(); ++e) {
         all[9][o + e] = 1.0 / (M.siny[e] * M.siny[e]);
         all[16][o + e] = 1.0 / (M.sinx[e] * M.sinx[e]);
+        all[19][o + e] = M.dy[e] * M.rdxc[e];
+        all[20][o + e] = M.dx[e] * M.rdyc[e];
       }
     }
     double* dptr[NM];
@@ -231,6 +244,7 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
       M.area = p[0]; M.rarea = p[1]; M.fA = p[2]; M.dx = p[3]; M.rdx = p[4]; M.dyc = p[5]; M.rdyc = p[6];
       M.cosy = p[7]; M.siny = p[8]; M.rsin2y = p[9]; M.dy = p[10]; M.rdy = p[11]; M.dxc = p[12]; M.rdxc = p[13];
       M.cosx = p[14]; M.sinx = p[15]; M.rsin2x = p[16]; M.fC = p[17]; M.rareac = p[18];
+      M.wx = p[19]; M.wy = p[20];
     };
     fill(c.Md, dptr);
     fill(c.Mf, fptr);
@@ -254,8 +268,6 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
       const Geo& g = c.geo[m];
       mfirst.push_back((int)planes.size());
       for (int t = 0; t < nt; ++t) {
-        for (int y0 = 0; y0 < g.n; y0 += c.BY)
-          for (int x0 = 0; x0 < g.n; x0 += c.BX) hz.push_back({m, t, x0, y0});
         for (int y0 = 0; y0 < g.n; y0 += c.BYc)
           for (int x0 = 0; x0 < g.n; x0 += c.BXc) dz.push_back({m, t, x0, y0});
         for (int j = 0; j < g.n; ++j) rows.push_back({m, t, j, 0});
@@ -263,6 +275,7 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
       }
     }
     mfirst.push_back((int)planes.size());
+    hz = block_items(c, c.BX, c.BY);
     c.n_items_hz = (int)hz.size();
     c.n_items_dz = (int)dz.size();
     c.n_rows = (int)rows.size();
@@ -587,4 +600,90 @@ extern "C" fv3_status fv3_calibrate(fv3_ctx* x, int what, fv3_stream stream, dou
   *work_per_launch = enqueue_calibration(x->c, what, (cudaStream_t)stream);
   CK(x, cudaGetLastError());
   return FV3_OK;
+}
+
+extern "C" fv3_status fv3_set_tiles(fv3_ctx* x, int bx, int by, int kchunk) {
+  if (!x) return FV3_ERR_ARG;
+  Ctx& c = x->c;
+  if (!shape_supported(bx, by)) return fail(x, FV3_ERR_UNSUPPORTED, "block shape not compiled");
+  if (kchunk < 1 || kchunk > c.nz) return fail(x, FV3_ERR_ARG, "kchunk must be in [1, npz]");
+  std::vector<Item> hz = block_items(c, bx, by);
+  Item* d = nullptr;
+  CK(x, dalloc(c, &d, hz.size()));
+  CK(x, cudaMemcpy(d, hz.data(), sizeof(Item) * hz.size(), cudaMemcpyHostToDevice));
+  c.items_hz = d;  // the previous list stays owned until destroy (graphs may refer to it)
+  c.n_items_hz = (int)hz.size();
+  c.BX = bx;
+  c.BY = by;
+  c.kchunk = kchunk;
+  if (c.graph) {
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+    c.graph_key.clear();
+  }
+  return FV3_OK;
+}
+
+extern "C" fv3_status fv3_get_tiles(const fv3_ctx* x, int* bx, int* by, int* kchunk) {
+  if (!x || !bx || !by || !kchunk) return FV3_ERR_ARG;
+  *bx = x->c.BX;
+  *by = x->c.BY;
+  *kchunk = x->c.kchunk;
+  return FV3_OK;
+}
+
+// Empirical tuning of the block shape and level chunk of the horizontal
+// kernels on the caller's state (the paper's transfer tuning, Section VII-B,
+// searches transformation configurations on representative cutouts and
+// transfers the best ones; here the search space is the compiled block
+// shapes x level chunks, timed with events on the full d_sw + c_sw stages).
+extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream,
+                                   double* best_ms) {
+  if (!x) return FV3_ERR_ARG;
+  fv3_status r = check_state(x, s, false);
+  if (r != FV3_OK) return r;
+  r = check_params(x, p);
+  if (r != FV3_OK) return r;
+  Ctx& c = x->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int shapes[4][2] = {{32, 8}, {32, 16}, {64, 8}, {16, 16}};
+  const int chunks[3] = {1, 4, 16};
+  const StateView in = view(s);
+  const StateView nx = internal_view(c, in);
+  const Params P = to_params(p);
+  enqueue_substep(c, in, nx, P, false, st, 5);  // intermediates for the stage runs
+  cudaEvent_t e0, e1;
+  CK(x, cudaEventCreate(&e0));
+  CK(x, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bb[3] = {c.BX, c.BY, c.kchunk};
+  for (const auto& sh : shapes)
+    for (int kc : chunks) {
+      if (kc > c.nz) continue;
+      if (fv3_set_tiles(x, sh[0], sh[1], kc) != FV3_OK) continue;
+      for (int w = 0; w < 2; ++w) {
+        enqueue_substep(c, in, nx, P, false, st, 99, 1);
+        enqueue_substep(c, in, nx, P, false, st, 99, 6);
+      }
+      CK(x, cudaEventRecord(e0, st));
+      for (int rep = 0; rep < 3; ++rep) {
+        enqueue_substep(c, in, nx, P, false, st, 99, 1);
+        enqueue_substep(c, in, nx, P, false, st, 99, 6);
+      }
+      CK(x, cudaEventRecord(e1, st));
+      CK(x, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(x, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms / 3 < best) {
+        best = ms / 3;
+        bb[0] = sh[0];
+        bb[1] = sh[1];
+        bb[2] = kc;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  r = fv3_set_tiles(x, bb[0], bb[1], bb[2]);
+  if (best_ms) *best_ms = best;
+  return r;
 }

@@ -44,6 +44,7 @@ struct Metric {
   const R *dx, *rdx, *dyc, *rdyc, *cosy, *siny, *rsin2y; // y-faces
   const R *dy, *rdy, *dxc, *rdxc, *cosx, *sinx, *rsin2x; // x-faces
   const R *fC, *rareac;                                // corners
+  const R *wx, *wy;  // dy/dxc on x-faces, dx/dyc on y-faces (damping weights)
 };
 
 struct Params {

@@ -65,13 +65,64 @@ __device__ __forceinline__ R ppm_face(const R* q, int s, R c) {
   return qu + (R(1) - ac) * (x - ac * (bl + br));
 }
 
+// FP64 specialisation.  On this GPU the FP64 pipe has 2 lanes per SM and per
+// clock, and FP64 compares, min/max and |x| occupy it like arithmetic does.
+// They are done here on the integer pipe instead, on the IEEE bit patterns:
+// x -> b ^ ((b >> 63) & 0x7fff...f) is an order-preserving signed integer
+// key, the magnitude bits of non-negative doubles order like the values, and
+// 2|x| is |x| with the exponent raised by one (twice the bits below the
+// normal range).  Results are the same as the generic version except for the
+// sign of zero in ties of the clamp, and except when bl*br underflows to zero
+// (opposite-signed slopes below 1e-162), neither of which changes a value.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ long long twice_mag(long long m) {
+  return m < (1LL << 52) ? (m << 1) : m + (1LL << 52);
+}
+
+template <>
+__device__ __forceinline__ double ppm_edge<double>(double qm, double q0, double q1, double qp) {
+  const double al = (7.0 / 12.0) * (q0 + q1) - (1.0 / 12.0) * (qm + qp);
+  const long long k0 = okey(q0), k1 = okey(q1), ka = okey(al);
+  const bool o = k0 < k1;
+  const double lo = o ? q0 : q1, hi = o ? q1 : q0;
+  const long long klo = o ? k0 : k1, khi = o ? k1 : k0;
+  return ka < klo ? lo : (ka > khi ? hi : al);
+}
+
+template <>
+__device__ __forceinline__ double ppm_face<double>(const double* q, int s, double c) {
+  const long long cb = __double_as_longlong(c);
+  const bool pos = cb > 0;  // c > 0 (and not -0)
+  const double* p = pos ? q - s : q;
+  const double qu = p[0];
+  double bl = ppm_edge<double>(p[-2 * s], p[-s], p[0], p[s]) - qu;
+  double br = ppm_edge<double>(p[-s], p[0], p[s], p[2 * s]) - qu;
+  const long long sb = __double_as_longlong(bl), sr = __double_as_longlong(br);
+  const long long MAG = 0x7fffffffffffffffLL;
+  const long long mb = sb & MAG, mr = sr & MAG;
+  if ((sb ^ sr) >= 0 || mb == 0 || mr == 0) {  // bl * br >= 0: local extremum
+    bl = 0.0;
+    br = 0.0;
+  } else if (mb > twice_mag(mr)) {  // |bl| > 2|br|: bl = -2 br
+    bl = __longlong_as_double(twice_mag(mr) | (~sr & ~MAG));
+  } else if (mr > twice_mag(mb)) {  // |br| > 2|bl|: br = -2 bl
+    br = __longlong_as_double(twice_mag(mb) | (~sb & ~MAG));
+  }
+  const double ac = __longlong_as_double(cb & MAG);
+  const double x = pos ? br : bl;
+  return qu + (1.0 - ac) * (x - ac * (bl + br));
+}
+
 // ------------------------------------------------------------------------
 // per-tile metric view: element (i, j) at p[j * pitch + i]
 // ------------------------------------------------------------------------
 template <typename R>
 struct TM {
   const R *area, *rarea, *fA, *dx, *rdx, *dyc, *rdyc, *cosy, *siny, *rsin2y, *dy, *rdy, *dxc, *rdxc, *cosx, *sinx,
-      *rsin2x, *fC, *rareac;
+      *rsin2x, *fC, *rareac, *wx, *wy;
   int pitch;
 };
 #define MT(name, j, i) __ldg(m.name + (long long)(j) * m.pitch + (i))
@@ -86,6 +137,7 @@ __device__ __forceinline__ TM<R> tile_metric(const Metric<R>& M, const Geo& g, i
   m.dy = M.dy + o; m.rdy = M.rdy + o; m.dxc = M.dxc + o; m.rdxc = M.rdxc + o;
   m.cosx = M.cosx + o; m.sinx = M.sinx + o; m.rsin2x = M.rsin2x + o;
   m.fC = M.fC + o; m.rareac = M.rareac + o;
+  m.wx = M.wx + o; m.wy = M.wy + o;
   m.pitch = g.pitch;
   return m;
 }
@@ -134,81 +186,165 @@ __device__ __forceinline__ void corner_roles(R* Q, const Blk& B, int n, int role
 // shared-memory arrays of the transport
 template <typename R>
 struct TS {
-  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP;
+  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL, *GX, *GY;
 };
+
+// monotone limiter on the cell's deviations (generic, then FP64 on the
+// integer pipe -- see okey / twice_mag above)
+template <typename R>
+__device__ __forceinline__ void ppm_limit(R& bl, R& br) {
+  if (bl * br >= R(0)) {
+    bl = R(0);
+    br = R(0);
+  } else if (fabs(bl) > R(2) * fabs(br)) {
+    bl = R(-2) * br;
+  } else if (fabs(br) > R(2) * fabs(bl)) {
+    br = R(-2) * bl;
+  }
+}
+template <>
+__device__ __forceinline__ void ppm_limit<double>(double& bl, double& br) {
+  const long long sb = __double_as_longlong(bl), sr = __double_as_longlong(br);
+  const long long MAG = 0x7fffffffffffffffLL;
+  const long long mb = sb & MAG, mr = sr & MAG;
+  if ((sb ^ sr) >= 0 || mb == 0 || mr == 0) {
+    bl = 0.0;
+    br = 0.0;
+  } else if (mb > twice_mag(mr)) {
+    bl = __longlong_as_double(twice_mag(mr) | (~sr & ~MAG));
+  } else if (mr > twice_mag(mb)) {
+    br = __longlong_as_double(twice_mag(mb) | (~sb & ~MAG));
+  }
+}
+template <typename R>
+__device__ __forceinline__ bool positive(R c) { return c > R(0); }
+template <>
+__device__ __forceinline__ bool positive<double>(double c) { return __double_as_longlong(c) > 0; }
+template <typename R>
+__device__ __forceinline__ R magnitude(R c) { return fabs(c); }
+template <>
+__device__ __forceinline__ double magnitude<double>(double c) {
+  return __longlong_as_double(__double_as_longlong(c) & 0x7fffffffffffffffLL);
+}
+
+// face value at face l from precomputed edge values AL (AL[l] is the edge
+// between cells l - s and l): limited parabola of the upwind cell, swept mean
+template <typename R>
+__device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, R c) {
+  const bool pos = positive(c);
+  const int p = pos ? l - s : l;
+  const R qu = Q[p];
+  R bl = AL[p] - qu, br = AL[p + s] - qu;
+  ppm_limit(bl, br);
+  const R ac = magnitude(c);
+  const R x = pos ? br : bl;
+  return qu + (R(1) - ac) * (x - ac * (bl + br));
+}
 
 // fv_tp_2d (reading R5) + optional delnflux (R6) of the shared-memory scalar
 // Q on the block: fluxes on x-faces [x0, x1] x [y0, y1) -> FXO and y-faces
 // [x0, x1) x [y0, y1] -> FYO.  mfx/mfy: mass fluxes (null: area fluxes).
 // damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
+// Every PPM sweep first computes each edge value once (AL), then the face
+// values; the Laplacian of the damping is the divergence of face gradients.
 template <typename R>
 __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const bool dmp = damp != R(0);
   __syncthreads();  // Q (and the strips the corner turn reads) complete
   if (cc) corner_roles(Q, B, n, 1);
   __syncthreads();
-  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  // y-sweep of the plain field (y-role corners): edges, then faces
+  for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
+    S.AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
   });
-  if (damp != R(0))
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+  if (dmp)
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.LAP[l] = (Q[l + SX] - Q[l]) * MT(dx, j + 1, i) * MT(rdyc, j + 1, i) -
-                 (Q[l] - Q[l - SX]) * MT(dx, j, i) * MT(rdyc, j, i);
+      S.GY[l] = (Q[l] - Q[l - SX]) * MT(wy, j, i);
     });
   __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
+  });
+  __syncthreads();
+  // inner y-update in every column of the block and its halo
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * S.RDYd[l];
   });
   if (cc) corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
   __syncthreads();
+  // x-sweep of the plain field (x-role corners)
+  for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
+  });
+  if (dmp)
+    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.GX[l] = (Q[l] - Q[l - 1]) * MT(wx, j, i);
+    });
+  __syncthreads();
   for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
+    S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
   });
-  if (damp != R(0))
+  if (dmp)
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R lx = (Q[l + 1] - Q[l]) * MT(dy, j, i + 1) * MT(rdxc, j, i + 1) -
-                   (Q[l] - Q[l - 1]) * MT(dy, j, i) * MT(rdxc, j, i);
-      S.LAP[l] = (S.LAP[l] + lx) * MT(rarea, j, i);
+      S.LAP[l] = (S.GX[l + 1] - S.GX[l] + S.GY[l + SX] - S.GY[l]) * MT(rarea, j, i);
     });
+  __syncthreads();
+  // outer x-sweep of the y-updated field
+  for2(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.AL[l] = ppm_edge(S.QIJ[l - 2], S.QIJ[l - 1], S.QIJ[l], S.QIJ[l + 1]);
+  });
   __syncthreads();
   for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
+    const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
     FXO[l] = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
   });
   __syncthreads();
+  // inner x-update in every row of the block and its halo
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * S.RDXd[l];
   });
   __syncthreads();
+  // outer y-sweep of the x-updated field
+  for2(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.AL[l] = ppm_edge(S.QIJ[l - 2 * SX], S.QIJ[l - SX], S.QIJ[l], S.QIJ[l + SX]);
+  });
+  __syncthreads();
   for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R f = ppm_face(S.QIJ + l, SX, S.CRY[l]);
+    const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
     FYO[l] = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
   });
-  if (damp != R(0)) {
+  if (dmp)
     for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * MT(dy, j, i) * MT(rdxc, j, i);
+      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * MT(wx, j, i);
       if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
       FXO[l] = FXO[l] + f;
     });
-    __syncthreads();  // FYO of this thread's faces written above by others
+  __syncthreads();
+  if (dmp) {
     for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * MT(dx, j, i) * MT(rdyc, j, i);
+      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * MT(wy, j, i);
       if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
       FYO[l] = FYO[l] + f;
     });
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // Courant numbers and area fluxes (reading R11) into shared memory, plus the
@@ -248,17 +384,17 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
 // d_sw (reading R11): one level of a block per loop iteration
 // ------------------------------------------------------------------------
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256) k_d_sw(StepArgs<R> a, int kchunk) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R> a, int kchunk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
   R *DP = sb, *PT = sb + SA, *W = sb + 2 * SA, *U = sb + 3 * SA, *V = sb + 4 * SA;
   R *MFX = sb + 5 * SA, *MFY = sb + 6 * SA, *FXO = sb + 7 * SA, *FYO = sb + 8 * SA, *DPN = sb + 9 * SA;
-  R* KE = sb + 10 * SA;
+  R* KE = DPN;  // 1/delp_new is dead once pt and w are written
   TS<R> S;
-  S.CRX = sb + 11 * SA; S.XFX = sb + 12 * SA; S.CRY = sb + 13 * SA; S.YFX = sb + 14 * SA;
-  S.RDXd = sb + 15 * SA; S.RDYd = sb + 16 * SA; S.FY2 = sb + 17 * SA; S.FX2 = sb + 18 * SA;
-  S.QIJ = sb + 19 * SA; S.LAP = sb + 20 * SA;
+  S.CRX = sb + 10 * SA; S.XFX = sb + 11 * SA; S.CRY = sb + 12 * SA; S.YFX = sb + 13 * SA;
+  S.RDXd = sb + 14 * SA; S.RDYd = sb + 15 * SA; S.FY2 = sb + 16 * SA; S.FX2 = sb + 17 * SA;
+  S.QIJ = sb + 18 * SA; S.LAP = sb + 19 * SA; S.AL = sb + 20 * SA; S.GX = sb + 21 * SA; S.GY = sb + 22 * SA;
   (void)SY;
 
   const Item it = a.items[blockIdx.x];
@@ -302,7 +438,7 @@ __global__ void __launch_bounds__(256) k_d_sw(StepArgs<R> a, int kchunk) {
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
-      DPN[l] = d;
+      DPN[l] = R(1) / d;  // reciprocal, used by pt and w
       dpo[G(j, i)] = d;
     });
     // pt and w with the mass fluxes and mass-weighted damping
@@ -313,7 +449,7 @@ __global__ void __launch_bounds__(256) k_d_sw(StepArgs<R> a, int kchunk) {
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
-            (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) / DPN[l];
+            (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) * DPN[l];
       });
     }
     __syncthreads();
@@ -686,7 +822,7 @@ __global__ void k_halo(const HaloBatch b, const Geo* geo) {
 // tracer_2d subcycle (reading R12)
 // ------------------------------------------------------------------------
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256) k_tracer(TracerArgs<R> a, int kchunk) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerArgs<R> a, int kchunk) {
   if (a.it >= *a.nsplt) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SA = SX * (BY + 7);
@@ -696,7 +832,7 @@ __global__ void __launch_bounds__(256) k_tracer(TracerArgs<R> a, int kchunk) {
   TS<R> S;
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
   S.RDXd = sb + 11 * SA; S.RDYd = sb + 12 * SA; S.FY2 = sb + 13 * SA; S.FX2 = sb + 14 * SA;
-  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA;
+  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA; S.AL = sb + 17 * SA; S.GX = S.LAP; S.GY = S.LAP;
   const Item it = a.items[blockIdx.x];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
@@ -885,6 +1021,25 @@ static void set_smem(K kern, size_t bytes) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// block shapes compiled for the horizontal kernels (picked at run time by
+// fv3_set_tiles / fv3_autotune)
+#define FV3_DISPATCH_SHAPE(BXv, BYv, CALL) \
+  do {                                     \
+    if (BXv == 32 && BYv == 8) {           \
+      CALL(32, 8);                         \
+    } else if (BXv == 32 && BYv == 16) {   \
+      CALL(32, 16);                        \
+    } else if (BXv == 64 && BYv == 8) {    \
+      CALL(64, 8);                         \
+    } else {                               \
+      CALL(16, 16);                        \
+    }                                      \
+  } while (0)
+
+bool shape_supported(int bx, int by) {
+  return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 8) || (bx == 16 && by == 16);
+}
+
 static size_t blk_smem(const Ctx& c, int arrays) {
   return (size_t)arrays * (c.BX + 7) * (c.BY + 7) * c.esize;
 }
@@ -958,13 +1113,11 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(0)) enqueue_halo_prognostics(c, in, st);
   if (run(1)) {  // c_sw
     const size_t sm = blk_smem(c, 13);
-    if (c.BX == 32 && c.BY == 8) {
-      set_smem(k_c_sw<R, 32, 8>, sm);
-      k_c_sw<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    } else {
-      set_smem(k_c_sw<R, 32, 16>, sm);
-      k_c_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    }
+#define FV3_CSW(X, Y)                                                                  \
+  set_smem(k_c_sw<R, X, Y>, sm);                                                       \
+  k_c_sw<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+    FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_CSW);
+#undef FV3_CSW
     ++c.launches;
   }
   if (run(2)) {  // update_dz_c
@@ -992,14 +1145,12 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     enqueue_halo_fields(c, F, st);
   }
   if (run(6)) {  // d_sw
-    const size_t sm = blk_smem(c, 21);
-    if (c.BX == 32 && c.BY == 8) {
-      set_smem(k_d_sw<R, 32, 8>, sm);
-      k_d_sw<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    } else {
-      set_smem(k_d_sw<R, 32, 16>, sm);
-      k_d_sw<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    }
+    const size_t sm = blk_smem(c, 23);
+#define FV3_DSW(X, Y)                                                                  \
+  set_smem(k_d_sw<R, X, Y>, sm);                                                       \
+  k_d_sw<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+    FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
+#undef FV3_DSW
     ++c.launches;
   }
 }
@@ -1077,19 +1228,17 @@ static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
   a.dp0 = (const R*)c.dp0;
   a.dp1 = (R*)c.dp1;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
-  const size_t sm = blk_smem(c, 17);
+  const size_t sm = blk_smem(c, 18);
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
     enqueue_halo_fields(c, Q, st);
     a.it = it;
-    if (c.BX == 32 && c.BY == 8) {
-      set_smem(k_tracer<R, 32, 8>, sm);
-      k_tracer<R, 32, 8><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    } else {
-      set_smem(k_tracer<R, 32, 16>, sm);
-      k_tracer<R, 32, 16><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk);
-    }
+#define FV3_TRC(X, Y)                                                                  \
+  set_smem(k_tracer<R, X, Y>, sm);                                                     \
+  k_tracer<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+    FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TRC);
+#undef FV3_TRC
     ++c.launches;
     std::vector<std::pair<void*, const void*>> pairs;
     for (int q = 0; q < s.nq; ++q) pairs.push_back({s.q[q], c.qtmp[q]});

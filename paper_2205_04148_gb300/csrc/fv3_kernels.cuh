@@ -144,6 +144,7 @@ void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStrea
 void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cudaStream_t st);
 void enqueue_zero_acc(Ctx& c, cudaStream_t st);
 void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st);
+bool shape_supported(int bx, int by);
 // calibration kernels (fv3_calib.cu): returns work per launch (flops or bytes)
 double enqueue_calibration(Ctx& c, int what, cudaStream_t st);
 

@@ -28,7 +28,8 @@ HALO_WIND, HALO_W, HALO_DELP, HALO_PT, HALO_DELZ, HALO_TRACERS = 1, 2, 4, 8, 16,
 SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", "fv3_elem_size",
            "fv3_get_layout", "fv3_import", "fv3_export", "fv3_halo_fill", "fv3_acoustic_substep",
            "fv3_run_dyn", "fv3_mass_sum", "fv3_check_status", "fv3_get_metric", "fv3_stage",
-           "fv3_get_intermediate")
+           "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
+           "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc")
 
 
 class GridDesc(C.Structure):
@@ -102,6 +103,20 @@ def load(path=LIB_PATH):
     L.fv3_stage.argtypes = [vp, C.POINTER(State), C.POINTER(Params), i, vp]
     L.fv3_get_intermediate.restype = st
     L.fv3_get_intermediate.argtypes = [vp, C.c_char_p, i, C.POINTER(d), vp]
+    L.fv3_launch_stage.restype = st
+    L.fv3_launch_stage.argtypes = [vp, C.POINTER(State), C.POINTER(Params), i, i, vp]
+    L.fv3_kernel_launches.restype = C.c_longlong
+    L.fv3_kernel_launches.argtypes = [vp]
+    L.fv3_calibrate.restype = st
+    L.fv3_calibrate.argtypes = [vp, i, vp, C.POINTER(d)]
+    L.fv3_set_tiles.restype = st
+    L.fv3_set_tiles.argtypes = [vp, i, i, i]
+    L.fv3_get_tiles.restype = st
+    L.fv3_get_tiles.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+    L.fv3_autotune.restype = st
+    L.fv3_autotune.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp, C.POINTER(d)]
+    L.fv3_riem_solver_c_noalloc.restype = st
+    L.fv3_riem_solver_c_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, C.POINTER(Params), vp]
     _lib = L
     return L
 
@@ -279,6 +294,21 @@ class Grid:
         out = (C.c_double * self.n_members)()
         self.check(self.L.fv3_mass_sum(self.ptr, C.byref(s), out, _stream(stream)))
         return np.array(out[:])
+
+    def set_tiles(self, bx, by, kchunk):
+        self.check(self.L.fv3_set_tiles(self.ptr, bx, by, kchunk))
+
+    def tiles(self):
+        bx, by, kc = C.c_int(), C.c_int(), C.c_int()
+        self.check(self.L.fv3_get_tiles(self.ptr, C.byref(bx), C.byref(by), C.byref(kc)))
+        return bx.value, by.value, kc.value
+
+    def autotune(self, st, prm=None, stream=None):
+        s = self.cstate(st)
+        prm = prm or params()
+        best = C.c_double()
+        self.check(self.L.fv3_autotune(self.ptr, C.byref(s), C.byref(prm), _stream(stream), C.byref(best)))
+        return self.tiles(), best.value
 
     def check_status(self, stream=None):
         return self.L.fv3_check_status(self.ptr, _stream(stream))

@@ -208,3 +208,30 @@ def test_invalid_arguments_rejected():
         g.substep(gs, fv3.params(dt=-1.0))
     with pytest.raises(fv3.Fv3Error):
         fv3.Grid(fv3.GRID_CUBED, 4, 2)   # npx < 8
+
+
+@pytest.mark.parametrize("shape", [(32, 8, 5), (32, 16, 4), (64, 8, 1), (16, 16, 3)])
+def test_block_shapes(orc, shape):
+    """every compiled block shape and level chunk gives the same substep"""
+    g, gs, d, s, st = pair(orc, True, 40, 5, seed=23)
+    g.set_tiles(*shape)
+    assert g.tiles() == shape
+    g.substep(gs)
+    s.substep()
+    for f in FIELDS:
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= TOL64, (shape, f, e)
+
+
+def test_autotune_keeps_parity(orc):
+    from paper_2205_04148_gb300 import fv3
+    g, gs, d, s, st = pair(orc, True, 24, 6, seed=29, nq=1)
+    (bx, by, kc), best = g.autotune(gs)
+    assert (bx, by) in ((32, 8), (32, 16), (64, 8), (16, 16)) and 1 <= kc <= 6 and best > 0
+    g.load(gs, st)           # autotune ran stages on the state's halos only; reload anyway
+    prm_g, prm_o = fv3.params(n_split=2), orc.params(n_split=2)
+    g.run_dyn(gs, prm_g, 1)
+    s.run_dyn(prm_o, 1)
+    for f in FIELDS + ("q0",):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 3 * TOL64, (f, e)
