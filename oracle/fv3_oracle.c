@@ -63,8 +63,10 @@ typedef struct {
 
 typedef struct {
   double dt;
-  int n_split, nord, hord;
+  int n_split, nord, hord; /* hord 0: monotone PPM; 1: learned face values (R14) */
   double d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air;
+  const double* mlp;       /* 1313 network parameters (hord 1) */
+  int mlp_bf16;            /* 1: inference with bfloat16 inputs/weights, float sums */
 } OParams;
 
 typedef struct {
@@ -657,6 +659,170 @@ static double ppm_face(const double* q, long s, double c) {
 double orc_ppm_face(const double* q6, double c) { return ppm_face(q6 + 3, 1, c); }
 
 /* ------------------------------------------------------------------ */
+/* learned edge value (reading R14; no counterpart in the paper, which */
+/* motivates machine-learned components in Section III-B)              */
+/* ------------------------------------------------------------------ */
+/* Parameters, flat (1313 values): W1[6][32] (input i -> hidden j at i*32+j),
+   b1[32], W2[32][32], b2[32], W3[32], b3.  Network: h1 = tanh(x W1 + b1),
+   h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, on the six cell means normalised by
+   their mean mu and standard deviation sigma; edge value = mu + sigma * y. */
+#define MLP_NP 1313
+#define MLP_W1 0
+#define MLP_B1 192
+#define MLP_W2 224
+#define MLP_B2 1248
+#define MLP_W3 1280
+#define MLP_B3 1312
+
+/* round-to-nearest-even to bfloat16, kept as a float */
+static float bf16r(float f) {
+  union { float f; uint32_t u; } v;
+  v.f = f;
+  uint32_t lsb = (v.u >> 16) & 1u;
+  v.u += 0x7fffu + lsb;
+  v.u &= 0xffff0000u;
+  return v.f;
+}
+
+static void mlp_normalise(const double* q6, double* mu, double* sig, double* x) {
+  double m = 0.0;
+  for (int i = 0; i < 6; i++) m += q6[i];
+  m /= 6.0;
+  double v = 0.0;
+  for (int i = 0; i < 6; i++) v += (q6[i] - m) * (q6[i] - m);
+  double sd = sqrt(v / 6.0);
+  double eps = 1e-12 * fabs(m) + 1e-300;
+  for (int i = 0; i < 6; i++) x[i] = (q6[i] - m) / (sd + eps);
+  *mu = m;
+  *sig = sd;
+}
+
+/* FP64 forward; h1, h2 (32 each) returned for the backward pass */
+double orc_mlp_forward(const double* w, const double* x, double* h1, double* h2) {
+  for (int j = 0; j < 32; j++) {
+    double a = w[MLP_B1 + j];
+    for (int i = 0; i < 6; i++) a += x[i] * w[MLP_W1 + i * 32 + j];
+    h1[j] = tanh(a);
+  }
+  for (int j = 0; j < 32; j++) {
+    double a = w[MLP_B2 + j];
+    for (int i = 0; i < 32; i++) a += h1[i] * w[MLP_W2 + i * 32 + j];
+    h2[j] = tanh(a);
+  }
+  double y = w[MLP_B3];
+  for (int i = 0; i < 32; i++) y += h2[i] * w[MLP_W3 + i];
+  return y;
+}
+
+/* gradient of 0.5 * (y - t)^2 * wt with respect to the parameters, added to g */
+double orc_mlp_backward(const double* w, const double* x, double t, double wt, double* g) {
+  double h1[32], h2[32], d2[32], d1[32];
+  double y = orc_mlp_forward(w, x, h1, h2);
+  double dy = (y - t) * wt;
+  g[MLP_B3] += dy;
+  for (int i = 0; i < 32; i++) {
+    g[MLP_W3 + i] += h2[i] * dy;
+    d2[i] = dy * w[MLP_W3 + i] * (1.0 - h2[i] * h2[i]);
+  }
+  for (int j = 0; j < 32; j++) {
+    g[MLP_B2 + j] += d2[j];
+    for (int i = 0; i < 32; i++) g[MLP_W2 + i * 32 + j] += h1[i] * d2[j];
+  }
+  for (int i = 0; i < 32; i++) {
+    double a = 0.0;
+    for (int j = 0; j < 32; j++) a += w[MLP_W2 + i * 32 + j] * d2[j];
+    d1[i] = a * (1.0 - h1[i] * h1[i]);
+  }
+  for (int j = 0; j < 32; j++) {
+    g[MLP_B1 + j] += d1[j];
+    for (int i = 0; i < 6; i++) g[MLP_W1 + i * 32 + j] += x[i] * d1[j];
+  }
+  return 0.5 * (y - t) * (y - t) * wt;
+}
+
+/* the mirror-symmetric network ys(x) = (y(x) + y(reversed x)) / 2 that the
+   learned face value uses: loss 0.5 (ys - t)^2 wt, gradient added to g */
+double orc_mlp_sym_backward(const double* w, const double* x, double t, double wt, double* g) {
+  double xr[6], h1[32], h2[32];
+  for (int i = 0; i < 6; i++) xr[i] = x[5 - i];
+  double ys = 0.5 * (orc_mlp_forward(w, x, h1, h2) + orc_mlp_forward(w, xr, h1, h2));
+  double dy = (ys - t) * wt;
+  /* d ys / d w = (dy(x) + dy(xr)) / 2: back-propagate each orientation with
+     target chosen so that its (y - t') equals dy / 2 per unit weight */
+  double y1 = orc_mlp_forward(w, x, h1, h2);
+  double y2 = orc_mlp_forward(w, xr, h1, h2);
+  orc_mlp_backward(w, x, y1 - 0.5 * dy, 1.0, g);
+  orc_mlp_backward(w, xr, y2 - 0.5 * dy, 1.0, g);
+  return 0.5 * (ys - t) * (ys - t) * wt;
+}
+
+double orc_mlp_sym_forward(const double* w, const double* x) {
+  double xr[6], h1[32], h2[32];
+  for (int i = 0; i < 6; i++) xr[i] = x[5 - i];
+  return 0.5 * (orc_mlp_forward(w, x, h1, h2) + orc_mlp_forward(w, xr, h1, h2));
+}
+
+/* inference as the tensor-core path computes it: inputs and weights rounded
+   to bfloat16, products accumulated in float, tanh in float, hidden
+   activations rounded to bfloat16 before the next layer */
+double orc_mlp_forward_bf16(const double* w, const double* x) {
+  float xb[6], h1[32], h2[32];
+  for (int i = 0; i < 6; i++) xb[i] = bf16r((float)x[i]);
+  for (int j = 0; j < 32; j++) {
+    float a = 0.0f;
+    for (int i = 0; i < 6; i++) a += xb[i] * bf16r((float)w[MLP_W1 + i * 32 + j]);
+    h1[j] = bf16r(tanhf(a + (float)w[MLP_B1 + j]));
+  }
+  for (int j = 0; j < 32; j++) {
+    float a = 0.0f;
+    for (int i = 0; i < 32; i++) a += h1[i] * bf16r((float)w[MLP_W2 + i * 32 + j]);
+    h2[j] = bf16r(tanhf(a + (float)w[MLP_B2 + j]));
+  }
+  float y = 0.0f;
+  for (int i = 0; i < 32; i++) y += h2[i] * bf16r((float)w[MLP_W3 + i]);
+  return (double)(y + (float)w[MLP_B3]);
+}
+
+/* learned face value at the face between q6[2] and q6[3] (cells q_{i-3..i+2}
+   of the PPM face-value stencil), with the plain PPM face value as the
+   fallback when the network leaves the range of the two cells or, for a
+   positive field, goes negative */
+static double learned_value(const double* mlp, int bf16, const double* q6, int positive, double plain) {
+  double mu, sig, x[6], xr[6], h1[32], h2[32];
+  mlp_normalise(q6, &mu, &sig, x);
+  for (int i = 0; i < 6; i++) xr[i] = x[5 - i];
+  /* mirror-symmetric evaluation: the two tiles that share a cube edge see
+     the stencil in opposite orders and must compute the same flux */
+  double y1 = bf16 ? orc_mlp_forward_bf16(mlp, x) : orc_mlp_forward(mlp, x, h1, h2);
+  double y2 = bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2);
+  double y = 0.5 * (y1 + y2);
+  double a = mu + sig * y;
+  double lo = fmin(q6[2], q6[3]), hi = fmax(q6[2], q6[3]);
+  if (!(a >= lo && a <= hi)) return plain;
+  if (positive && a < 0.0) return plain;
+  return a;
+}
+
+/* the learned context of one fv_tp_2d call (NULL: plain PPM) */
+typedef struct {
+  const double* w;
+  int bf16, positive;
+} Learn;
+
+/* face value, learned where the context asks for it (reading R14) */
+static double ppm_face_l(const double* q, long s, double c, const Learn* L) {
+  double plain = ppm_face(q, s, c);
+  if (!L) return plain;
+  double q6[6];
+  for (int i = 0; i < 6; i++) q6[i] = q[(i - 3) * s];
+  return learned_value(L->w, L->bf16, q6, L->positive, plain);
+}
+
+double orc_learned_face(const double* mlp, int bf16, const double* q6, double c, int positive) {
+  return learned_value(mlp, bf16, q6, positive, ppm_face(q6 + 3, 1, c));
+}
+
+/* ------------------------------------------------------------------ */
 /* fv_tp_2d (Section IX-C; reading R5: Lin-Rood split, averaged orders) */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -682,7 +848,7 @@ static void work_free(Work* w) {
  */
 static void fv_tp_2d_plane(const ODom* d, int t, const double* q, const double* crx, const double* cry,
                            const double* xfx, const double* yfx, const double* mfx, const double* mfy, double* Fx,
-                           double* Fy, Work* w) {
+                           double* Fy, Work* w, const Learn* L) {
   int n = d->n;
   const double* area = d->area + t * d->pc;
   long sc = d->wc;
@@ -692,7 +858,7 @@ static void fv_tp_2d_plane(const ODom* d, int t, const double* q, const double* 
   copy_corners(d, w->qy, 1);
   /* 1. y-sweep on the plain field; inner y-update in every column */
   for (int j = 0; j <= n; j++)
-    for (int i = -H; i < n + H; i++) w->fy2[IY(d, j, i)] = ppm_face(&w->qy[IC(d, j, i)], sc, cry[IY(d, j, i)]);
+    for (int i = -H; i < n + H; i++) w->fy2[IY(d, j, i)] = ppm_face_l(&w->qy[IC(d, j, i)], sc, cry[IY(d, j, i)], L);
   for (int j = 0; j < n; j++)
     for (int i = -H; i < n + H; i++) {
       long c = IC(d, j, i);
@@ -703,10 +869,10 @@ static void fv_tp_2d_plane(const ODom* d, int t, const double* q, const double* 
     }
   /* 2. outer x-sweep of the y-updated field */
   for (int j = 0; j < n; j++)
-    for (int i = 0; i <= n; i++) w->fx[IX(d, j, i)] = ppm_face(&w->qi[IC(d, j, i)], 1, crx[IX(d, j, i)]);
+    for (int i = 0; i <= n; i++) w->fx[IX(d, j, i)] = ppm_face_l(&w->qi[IC(d, j, i)], 1, crx[IX(d, j, i)], L);
   /* 3. x-sweep on the plain field; inner x-update in every row */
   for (int j = -H; j < n + H; j++)
-    for (int i = 0; i <= n; i++) w->fx2[IX(d, j, i)] = ppm_face(&w->qx[IC(d, j, i)], 1, crx[IX(d, j, i)]);
+    for (int i = 0; i <= n; i++) w->fx2[IX(d, j, i)] = ppm_face_l(&w->qx[IC(d, j, i)], 1, crx[IX(d, j, i)], L);
   for (int j = -H; j < n + H; j++)
     for (int i = 0; i < n; i++) {
       long c = IC(d, j, i);
@@ -717,7 +883,7 @@ static void fv_tp_2d_plane(const ODom* d, int t, const double* q, const double* 
     }
   /* 4. outer y-sweep of the x-updated field */
   for (int j = 0; j <= n; j++)
-    for (int i = 0; i < n; i++) w->fy[IY(d, j, i)] = ppm_face(&w->qj[IC(d, j, i)], sc, cry[IY(d, j, i)]);
+    for (int i = 0; i < n; i++) w->fy[IY(d, j, i)] = ppm_face_l(&w->qj[IC(d, j, i)], sc, cry[IY(d, j, i)], L);
   /* 5. average of both orders times the mass (or area) flux */
   for (int j = 0; j < n; j++)
     for (int i = 0; i <= n; i++) {
@@ -1217,7 +1383,9 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
           cry[o] = dt * vt[o] * siny[o] * rdyc[o];
         }
       /* 2. mass: transport + damping -> mass fluxes, new delp */
-      fv_tp_2d_plane(d, t, delp, crx, cry, xfx, yfx, NULL, NULL, mfx, mfy, &w);
+      Learn Ld = {P->mlp, P->mlp_bf16, 1};
+      const Learn* Lp = (P->hord == 1 && P->mlp) ? &Ld : NULL;
+      fv_tp_2d_plane(d, t, delp, crx, cry, xfx, yfx, NULL, NULL, mfx, mfy, &w, Lp);
       delnflux_plane(d, t, delp, damp, NULL, mfx, mfy, &w);
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
@@ -1229,7 +1397,7 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
       for (int fld = 0; fld < 2; fld++) {
         const double* q = fld == 0 ? pt : wv;
         double* qn = fld == 0 ? pt_n : w_n;
-        fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w);
+        fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w, fld == 0 ? Lp : NULL);
         delnflux_plane(d, t, q, damp, delp, Fx, Fy, &w);
         for (int j = 0; j < n; j++)
           for (int i = 0; i < n; i++) {
@@ -1258,7 +1426,7 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
                                v[IX(d, j, i + 1)] * dy[IX(d, j, i + 1)] - v[IX(d, j, i)] * dy[IX(d, j, i)]) *
                                   rarea[IC(d, j, i)] + fA[IC(d, j, i)];
         }
-      fv_tp_2d_plane(d, t, vort, crx, cry, xfx, yfx, NULL, NULL, Fx, Fy, &w);
+      fv_tp_2d_plane(d, t, vort, crx, cry, xfx, yfx, NULL, NULL, Fx, Fy, &w, NULL);
       delnflux_plane(d, t, vort, damp, NULL, Fx, Fy, &w);
       /* 6. new D-grid winds: vorticity flux plus kinetic-energy gradient */
       for (int j = 0; j <= n; j++)
@@ -1339,7 +1507,7 @@ int orc_substep(OState* s, const OParams* P, int stop_after, int accumulate) {
 /* ------------------------------------------------------------------ */
 /* tracer_2d (reading R12) and the remapping-step driver               */
 /* ------------------------------------------------------------------ */
-static void tracer_2d(OState* s, const double* dp_start) {
+static void tracer_2d(OState* s, const double* dp_start, const OParams* P) {
   ODom* d = s->d;
   int n = d->n, nz = d->nz;
   fill_faces(d, s->amfx, s->amfy, nz, H, 2, 0);
@@ -1383,7 +1551,8 @@ static void tracer_2d(OState* s, const double* dp_start) {
           }
         for (int m = 0; m < s->nq; m++) {
           double* q = s->q[m] + oc;
-          fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w);
+          Learn Lq = {P->mlp, P->mlp_bf16, 1};
+          fv_tp_2d_plane(d, t, q, crx, cry, xfx, yfx, mfx, mfy, Fx, Fy, &w, (P->hord == 1 && P->mlp) ? &Lq : NULL);
           for (int j = 0; j < n; j++)
             for (int i = 0; i < n; i++) {
               long c = IC(d, j, i);
@@ -1412,7 +1581,7 @@ int orc_run_dyn(OState* s, const OParams* P, int n_steps) {
     memset(s->axfx, 0, sizeof(double) * nx); memset(s->amfy, 0, sizeof(double) * ny);
     memset(s->acry, 0, sizeof(double) * ny); memset(s->ayfx, 0, sizeof(double) * ny);
     for (int it = 0; it < P->n_split; it++) orc_substep(s, P, -1, 1);
-    if (s->nq > 0) tracer_2d(s, dp_start);
+    if (s->nq > 0) tracer_2d(s, dp_start, P);
   }
   free(dp_start);
   return 0;
@@ -1467,7 +1636,7 @@ int orc_fv_tp_2d_dense(ODom* d, int t, const double* q, const double* crx, const
   fill_faces(d, XF, YF, 1, H, 2, 0);
   Work w = work_new(d);
   fv_tp_2d_plane(d, t, Q + t * d->pc, CX + t * d->px, CY + t * d->py, XF + t * d->px, YF + t * d->py, NULL, NULL,
-                 Fx, Fy, &w);
+                 Fx, Fy, &w, NULL);
   for (int j = 0; j < n; j++)
     for (int i = 0; i <= n; i++) Fx_out[(long)j * (n + 1) + i] = Fx[IX(d, j, i)];
   for (int j = 0; j <= n; j++)

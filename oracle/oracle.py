@@ -35,7 +35,7 @@ class OParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double),
                 ("ptop", C.c_double), ("grav", C.c_double), ("rdgas", C.c_double),
-                ("cp_air", C.c_double)]
+                ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int)]
 
 
 def _load():
@@ -76,6 +76,18 @@ def _load():
     L.orc_copy_corners.argtypes = [vp, dp, C.c_int]
     L.orc_plane_sizes.argtypes = [vp, C.POINTER(C.c_long)]
     L.orc_gpoint.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp]
+    L.orc_mlp_forward.restype = C.c_double
+    L.orc_mlp_forward.argtypes = [dp, dp, dp, dp]
+    L.orc_mlp_backward.restype = C.c_double
+    L.orc_mlp_backward.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+    L.orc_mlp_forward_bf16.restype = C.c_double
+    L.orc_mlp_forward_bf16.argtypes = [dp, dp]
+    L.orc_mlp_sym_backward.restype = C.c_double
+    L.orc_mlp_sym_backward.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+    L.orc_mlp_sym_forward.restype = C.c_double
+    L.orc_mlp_sym_forward.argtypes = [dp, dp]
+    L.orc_learned_face.restype = C.c_double
+    L.orc_learned_face.argtypes = [dp, C.c_int, dp, C.c_double, C.c_int]
     _lib = L
     return L
 
@@ -88,12 +100,19 @@ def _c(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def params(**kw):
+def params(mlp=None, mlp_bf16=0, **kw):
+    """Substep parameters; ``mlp`` (1313 network parameters) with hord=1 selects
+    the learned face values."""
     from paper_2205_04148_gb300.inputs import default_params
     p = default_params()
     p.update(kw)
-    return OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
-                   p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"])
+    prm = OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
+                  p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16))
+    if mlp is not None:
+        w = _c(mlp)
+        prm._w = w
+        prm.mlp = _p(w)
+    return prm
 
 
 class Domain:
@@ -302,3 +321,75 @@ def copy_corners(dom: Domain, q, direction):
     q = _c(q)
     L.orc_copy_corners(dom.ptr, _p(q), direction)
     return q
+
+
+MLP_NP = 1313
+
+
+def mlp_init(seed=0, scale=1.0):
+    """Random network parameters (flat, 1313 values), Glorot-style scale."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(MLP_NP)
+    w[0:192] = rng.standard_normal(192) * scale * np.sqrt(2.0 / (6 + 32))
+    w[224:1248] = rng.standard_normal(1024) * scale * np.sqrt(2.0 / 64)
+    w[1280:1312] = rng.standard_normal(32) * scale * np.sqrt(2.0 / 33)
+    return w
+
+
+def mlp_forward(w, x):
+    L = _load()
+    w, x = _c(w), _c(x)
+    h1, h2 = np.empty(32), np.empty(32)
+    return L.orc_mlp_forward(_p(w), _p(x), _p(h1), _p(h2))
+
+
+def mlp_forward_bf16(w, x):
+    L = _load()
+    w, x = _c(w), _c(x)
+    return L.orc_mlp_forward_bf16(_p(w), _p(x))
+
+
+def mlp_grad(w, X, T, wt=None):
+    """Loss sum 0.5 (y - t)^2 wt and its gradient over samples X [F, 6], T [F]."""
+    L = _load()
+    w = _c(w)
+    g = np.zeros(MLP_NP)
+    loss = 0.0
+    X = _c(X)
+    for f in range(len(T)):
+        x = np.ascontiguousarray(X[f])
+        loss += L.orc_mlp_backward(_p(w), _p(x), float(T[f]), 1.0 if wt is None else float(wt), _p(g))
+    return loss, g
+
+
+def mlp_sym_grad(w, X, T, wt=1.0):
+    """Loss sum 0.5 (ys - t)^2 wt of the mirror-symmetric network and its gradient."""
+    L = _load()
+    w = _c(w)
+    g = np.zeros(MLP_NP)
+    loss = 0.0
+    X = _c(X)
+    for f in range(len(T)):
+        x = np.ascontiguousarray(X[f])
+        loss += L.orc_mlp_sym_backward(_p(w), _p(x), float(T[f]), float(wt), _p(g))
+    return loss, g
+
+
+def mlp_sym_forward(w, X):
+    L = _load()
+    w, X = _c(w), _c(X)
+    return np.array([L.orc_mlp_sym_forward(_p(w), _p(np.ascontiguousarray(x))) for x in X])
+
+
+def learned_face(w, q6, c, positive=1, bf16=0):
+    L = _load()
+    w, q6 = _c(w), _c(q6)
+    return L.orc_learned_face(_p(w), int(bf16), _p(q6), float(c), int(positive))
+
+
+def mlp_normalise(q6):
+    q6 = np.asarray(q6, dtype=np.float64)
+    mu = q6.mean(axis=-1, keepdims=True)
+    sd = np.sqrt(((q6 - mu) ** 2).mean(axis=-1, keepdims=True))
+    eps = 1e-12 * np.abs(mu) + 1e-300
+    return (q6 - mu) / (sd + eps), mu[..., 0], sd[..., 0]
