@@ -684,12 +684,13 @@ static float bf16r(float f) {
   return v.f;
 }
 
+/* mean and standard deviation of the six cells, summed in mirror pairs so
+   that the reversed stencil gives the same bits */
 static void mlp_normalise(const double* q6, double* mu, double* sig, double* x) {
-  double m = 0.0;
-  for (int i = 0; i < 6; i++) m += q6[i];
-  m /= 6.0;
-  double v = 0.0;
-  for (int i = 0; i < 6; i++) v += (q6[i] - m) * (q6[i] - m);
+  double m = ((q6[0] + q6[5]) + (q6[1] + q6[4]) + (q6[2] + q6[3])) / 6.0;
+  double d[6];
+  for (int i = 0; i < 6; i++) d[i] = (q6[i] - m) * (q6[i] - m);
+  double v = (d[0] + d[5]) + (d[1] + d[4]) + (d[2] + d[3]);
   double sd = sqrt(v / 6.0);
   double eps = 1e-12 * fabs(m) + 1e-300;
   for (int i = 0; i < 6; i++) x[i] = (q6[i] - m) / (sd + eps);

@@ -388,8 +388,12 @@ def learned_face(w, q6, c, positive=1, bf16=0):
 
 
 def mlp_normalise(q6):
-    q6 = np.asarray(q6, dtype=np.float64)
-    mu = q6.mean(axis=-1, keepdims=True)
-    sd = np.sqrt(((q6 - mu) ** 2).mean(axis=-1, keepdims=True))
+    """inputs of the network: the six cells minus their mean over their standard
+    deviation (mirror-pair sums, as in the C oracle)"""
+    q = np.asarray(q6, dtype=np.float64)
+    mu = ((q[..., 0] + q[..., 5]) + (q[..., 1] + q[..., 4]) + (q[..., 2] + q[..., 3])) / 6.0
+    d = (q - mu[..., None]) ** 2
+    v = (d[..., 0] + d[..., 5]) + (d[..., 1] + d[..., 4]) + (d[..., 2] + d[..., 3])
+    sd = np.sqrt(v / 6.0)
     eps = 1e-12 * np.abs(mu) + 1e-300
-    return (q6 - mu) / (sd + eps), mu[..., 0], sd[..., 0]
+    return (q - mu[..., None]) / (sd + eps)[..., None], mu, sd
