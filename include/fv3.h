@@ -102,12 +102,13 @@ typedef struct {
   double dt;     /* acoustic substep (s) */
   int n_split;   /* substeps per remapping step (fv3_run_dyn) */
   int nord;      /* damping order: 1 (del-4) */
-  int hord;      /* edge reconstruction: 0 monotone PPM */
+  int hord;      /* face values: 0 monotone PPM; 1 learned network for delp, pt and tracers */
   double d4_bg;  /* damping coefficient (0.12) */
   double a_imp;  /* implicit weight of the column solve (1 = fully implicit) */
   double dz_min; /* minimum layer thickness (m) */
   double ptop;   /* model-top pressure (Pa) */
   double grav, rdgas, cp_air;
+  const void* mlp; /* hord 1: device float[1313] network parameters (see fv3_mlp_forward) */
 } fv3_params;
 
 typedef struct {
@@ -222,6 +223,29 @@ fv3_status fv3_get_tiles(const fv3_ctx* ctx, int* bx, int* by, int* kchunk);
  * time per (c_sw + d_sw) in *best_ms (may be NULL).  Synchronises `stream`. */
 fv3_status fv3_autotune(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream,
                         double* best_ms);
+
+/* ---- learned face values (reading R14; the paper has no learned part) ----
+ * Network: 6 -> 32 -> 32 -> 1 with tanh, parameters float[1313] on the device
+ * (W1[6][32] at 0, b1 at 192, W2[32][32] at 224, b2 at 1248, W3[32] at 1280,
+ * b3 at 1312).  Inputs per face: the six cells of the PPM face stencil minus
+ * their mean, over their standard deviation.  Tensor-core evaluation
+ * (bfloat16 operands, float accumulation, hardware tanh). */
+
+/* y[n] = network(x[n][6]); symmetric != 0 averages x and the reversed x. */
+fv3_status fv3_mlp_forward(const float* w, const float* x, int n, int symmetric, float* y, fv3_stream stream);
+
+/* Floats of workspace fv3_mlp_grad needs for n samples. */
+size_t fv3_mlp_work_floats(int n);
+
+/* grad[1313] = d/dw sum_s 0.5 * weight * (ys(x_s) - t_s)^2 with the
+ * mirror-symmetric network ys; *loss receives the sum (device pointers;
+ * loss may be NULL).  Deterministic (fixed-order reduction). */
+fv3_status fv3_mlp_grad(const float* w, const float* x, const float* t, int n, float weight, float* work,
+                        float* grad, float* loss, fv3_stream stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected, step >= 1) on
+ * float master weights w with moments m, v. */
+fv3_status fv3_mlp_adam(float* w, float* m, float* v, const float* grad, int step, float lr, fv3_stream stream);
 
 /* Column solve of riem_solver_c for callers that cannot allocate device
  * memory (no counterpart in the paper).  Code that runs under a fixed,

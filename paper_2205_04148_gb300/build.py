@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfv3.so")
-SOURCES = ["fv3_grid.cpp", "fv3_kernels.cu", "fv3_capi.cu", "fv3_calib.cu", "fv3_noalloc.cu"]
+SOURCES = ["fv3_grid.cpp", "fv3_kernels.cu", "fv3_capi.cu", "fv3_calib.cu", "fv3_noalloc.cu", "fv3_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

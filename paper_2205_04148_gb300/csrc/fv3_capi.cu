@@ -87,7 +87,8 @@ fv3_status check_params(fv3_ctx* x, const fv3_params* p) {
   if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(x, FV3_ERR_ARG, "dt must be positive");
   if (p->n_split < 1) return fail(x, FV3_ERR_ARG, "n_split must be >= 1");
   if (p->nord != 1) return fail(x, FV3_ERR_UNSUPPORTED, "only nord = 1 (del-4 damping) is built");
-  if (p->hord != 0) return fail(x, FV3_ERR_UNSUPPORTED, "only hord = 0 (monotone PPM) is built");
+  if (p->hord != 0 && p->hord != 1) return fail(x, FV3_ERR_UNSUPPORTED, "hord must be 0 (PPM) or 1 (learned)");
+  if (p->hord == 1 && !p->mlp) return fail(x, FV3_ERR_ARG, "hord = 1 needs the network parameters (mlp)");
   if (!(p->a_imp > 0) || !(p->grav > 0) || !(p->rdgas > 0) || !(p->cp_air > p->rdgas) || !(p->ptop > 0) ||
       !(p->dz_min >= 0) || !(p->d4_bg >= 0))
     return fail(x, FV3_ERR_ARG, "physical constant out of range");
@@ -107,6 +108,7 @@ Params to_params(const fv3_params* p) {
   P.dt = p->dt; P.d4_bg = p->d4_bg; P.a_imp = p->a_imp; P.dz_min = p->dz_min; P.ptop = p->ptop;
   P.grav = p->grav; P.rdgas = p->rdgas; P.cp_air = p->cp_air;
   P.n_split = p->n_split; P.nord = p->nord; P.hord = p->hord;
+  P.mlp = (const float*)p->mlp;
   return P;
 }
 
@@ -464,7 +466,7 @@ static void enqueue_remap_step(Ctx& c, const StateView& in, const Params& P, cud
     enqueue_substep(c, even ? in : nx, even ? nx : in, P, true, st);
   }
   if (P.n_split % 2 == 1) enqueue_copy_state(c, in, nx, st);
-  enqueue_tracers(c, in, st);
+  enqueue_tracers(c, in, P, st);
 }
 
 extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_params* p, int n_steps,

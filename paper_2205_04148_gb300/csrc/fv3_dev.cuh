@@ -50,6 +50,7 @@ struct Metric {
 struct Params {
   double dt, d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air;
   int n_split, nord, hord, pad;
+  const float* mlp;  // face-value network parameters (hord 1)
 };
 
 // halo-plan entry: destination slot <- sign * source value (sign 0: NaN)

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "fv3_kernels.cuh"
+#include "fv3_mlp.cuh"
 
 namespace fv3 {
 
@@ -241,17 +242,53 @@ __device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, 
   return qu + (R(1) - ac) * (x - ac * (bl + br));
 }
 
+// Learned face values (reading R14) over a 2-D range of faces with stride s
+// along the sweep: the mirror-symmetric network value mu + sigma * y, or the
+// plain PPM value where it leaves the range of the two cells or is negative
+// (every learned field is positive).  All lanes of a warp take part in the
+// tensor-core evaluation; padding lanes repeat a valid face and do not store.
+template <typename R>
+__device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int ilo, int ihi, int jlo, int jhi,
+                              int s, const Blk& B, const MlpFrag& F) {
+  const int w = ihi - ilo, total = w * (jhi - jlo);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int warp = tid >> 5, nwarps = (blockDim.x * blockDim.y) >> 5, lane = tid & 31;
+  for (int base = warp * 32; base < total; base += nwarps * 32) {
+    const int e = base + lane;
+    const bool valid = e < total;
+    const int ee = valid ? e : base;
+    const int i = ilo + ee % w, j = jlo + ee / w;
+    const int l = B.L(i, j);
+    const R plain = ppm_face_al(Q, AL, l, s, CC[l]);
+    R q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = Q[l + (k - 3) * s];
+    R mu, sd;
+    float x[6], xr[6];
+    mlp_inputs(q, mu, sd, x, xr);
+    const float y1 = mlp_warp(F, x);
+    const float y2 = mlp_warp(F, xr);
+    const R ys = (R)(0.5f * (y1 + y2));
+    const R a = mu + sd * ys;
+    const R lo = q[2] < q[3] ? q[2] : q[3], hi = q[2] < q[3] ? q[3] : q[2];
+    const R res = (a >= lo && a <= hi && a >= R(0)) ? a : plain;
+    if (valid) OUT[l] = res;
+  }
+}
+
 // fv_tp_2d (reading R5) + optional delnflux (R6) of the shared-memory scalar
 // Q on the block: fluxes on x-faces [x0, x1] x [y0, y1) -> FXO and y-faces
 // [x0, x1) x [y0, y1] -> FYO.  mfx/mfy: mass fluxes (null: area fluxes).
 // damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
 // Every PPM sweep first computes each edge value once (AL), then the face
 // values; the Laplacian of the damping is the divergence of face gradients.
-template <typename R>
+template <typename R, bool LEARN = false>
 __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, int n, bool cc, const R* mfx,
-                          const R* mfy, R damp, const R* wdp, R* FXO, R* FYO) {
+                          const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   const bool dmp = damp != R(0);
+  MlpFrag F;
+  if (LEARN) mlp_load(mlp, F);
   __syncthreads();  // Q (and the strips the corner turn reads) complete
   if (cc) corner_roles(Q, B, n, 1);
   __syncthreads();
@@ -266,10 +303,13 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
       S.GY[l] = (Q[l] - Q[l - SX]) * MT(wy, j, i);
     });
   __syncthreads();
-  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
-    const int l = B.L(i, j);
-    S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
-  });
+  if (LEARN)
+    learned_faces(Q, S.AL, S.CRY, S.FY2, x0 - 3, x1 + 3, y0, y1 + 1, SX, B, F);
+  else
+    for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
+    });
   __syncthreads();
   // inner y-update in every column of the block and its halo
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
@@ -289,10 +329,13 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
       S.GX[l] = (Q[l] - Q[l - 1]) * MT(wx, j, i);
     });
   __syncthreads();
-  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
-    const int l = B.L(i, j);
-    S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
-  });
+  if (LEARN)
+    learned_faces(Q, S.AL, S.CRX, S.FX2, x0, x1 + 1, y0 - 3, y1 + 3, 1, B, F);
+  else
+    for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
+    });
   if (dmp)
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
@@ -305,11 +348,20 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     S.AL[l] = ppm_edge(S.QIJ[l - 2], S.QIJ[l - 1], S.QIJ[l], S.QIJ[l + 1]);
   });
   __syncthreads();
-  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
-    const int l = B.L(i, j);
-    const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
-    FXO[l] = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
-  });
+  if (LEARN) {
+    learned_faces(S.QIJ, S.AL, S.CRX, FXO, x0, x1 + 1, y0, y1, 1, B, F);
+    __syncthreads();
+    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      FXO[l] = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+    });
+  } else {
+    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
+      FXO[l] = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+    });
+  }
   __syncthreads();
   // inner x-update in every row of the block and its halo
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
@@ -323,11 +375,20 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     S.AL[l] = ppm_edge(S.QIJ[l - 2 * SX], S.QIJ[l - SX], S.QIJ[l], S.QIJ[l + SX]);
   });
   __syncthreads();
-  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
-    const int l = B.L(i, j);
-    const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
-    FYO[l] = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
-  });
+  if (LEARN) {
+    learned_faces(S.QIJ, S.AL, S.CRY, FYO, x0, x1, y0, y1 + 1, SX, B, F);
+    __syncthreads();
+    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      FYO[l] = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+    });
+  } else {
+    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
+      FYO[l] = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+    });
+  }
   if (dmp)
     for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
@@ -433,7 +494,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
       if (bad) atomicOr(a.status, ST_CFL);
     }
     // mass
-    transport(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY);
+    const bool learn = a.P.hord == 1 && a.mlp;
+    if (learn)
+      transport<R, true>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY,
+                         a.mlp);
+    else
+      transport(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY);
     R* dpo = a.delp_o + o;
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
@@ -445,7 +511,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
     for (int fld = 0; fld < 2; ++fld) {
       R* Q = fld == 0 ? PT : W;
       R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
-      transport(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+      if (learn && fld == 0)
+        transport<R, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
+      else
+        transport(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
@@ -880,7 +949,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerAr
       const R* q = a.q[tq] + o;
       __syncthreads();
       for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
-      transport(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+      if (a.learn)
+        transport<R, true>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
+      else
+        transport(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
       R* qo = a.q_o[tq] + o;
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
@@ -1097,6 +1169,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   a.delzc = (R*)c.delzc; a.fx1 = (R*)c.fx1; a.fy1 = (R*)c.fy1; a.pef = (R*)c.pef; a.gz = (R*)c.gz;
   a.scratch = c.scratch;
   a.ncol = c.ncol;
+  a.mlp = P.mlp;
   if (acc) {
     a.amfx = (R*)c.amfx; a.amfy = (R*)c.amfy; a.acrx = (R*)c.acrx; a.acry = (R*)c.acry;
     a.axfx = (R*)c.axfx; a.ayfx = (R*)c.ayfx;
@@ -1198,7 +1271,7 @@ void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st) {
 }
 
 template <typename R>
-static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
+static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
   std::vector<HaloField> F;
   F.push_back(hf(c, K_CGRID, c.amfx, c.amfy, c.nz, 0));
   F.push_back(hf(c, K_CGRID, c.acrx, c.acry, c.nz, 0));
@@ -1227,6 +1300,8 @@ static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
   a.amfx = (const R*)c.amfx; a.amfy = (const R*)c.amfy;
   a.dp0 = (const R*)c.dp0;
   a.dp1 = (R*)c.dp1;
+  a.mlp = P.mlp;
+  a.learn = P.hord == 1 && P.mlp != nullptr;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const size_t sm = blk_smem(c, 18);
   for (int it = 0; it < NSPLT_MAX; ++it) {
@@ -1247,10 +1322,10 @@ static void tracers_t(Ctx& c, const StateView& s, cudaStream_t st) {
   }
 }
 
-void enqueue_tracers(Ctx& c, const StateView& s, cudaStream_t st) {
+void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
   if (s.nq <= 0) return;
-  if (c.prec == 0) tracers_t<double>(c, s, st);
-  else tracers_t<float>(c, s, st);
+  if (c.prec == 0) tracers_t<double>(c, s, P, st);
+  else tracers_t<float>(c, s, P, st);
 }
 
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st) {

@@ -29,6 +29,7 @@ struct StepArgs {
   // flux accumulators of the remapping step (null: not accumulating)
   R *amfx, *amfy, *acrx, *acry, *axfx, *ayfx;
   unsigned* status;
+  const float* mlp;      // face-value network (hord 1), float[1313] on the device
 };
 
 struct HaloField {
@@ -57,6 +58,8 @@ struct TracerArgs {
   const R *acrx, *acry, *axfx, *ayfx, *amfx, *amfy;
   const R* dp0;          // delp at the start of the subcycle
   R* dp1;                // delp after the subcycle
+  const float* mlp;      // face-value network
+  bool learn;            // tracers use learned face values
 };
 
 template <typename R>
@@ -136,7 +139,7 @@ struct ParamView {
 void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
                      cudaStream_t st, int stop_after = 99, int only = -1);
-void enqueue_tracers(Ctx& c, const StateView& s, cudaStream_t st);
+void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st);
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
                   int dir, cudaStream_t st);

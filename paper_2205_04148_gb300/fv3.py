@@ -29,7 +29,8 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_get_layout", "fv3_import", "fv3_export", "fv3_halo_fill", "fv3_acoustic_substep",
            "fv3_run_dyn", "fv3_mass_sum", "fv3_check_status", "fv3_get_metric", "fv3_stage",
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
-           "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc")
+           "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
+           "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam")
 
 
 class GridDesc(C.Structure):
@@ -46,7 +47,7 @@ class State(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double), ("ptop", C.c_double),
-                ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double)]
+                ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double), ("mlp", C.c_void_p)]
 
 
 class Layout(C.Structure):
@@ -115,18 +116,32 @@ def load(path=LIB_PATH):
     L.fv3_get_tiles.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     L.fv3_autotune.restype = st
     L.fv3_autotune.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp, C.POINTER(d)]
+    L.fv3_mlp_forward.restype = st
+    L.fv3_mlp_forward.argtypes = [vp, vp, i, i, vp, vp]
+    L.fv3_mlp_work_floats.restype = C.c_size_t
+    L.fv3_mlp_work_floats.argtypes = [i]
+    L.fv3_mlp_grad.restype = st
+    L.fv3_mlp_grad.argtypes = [vp, vp, vp, i, C.c_float, vp, vp, vp, vp]
+    L.fv3_mlp_adam.restype = st
+    L.fv3_mlp_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
     L.fv3_riem_solver_c_noalloc.restype = st
     L.fv3_riem_solver_c_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, C.POINTER(Params), vp]
     _lib = L
     return L
 
 
-def params(**kw):
+def params(mlp=None, **kw):
+    """Substep parameters; ``mlp`` (a device float tensor of 1313 network
+    parameters) with hord=1 selects the learned face values."""
     from .inputs import default_params
     p = default_params()
     p.update(kw)
-    return Params(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"], p["dz_min"],
-                  p["ptop"], p["grav"], p["rdgas"], p["cp_air"])
+    prm = Params(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"], p["dz_min"],
+                 p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None)
+    if mlp is not None:
+        prm.mlp = C.c_void_p(mlp.data_ptr())
+        prm._keep = mlp
+    return prm
 
 
 def _stream(stream):
@@ -312,3 +327,62 @@ class Grid:
 
     def check_status(self, stream=None):
         return self.L.fv3_check_status(self.ptr, _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# learned face values: batch inference and training through the C-ABI
+# ---------------------------------------------------------------------------
+MLP_NP = 1313
+
+
+def _chk(rc, what):
+    if rc != FV3_OK:
+        raise Fv3Error("%s: %s" % (what, STATUS.get(rc, rc)))
+
+
+def mlp_forward(w, x, symmetric=True, stream=None):
+    """w: cuda float32[1313]; x: cuda float32[n, 6] -> cuda float32[n]"""
+    import torch
+    L = load()
+    n = x.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    _chk(L.fv3_mlp_forward(C.c_void_p(w.data_ptr()), C.c_void_p(x.data_ptr()), n, int(symmetric),
+                           C.c_void_p(y.data_ptr()), _stream(stream)), "fv3_mlp_forward")
+    return y
+
+
+class MlpTrainer:
+    """Adam on the face-value network with the C-ABI gradient kernel."""
+
+    def __init__(self, w0, lr=1e-3):
+        import torch
+        self.w = torch.as_tensor(w0, dtype=torch.float32, device="cuda").contiguous().clone()
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.g = torch.zeros_like(self.w)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.lr = lr
+        self.step = 0
+        self.work = None
+        self.L = load()
+
+    def grad(self, x, t, weight=None):
+        import torch
+        n = x.shape[0]
+        need = int(self.L.fv3_mlp_work_floats(n))
+        if self.work is None or self.work.numel() < need:
+            self.work = torch.empty(need, dtype=torch.float32, device="cuda")
+        wt = 1.0 / n if weight is None else weight
+        _chk(self.L.fv3_mlp_grad(C.c_void_p(self.w.data_ptr()), C.c_void_p(x.data_ptr()),
+                                 C.c_void_p(t.data_ptr()), n, wt, C.c_void_p(self.work.data_ptr()),
+                                 C.c_void_p(self.g.data_ptr()), C.c_void_p(self.loss.data_ptr()), _stream(None)),
+             "fv3_mlp_grad")
+        return self.g, self.loss
+
+    def update(self, x, t):
+        self.grad(x, t)
+        self.step += 1
+        _chk(self.L.fv3_mlp_adam(C.c_void_p(self.w.data_ptr()), C.c_void_p(self.m.data_ptr()),
+                                 C.c_void_p(self.v.data_ptr()), C.c_void_p(self.g.data_ptr()), self.step,
+                                 self.lr, _stream(None)), "fv3_mlp_adam")
+        return self.loss
