@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="single", choices=["single", "batched", "modules"],
+                   help="single: one cubed sphere (--npx, --precision); batched: the 24-member ensemble "
+                        "8 x C48 + 8 x C96 + 8 x C128, FP32 bulk; modules: riem_solver_c and fv_tp_2d alone on "
+                        "one 192 x 192 x 80 tile, FP64 (the module timings the paper reports)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--npx", type=int, default=96)
     p.add_argument("--npz", type=int, default=80)
@@ -61,6 +65,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default block shape (32 x 8, 8 levels per CTA, one CTA per item)")
     return p.parse_args()
 
 
@@ -224,7 +230,12 @@ def ours(a):
     stream = torch.cuda.current_stream()
     sp = C.c_void_p(stream.cuda_stream)
 
-    # --- warm-up and timed region -------------------------------------
+    # --- autotune (outside the timed region), warm-up, timed region ------
+    tuned = None
+    if not a.no_autotune:
+        (bx, by, kc), tuned_ms = g.autotune(gs, prm)
+        tuned = {"bx": bx, "by": by, "kchunk": kc, "persistent": g.persistent(), "c_sw+d_sw_ms": tuned_ms}
+        g.load(gs, st)
     for _ in range(max(1, a.warmup)):
         g.run_dyn(gs, prm, 1)
     torch.cuda.synchronize()
@@ -355,7 +366,7 @@ def ours(a):
                "config": {"workload": "cubed-sphere C%d x %d levels, %s, n_split %d, %d tracers, one remapping "
                                       "step per bench step" % (a.npx, a.npz, a.precision.upper(), a.n_split, a.nq),
                           "cells": cells, "substeps_per_step": a.n_split, "l2": "inputs larger than L2",
-                          "parallelism": "replicas" if ws > 1 else "single GPU"},
+                          "tiles": tuned, "parallelism": "replicas" if ws > 1 else "single GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "status": status}
         print(json.dumps(out), flush=True)
@@ -365,10 +376,238 @@ def ours(a):
     return 0
 
 
+# ---------------------------------------------------------------------------
+BATCH_SIZES = [48] * 8 + [96] * 8 + [128] * 8
+
+
+def _time_steps(g, gs, prm, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.run_dyn(gs, prm, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def batched(a):
+    """The batched ensemble: 24 members of mixed resolution in one context,
+    every stage one launch over the work list of all members (persistent or
+    one CTA per item, as tuned), the n_split loop replayed from a CUDA graph.
+    Tile shape, level chunk and launch mode are tuned on a single C96 member
+    and transferred.  Beside it: the same members advanced one at a time by
+    the plain FP64 path and by the FP32 path, for the speed-ups."""
+    import ctypes as C
+
+    import torch
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as D
+        torch.cuda.set_device(local)
+        D.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+
+    nz = a.npz
+    sizes = BATCH_SIZES
+    base = {n: I.cubed_state(n, nz, seed=0, ntracers=0) for n in sorted(set(sizes))}
+    members = [I.perturb_member(base[n], member_seed=100 * rank + m) for m, n in enumerate(sizes)]
+    prm = fv3.params(n_split=a.n_split)
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    cells = sum(6 * n * n * nz for n in sizes)
+
+    # transfer tuning: search on one C96 member, apply to the ensemble
+    gt = fv3.Grid(fv3.GRID_CUBED, 96, nz, precision=fv3.FP32)
+    gts = gt.alloc_state()
+    gt.load(gts, base[96])
+    (bx, by, kc), tuned_ms = gt.autotune(gts, prm)
+    pers = gt.persistent()
+    gt.close()
+    del gts
+
+    g = fv3.Grid(fv3.GRID_CUBED, max(sizes), nz, n_members=len(sizes), member_npx=sizes, precision=fv3.FP32)
+    gs = g.alloc_state()
+    for m, st in enumerate(members):
+        g.load(gs, st, member=m)
+    g.set_tiles(bx, by, kc)
+    g.set_persistent(pers)
+    for _ in range(max(1, a.warmup)):
+        g.run_dyn(gs, prm, 1)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
+    clocks = Clocks(smi_index, enabled=not a.no_clocks)
+    L = g.L
+    if ws > 1:
+        import torch.distributed as D
+        D.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = L.fv3_kernel_launches(g.ptr)
+    ms_step = _time_steps(g, gs, prm, a.steps, stream)
+    if ws > 1:
+        D.barrier()
+    clk = clocks.stop()
+    launches = L.fv3_kernel_launches(g.ptr) - l0
+    if ws > 1:
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        D.all_reduce(t, op=D.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * a.n_split * cells / (ms_step / 1e3)
+    status = g.check_status()
+
+    # dominant kernel (d_sw over all members) timed alone
+    s = g.cstate(gs)
+    g.stage(gs, 4, prm)
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 5, 1, sp))
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 6, 2, sp))
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    reps = 10
+    k0.record(stream)
+    g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 6, reps, sp))
+    k1.record(stream)
+    torch.cuda.synchronize()
+    t_dsw = k0.elapsed_time(k1) / reps / 1e3
+    g.close()
+    del gs
+    torch.cuda.empty_cache()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach = DSW_WORDS_PER_CELL * 4 * cells / t_dsw / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3, "peak_source": "measured hbm_gbs"}
+
+    # the same members one at a time: plain FP64 path and FP32 path
+    per_member = {}
+    for label, prec in (("fp64", fv3.FP64), ("fp32", fv3.FP32)):
+        tot = 0.0
+        for n in sorted(set(sizes)):
+            g1 = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=prec)
+            s1 = g1.alloc_state()
+            g1.load(s1, members[sizes.index(n)])
+            for _ in range(2):
+                g1.run_dyn(s1, prm, 1)
+            torch.cuda.synchronize()
+            tot += sizes.count(n) * _time_steps(g1, s1, prm, max(3, a.steps // 2), stream)
+            g1.close()
+            del s1
+            torch.cuda.empty_cache()
+        per_member[label] = tot
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32 (column solve f64)", "data": "synthetic",
+               "config": {"workload": "batched ensemble 8 x C48 + 8 x C96 + 8 x C128, %d levels, FP32 bulk, "
+                                      "n_split %d, perturbations 1%% delp and 1 m/s wind" % (nz, a.n_split),
+                          "members": len(sizes), "cells": cells, "substeps_per_step": a.n_split,
+                          "l2": "inputs larger than L2",
+                          "tiles": {"bx": bx, "by": by, "kchunk": kc, "persistent": pers,
+                                    "tuned_on": "single C96 member (transferred)", "tuned_ms": tuned_ms},
+                          "parallelism": "replicas" if ws > 1 else "single GPU"},
+               "speedup": {"vs_fp64_one_member_at_a_time": per_member["fp64"] / ms_step,
+                           "vs_fp32_one_member_at_a_time": per_member["fp32"] / ms_step,
+                           "fp64_one_at_a_time_ms_per_step": per_member["fp64"],
+                           "fp32_one_at_a_time_ms_per_step": per_member["fp32"]},
+               "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
+               "clocks": clk, "status": status}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        D.destroy_process_group()
+    return 0
+
+
+# the paper's module timings (Table II; P100, GT4Py + DaCe, FP64, 192 x 192 x 80 per GPU)
+PAPER_MODULE_MS_192 = {"riem_solver_c": 3.86, "fv_tp_2d": 3.41}
+
+
+def modules(a):
+    """riem_solver_c and fv_tp_2d alone on one doubly periodic 192 x 192 x 80
+    tile in FP64 -- the per-GPU domain and modules of the paper's Table II --
+    each timed over repeated launches with CUDA events (inputs 600 MB, larger
+    than L2).  fv_tp_2d includes the halo fill of its inputs."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+
+    n, nz = 192, a.npz
+    g = fv3.Grid(fv3.GRID_PERIODIC, n, nz)
+    st = I.periodic_state(n, nz, seed=0)
+    gs = g.alloc_state()
+    g.load(gs, st)
+    prm = fv3.params()
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    L = g.L
+    s = g.cstate(gs)
+    reps = max(5, a.steps)
+
+    def timed(fn):
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g.stage(gs, 2, prm)   # c_sw and update_dz_c: the column solve's inputs
+    t_riem = timed(lambda: g.check(L.fv3_launch_stage(g.ptr, C.byref(s), C.byref(prm), 3, 1, sp)))
+    rng = np.random.default_rng(1)
+    a0 = 0.5e10
+    q = 1000.0 + 50.0 * rng.standard_normal((1, nz, n, n))
+    crx = rng.uniform(-0.6, 0.6, (1, nz, n, n + 1))
+    cry = rng.uniform(-0.6, 0.6, (1, nz, n + 1, n))
+    t = {}
+    for name, arr, kind in (("q", q, fv3.KIND_CELL), ("crx", crx, fv3.KIND_XFACE), ("cry", cry, fv3.KIND_YFACE),
+                            ("xfx", crx * a0, fv3.KIND_XFACE), ("yfx", cry * a0, fv3.KIND_YFACE)):
+        t[name] = g.alloc(kind)
+        g.put(t[name], kind, arr)
+    fx, fy = g.alloc(fv3.KIND_XFACE), g.alloc(fv3.KIND_YFACE)
+    t_tp = timed(lambda: g.fv_tp_2d(t["q"], t["crx"], t["cry"], t["xfx"], t["yfx"], fx=fx, fy=fy))
+    cells = n * n * nz
+    out = {"metric": "module ms per call", "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": reps,
+           "warmup": a.warmup, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "one doubly periodic tile %d x %d x %d, FP64" % (n, n, nz), "cells": cells},
+           "riem_solver_c_ms": t_riem, "fv_tp_2d_ms": t_tp,
+           "cells_per_s": {"riem_solver_c": cells / (t_riem / 1e3), "fv_tp_2d": cells / (t_tp / 1e3)},
+           "paper_p100_ms": PAPER_MODULE_MS_192 if nz == 80 else None,
+           "paper_note": "Table II of the paper: GT4Py + DaCe on a P100, FP64 -- context, other hardware"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return reference_arm(a)
+    if a.workload == "batched":
+        return batched(a)
+    if a.workload == "modules":
+        return modules(a)
     return ours(a)
 
 

@@ -167,6 +167,28 @@ fv3_status fv3_acoustic_substep(fv3_ctx* ctx, const fv3_state* state, const fv3_
 fv3_status fv3_run_dyn(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int n_steps,
                        fv3_stream stream);
 
+/* fv_tp_2d alone (Section IX-C, "2-D mass-conserving flux-form transport";
+ * readings R4-R6): the face fluxes of the scalar q for the given Courant
+ * numbers and area fluxes -- Lin-Rood inner/outer PPM sweeps in both orders,
+ * face value = mean of the two, flux = face value x area flux (x mass flux
+ * when mfx/mfy are given) -- plus, when damp > 0, the del-4 damping flux
+ * damp * (L_{i-1} - L_i) * dy/dxc with L the discrete Laplacian of q.  The same
+ * transport runs inside fv3_acoustic_substep (d_sw) and fv3_run_dyn
+ * (tracer_2d); this entry point exposes it for tests and module timings.
+ *
+ * All arrays are device arrays of the context's precision in the library
+ * layout, every level of every tile of every member: q cell field
+ * (FV3_KIND_CELL); crx, xfx, mfx, fx x-face fields (FV3_KIND_XFACE: between
+ * cells i-1 and i); cry, yfx, mfy, fy y-face fields (FV3_KIND_YFACE).  mfx
+ * and mfy: both NULL (area fluxes) or both set.  The halo rings of q, crx/cry,
+ * xfx/yfx and mfx/mfy are filled by this call (C-grid vector rule for the
+ * face pairs), so they are written as well as read; fx and fy receive the
+ * interior faces.  |crx|, |cry| must be below 1 (not checked here).
+ * Errors: FV3_ERR_ARG (NULL pointer, mfx without mfy, damp < 0 or not
+ * finite), FV3_ERR_ALIGN (a pointer not 128-byte aligned). */
+fv3_status fv3_fv_tp_2d(fv3_ctx* ctx, void* q, void* crx, void* cry, void* xfx, void* yfx, void* mfx, void* mfy,
+                        double damp, void* fx, void* fy, fv3_stream stream);
+
 /* Global mass sum(delp * area) per member in FP64 (Neumaier-compensated, fixed
  * order).  out_per_member: host array [n_members]; returns after the sum is
  * on the host. */
@@ -217,9 +239,18 @@ fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work
 fv3_status fv3_set_tiles(fv3_ctx* ctx, int bx, int by, int kchunk);
 fv3_status fv3_get_tiles(const fv3_ctx* ctx, int* bx, int* by, int* kchunk);
 
+/* on != 0: the horizontal kernels (c_sw, d_sw, tracer_2d) run as persistent
+ * launches -- a grid of (SMs x resident blocks) CTAs that stride over the
+ * work list of (member, tile, block, level chunk) items of all members --
+ * instead of one CTA per item.  Drops the cached graph. */
+fv3_status fv3_set_persistent(fv3_ctx* ctx, int on);
+/* *on = the launch mode set by fv3_set_persistent or chosen by fv3_autotune. */
+fv3_status fv3_get_persistent(const fv3_ctx* ctx, int* on);
+
 /* Autotuner (the paper's transfer tuning, Section VII-B, as an empirical
- * search): times c_sw + d_sw on `state` for every compiled block shape and
- * level chunks 1, 4, 16, keeps the fastest (fv3_set_tiles) and returns its
+ * search): times c_sw + d_sw on `state` for every compiled block shape,
+ * level chunks 1, 4, 16 and both launch modes (one CTA per item, persistent),
+ * keeps the fastest (fv3_set_tiles, fv3_set_persistent) and returns its
  * time per (c_sw + d_sw) in *best_ms (may be NULL).  Synchronises `stream`. */
 fv3_status fv3_autotune(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream,
                         double* best_ms);

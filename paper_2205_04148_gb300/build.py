@@ -14,7 +14,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfv3.so")
-SOURCES = ["fv3_grid.cpp", "fv3_kernels.cu", "fv3_capi.cu", "fv3_calib.cu", "fv3_noalloc.cu", "fv3_mlp.cu"]
+# (source, object name, defines): fv3_kernels.cu is three units, one per
+# precision plus the shared host code, so the heavy kernels build in parallel
+SOURCES = [("fv3_grid.cpp", "fv3_grid", ()),
+           ("fv3_kernels.cu", "fv3_kernels_f64", ("-DFV3_TU=64",)),
+           ("fv3_kernels.cu", "fv3_kernels_f32", ("-DFV3_TU=32",)),
+           ("fv3_kernels.cu", "fv3_kernels_main", ("-DFV3_TU=1",)),
+           ("fv3_capi.cu", "fv3_capi", ()), ("fv3_calib.cu", "fv3_calib", ()),
+           ("fv3_noalloc.cu", "fv3_noalloc", ()), ("fv3_mlp.cu", "fv3_mlp", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -25,17 +32,18 @@ def _deps():
     return files
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+def _compile(unit, extra):
+    src, name, defs = unit
+    obj = os.path.join(OUT, name + ".o")
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra, "-c",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, *defs, *extra, "-c",
            os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "cu")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
+        raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (name, " ".join(cmd), r.stderr))
     return obj, r.stderr
 
 

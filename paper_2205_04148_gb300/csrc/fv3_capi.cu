@@ -520,6 +520,24 @@ extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_para
   return FV3_OK;
 }
 
+extern "C" fv3_status fv3_fv_tp_2d(fv3_ctx* x, void* q, void* crx, void* cry, void* xfx, void* yfx, void* mfx,
+                                   void* mfy, double damp, void* fx, void* fy, fv3_stream stream) {
+  if (!x) return FV3_ERR_ARG;
+  void* need[7] = {q, crx, cry, xfx, yfx, fx, fy};
+  for (void* p : need) {
+    if (!p) return fail(x, FV3_ERR_ARG, "fv_tp_2d: a field is NULL");
+    if (!aligned(p)) return fail(x, FV3_ERR_ALIGN, "fv_tp_2d: a field is not 128-byte aligned");
+  }
+  if ((mfx == nullptr) != (mfy == nullptr)) return fail(x, FV3_ERR_ARG, "fv_tp_2d: mfx and mfy go together");
+  if (mfx && (!aligned(mfx) || !aligned(mfy)))
+    return fail(x, FV3_ERR_ALIGN, "fv_tp_2d: a mass flux is not 128-byte aligned");
+  if (!(damp >= 0.0) || !std::isfinite(damp)) return fail(x, FV3_ERR_ARG, "fv_tp_2d: damp must be >= 0");
+  TpPtrs p{q, crx, cry, xfx, yfx, mfx, mfy, fx, fy, damp};
+  enqueue_fv_tp_2d(x->c, p, (cudaStream_t)stream);
+  CK(x, cudaGetLastError());
+  return FV3_OK;
+}
+
 extern "C" fv3_status fv3_mass_sum(fv3_ctx* x, const fv3_state* s, double* out, fv3_stream stream) {
   if (!x) return FV3_ERR_ARG;
   if (!s || !s->delp || !out) return fail(x, FV3_ERR_ARG, "null argument");
@@ -626,6 +644,23 @@ extern "C" fv3_status fv3_set_tiles(fv3_ctx* x, int bx, int by, int kchunk) {
   return FV3_OK;
 }
 
+extern "C" fv3_status fv3_set_persistent(fv3_ctx* x, int on) {
+  if (!x) return FV3_ERR_ARG;
+  x->c.persistent = on ? 1 : 0;
+  if (x->c.graph) {
+    cudaGraphExecDestroy(x->c.graph);
+    x->c.graph = nullptr;
+    x->c.graph_key.clear();
+  }
+  return FV3_OK;
+}
+
+extern "C" fv3_status fv3_get_persistent(const fv3_ctx* x, int* on) {
+  if (!x || !on) return FV3_ERR_ARG;
+  *on = x->c.persistent;
+  return FV3_OK;
+}
+
 extern "C" fv3_status fv3_get_tiles(const fv3_ctx* x, int* bx, int* by, int* kchunk) {
   if (!x || !bx || !by || !kchunk) return FV3_ERR_ARG;
   *bx = x->c.BX;
@@ -650,6 +685,7 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
   cudaStream_t st = (cudaStream_t)stream;
   const int shapes[4][2] = {{32, 8}, {32, 16}, {64, 8}, {16, 16}};
   const int chunks[3] = {1, 4, 16};
+  const int pmodes[2] = {0, 1};
   const StateView in = view(s);
   const StateView nx = internal_view(c, in);
   const Params P = to_params(p);
@@ -658,11 +694,13 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
   CK(x, cudaEventCreate(&e0));
   CK(x, cudaEventCreate(&e1));
   double best = 1e300;
-  int bb[3] = {c.BX, c.BY, c.kchunk};
+  int bb[4] = {c.BX, c.BY, c.kchunk, c.persistent};
+  for (int pm : pmodes)
   for (const auto& sh : shapes)
     for (int kc : chunks) {
       if (kc > c.nz) continue;
       if (fv3_set_tiles(x, sh[0], sh[1], kc) != FV3_OK) continue;
+      c.persistent = pm;
       for (int w = 0; w < 2; ++w) {
         enqueue_substep(c, in, nx, P, false, st, 99, 1);
         enqueue_substep(c, in, nx, P, false, st, 99, 6);
@@ -681,11 +719,13 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
         bb[0] = sh[0];
         bb[1] = sh[1];
         bb[2] = kc;
+        bb[3] = pm;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   r = fv3_set_tiles(x, bb[0], bb[1], bb[2]);
+  c.persistent = bb[3];
   if (best_ms) *best_ms = best;
   return r;
 }

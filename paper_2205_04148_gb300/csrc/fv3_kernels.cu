@@ -27,6 +27,17 @@
 #include "fv3_kernels.cuh"
 #include "fv3_mlp.cuh"
 
+// The file is compiled as three translation units so that the two
+// precisions' kernels build in parallel: FV3_TU=1 the shared host code and
+// utility kernels, FV3_TU=64 the FP64 substep and tracer kernels, FV3_TU=32
+// the FP32 ones.  Without FV3_TU it is all of them in one unit.
+#ifndef FV3_TU
+#define FV3_TU 0
+#endif
+#define FV3_TU_MAIN (FV3_TU == 0 || FV3_TU == 1)
+#define FV3_TU_F64 (FV3_TU == 0 || FV3_TU == 64)
+#define FV3_TU_F32 (FV3_TU == 0 || FV3_TU == 32)
+
 namespace fv3 {
 
 template <typename R>
@@ -444,8 +455,8 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
 // ------------------------------------------------------------------------
 // d_sw (reading R11): one level of a block per loop iteration
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R> a, int kchunk) {
+template <typename R, int BX, int BY, bool LEARN>
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
@@ -458,7 +469,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
   S.QIJ = sb + 18 * SA; S.LAP = sb + 19 * SA; S.AL = sb + 20 * SA; S.GX = sb + 21 * SA; S.GY = sb + 22 * SA;
   (void)SY;
 
-  const Item it = a.items[blockIdx.x];
+  const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
+  // work items (block, level chunk): one per CTA, or strided over a
+  // persistent grid
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
   const R dt = (R)a.P.dt;
   const double dd = a.P.d4_bg * g.da_min;
   const R damp = (R)(dd * dd);
-  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
@@ -494,12 +509,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
       if (bad) atomicOr(a.status, ST_CFL);
     }
     // mass
-    const bool learn = a.P.hord == 1 && a.mlp;
-    if (learn)
-      transport<R, true>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY,
-                         a.mlp);
-    else
-      transport(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY);
+    transport<R, LEARN>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY,
+                        a.mlp);
     R* dpo = a.delp_o + o;
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
@@ -511,10 +522,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
     for (int fld = 0; fld < 2; ++fld) {
       R* Q = fld == 0 ? PT : W;
       R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
-      if (learn && fld == 0)
-        transport<R, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
+      if (LEARN && fld == 0)
+        transport<R, LEARN>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
       else
-        transport(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+        transport<R, false>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
@@ -568,13 +579,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_d_sw(StepArgs<R
     }
     __syncthreads();
   }
+  }
 }
 
 // ------------------------------------------------------------------------
 // c_sw (reading R7)
 // ------------------------------------------------------------------------
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk) {
+__global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
@@ -582,14 +594,16 @@ __global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk) {
   R *UC0 = sb + 5 * SA, *VC0 = sb + 6 * SA, *UT = sb + 7 * SA, *VT = sb + 8 * SA, *KE = sb + 9 * SA;
   R *VO = sb + 10 * SA, *FX1 = sb + 11 * SA, *FY1 = sb + 12 * SA;
   (void)SY;
-  const Item it = a.items[blockIdx.x];
+  const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
   const TM<R> m = tile_metric(a.M, g, it.t);
   const R dt2 = R(0.5 * a.P.dt);
-  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
@@ -678,6 +692,7 @@ __global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk) {
       vco[G(j, i)] = VC0[l] - dt2 * R(0.5) * (VO[l] + VO[l + 1]) * U[l] + (KE[l - SX] - KE[l]) * MT(rdyc, j, i);
     });
     __syncthreads();
+  }
   }
 }
 
@@ -890,8 +905,8 @@ __global__ void k_halo(const HaloBatch b, const Geo* geo) {
 // ------------------------------------------------------------------------
 // tracer_2d subcycle (reading R12)
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerArgs<R> a, int kchunk) {
+template <typename R, int BX, int BY, bool LEARN>
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_tracer(TracerArgs<R> a, int kchunk, int nwork) {
   if (a.it >= *a.nsplt) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SA = SX * (BY + 7);
@@ -902,7 +917,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerAr
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
   S.RDXd = sb + 11 * SA; S.RDYd = sb + 12 * SA; S.FY2 = sb + 13 * SA; S.FX2 = sb + 14 * SA;
   S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA; S.AL = sb + 17 * SA; S.GX = S.LAP; S.GY = S.LAP;
-  const Item it = a.items[blockIdx.x];
+  const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
@@ -910,7 +927,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerAr
   const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
   const TM<R> m = tile_metric(a.M, g, it.t);
   const R fr = R(1) / R(*a.nsplt);
-  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, g.nz);
+  const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
@@ -949,10 +966,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerAr
       const R* q = a.q[tq] + o;
       __syncthreads();
       for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
-      if (a.learn)
-        transport<R, true>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
-      else
-        transport(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+      transport<R, LEARN>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
       R* qo = a.q_o[tq] + o;
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
@@ -960,6 +974,71 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_tracer(TracerAr
       });
     }
     __syncthreads();
+  }
+  }
+}
+
+// ------------------------------------------------------------------------
+// standalone fv_tp_2d (Section IX-C; readings R5, R6): fluxes of one scalar
+// field for given Courant numbers and area fluxes (and optionally mass
+// fluxes), every level of every tile of every member.  The same transport as
+// inside d_sw and tracer_2d, with the fluxes written out.
+// ------------------------------------------------------------------------
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs<R> a, int kchunk, int nwork) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int SX = BX + 7, SA = SX * (BY + 7);
+  R* sb = reinterpret_cast<R*>(smraw);
+  R *Q = sb, *MFX = sb + SA, *MFY = sb + 2 * SA, *FXO = sb + 3 * SA, *FYO = sb + 4 * SA;
+  TS<R> S;
+  S.CRX = sb + 5 * SA; S.XFX = sb + 6 * SA; S.CRY = sb + 7 * SA; S.YFX = sb + 8 * SA;
+  S.RDXd = sb + 9 * SA; S.RDYd = sb + 10 * SA; S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA;
+  S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA; S.GX = sb + 16 * SA; S.GY = sb + 17 * SA;
+  const bool mass = a.mfx != nullptr;
+  const R damp = (R)a.damp;
+  const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  const Item it = a.items[wi / kz];
+  const Geo g = a.geo[it.m];
+  const int n = g.n, P = g.pitch;
+  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
+  const TM<R> m = tile_metric(a.M, g, it.t);
+  const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
+  auto G = [&](int j, int i) { return (long long)j * P + i; };
+  for (int k = k0; k < k1; ++k) {
+    const long long o = fld0(g, g.off3, g.nz, it.t, k);
+    for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = o + G(j, i);
+      S.CRX[l] = a.crx[q];
+      S.XFX[l] = a.xfx[q];
+      if (mass) MFX[l] = a.mfx[q];
+    });
+    for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      const long long q = o + G(j, i);
+      S.CRY[l] = a.cry[q];
+      S.YFX[l] = a.yfx[q];
+      if (mass) MFY[l] = a.mfy[q];
+    });
+    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = a.q[o + G(j, i)]; });
+    __syncthreads();
+    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+    });
+    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+    });
+    transport<R, false>(Q, S, B, m, n, cc, mass ? MFX : (const R*)nullptr, mass ? MFY : (const R*)nullptr, damp,
+                        (const R*)nullptr, FXO, FYO);
+    for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.fx[o + G(j, i)] = FXO[B.L(i, j)]; });
+    for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.fy[o + G(j, i)] = FYO[B.L(i, j)]; });
+    __syncthreads();
+  }
   }
 }
 
@@ -1043,6 +1122,7 @@ __global__ void k_mass_partial(const Geo* geo, const int4* planes, const R* delp
   }
 }
 
+#if FV3_TU_MAIN
 __global__ void k_mass_final(const double* partial, const int* first, int nmem, double* out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nmem) return;
@@ -1053,6 +1133,8 @@ __global__ void k_mass_final(const double* partial, const int* first, int nmem, 
   }
   out[m] = S + Cc;
 }
+#endif
+
 
 // ------------------------------------------------------------------------
 // dense <-> padded layout (argument marshalling for import / export)
@@ -1084,9 +1166,9 @@ __global__ void k_pack(const Geo* geo, int mem, int kind, int nlev, int iface, R
 template <typename R>
 Metric<R> metric_of(const Ctx& c);
 template <>
-Metric<double> metric_of<double>(const Ctx& c) { return c.Md; }
+inline Metric<double> metric_of<double>(const Ctx& c) { return c.Md; }
 template <>
-Metric<float> metric_of<float>(const Ctx& c) { return c.Mf; }
+inline Metric<float> metric_of<float>(const Ctx& c) { return c.Mf; }
 
 template <typename K>
 static void set_smem(K kern, size_t bytes) {
@@ -1108,14 +1190,47 @@ static void set_smem(K kern, size_t bytes) {
     }                                      \
   } while (0)
 
+#if FV3_TU_MAIN
 bool shape_supported(int bx, int by) {
   return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 8) || (bx == 16 && by == 16);
 }
+#endif
 
-static size_t blk_smem(const Ctx& c, int arrays) {
+
+// grid of a horizontal kernel: one CTA per work item, or (persistent mode)
+// as many CTAs as fit on the GPU at once, each striding over the work list
+template <typename K>
+static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork) {
+  if (c.persistent <= 0) return dim3(nwork);
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int g = sms * per_sm;
+  return dim3(g < nwork ? g : nwork);
+}
+
+// the d_sw and tracer kernels exist with and without learned face values
+// (separate instantiations: the network's fragments need registers the
+// plain kernel does not)
+template <typename R, int X, int Y, bool L>
+static void launch_d_sw(const Ctx& c, const StepArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
+  set_smem(k_d_sw<R, X, Y, L>, sm);
+  k_d_sw<R, X, Y, L><<<work_grid(c, k_d_sw<R, X, Y, L>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork);
+}
+
+template <typename R, int X, int Y, bool L>
+static void launch_tracer(const Ctx& c, const TracerArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
+  set_smem(k_tracer<R, X, Y, L>, sm);
+  k_tracer<R, X, Y, L><<<work_grid(c, k_tracer<R, X, Y, L>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork);
+}
+
+[[maybe_unused]] static size_t blk_smem(const Ctx& c, int arrays) {
   return (size_t)arrays * (c.BX + 7) * (c.BY + 7) * c.esize;
 }
 
+#if FV3_TU_MAIN
 void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStream_t st) {
   for (size_t base = 0; base < fields.size(); base += MAX_HALO_FIELDS) {
     HaloBatch b{};
@@ -1132,6 +1247,8 @@ void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStrea
     ++c.launches;
   }
 }
+#endif
+
 
 static HaloField hf(const Ctx& c, int kind, void* xa, void* ya, int nlev, int iface) {
   HaloField f{};
@@ -1144,6 +1261,7 @@ static HaloField hf(const Ctx& c, int kind, void* xa, void* ya, int nlev, int if
   return f;
 }
 
+#if FV3_TU_MAIN
 void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st) {
   std::vector<HaloField> F;
   F.push_back(hf(c, K_DGRID, s.v, s.u, c.nz, 0));
@@ -1153,6 +1271,8 @@ void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st) {
   F.push_back(hf(c, K_CELL3, s.delz, nullptr, c.nz, 0));
   enqueue_halo_fields(c, F, st);
 }
+#endif
+
 
 template <typename R>
 static void substep_t(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool acc,
@@ -1176,6 +1296,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   }
   a.status = c.status;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
+  const int nwork = c.n_items_hz * kz;
   // stage ids: 0 halo fill, 1 c_sw, 2 update_dz_c, 3 riem_solver_c,
   // 4 pef/gz halo + p_grad_c, 5 C-grid halo, 6 d_sw
   auto run = [&](int stage) {
@@ -1188,7 +1309,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     const size_t sm = blk_smem(c, 13);
 #define FV3_CSW(X, Y)                                                                  \
   set_smem(k_c_sw<R, X, Y>, sm);                                                       \
-  k_c_sw<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+  k_c_sw<R, X, Y><<<work_grid(c, k_c_sw<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_CSW);
 #undef FV3_CSW
     ++c.launches;
@@ -1219,20 +1340,34 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   }
   if (run(6)) {  // d_sw
     const size_t sm = blk_smem(c, 23);
+    const bool learn = P.hord == 1 && P.mlp;
 #define FV3_DSW(X, Y)                                                                  \
-  set_smem(k_d_sw<R, X, Y>, sm);                                                       \
-  k_d_sw<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+  (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
 #undef FV3_DSW
     ++c.launches;
   }
 }
 
+#if FV3_TU_F64
+void enqueue_substep_f64(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                         cudaStream_t st, int stop_after, int only) {
+  substep_t<double>(c, in, out, P, accumulate, st, stop_after, only);
+}
+#endif
+#if FV3_TU_F32
+void enqueue_substep_f32(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                         cudaStream_t st, int stop_after, int only) {
+  substep_t<float>(c, in, out, P, accumulate, st, stop_after, only);
+}
+#endif
+#if FV3_TU_MAIN
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
                      cudaStream_t st, int stop_after, int only) {
-  if (c.prec == 0) substep_t<double>(c, in, out, P, accumulate, st, stop_after, only);
-  else substep_t<float>(c, in, out, P, accumulate, st, stop_after, only);
+  if (c.prec == 0) enqueue_substep_f64(c, in, out, P, accumulate, st, stop_after, only);
+  else enqueue_substep_f32(c, in, out, P, accumulate, st, stop_after, only);
 }
+#endif
 
 template <typename R>
 static void copy_planes_t(Ctx& c, const std::vector<std::pair<void*, const void*>>& pairs, const int* gate, int it,
@@ -1255,6 +1390,7 @@ static void copy_planes(Ctx& c, const std::vector<std::pair<void*, const void*>>
   else copy_planes_t<float>(c, pairs, gate, it, st);
 }
 
+#if FV3_TU_MAIN
 void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cudaStream_t st) {
   copy_planes(c, {{dst.u, src.u}, {dst.v, src.v}, {dst.w, src.w}, {dst.delp, src.delp}, {dst.pt, src.pt}}, nullptr,
               0, st);
@@ -1269,6 +1405,8 @@ void enqueue_zero_acc(Ctx& c, cudaStream_t st) {
 void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st) {
   copy_planes(c, {{c.dpstart, delp}}, nullptr, 0, st);
 }
+#endif
+
 
 template <typename R>
 static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
@@ -1303,6 +1441,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   a.mlp = P.mlp;
   a.learn = P.hord == 1 && P.mlp != nullptr;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
+  const int nwork = c.n_items_hz * kz;
   const size_t sm = blk_smem(c, 18);
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
@@ -1310,8 +1449,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
     enqueue_halo_fields(c, Q, st);
     a.it = it;
 #define FV3_TRC(X, Y)                                                                  \
-  set_smem(k_tracer<R, X, Y>, sm);                                                     \
-  k_tracer<R, X, Y><<<dim3(c.n_items_hz, kz), dim3(32, 8), sm, st>>>(a, c.kchunk)
+  (a.learn ? launch_tracer<R, X, Y, true>(c, a, sm, nwork, st) : launch_tracer<R, X, Y, false>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TRC);
 #undef FV3_TRC
     ++c.launches;
@@ -1322,12 +1460,64 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   }
 }
 
-void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
-  if (s.nq <= 0) return;
-  if (c.prec == 0) tracers_t<double>(c, s, P, st);
-  else tracers_t<float>(c, s, P, st);
+#if FV3_TU_F64
+void enqueue_tracers_f64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
+  tracers_t<double>(c, s, P, st);
+}
+#endif
+#if FV3_TU_F32
+void enqueue_tracers_f32(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
+  tracers_t<float>(c, s, P, st);
+}
+#endif
+template <typename R>
+static void fv_tp_2d_t(Ctx& c, const TpPtrs& p, cudaStream_t st) {
+  TpArgs<R> a{};
+  a.geo = c.geo_d;
+  a.items = c.items_hz;
+  a.M = metric_of<R>(c);
+  a.q = (const R*)p.q; a.crx = (const R*)p.crx; a.cry = (const R*)p.cry;
+  a.xfx = (const R*)p.xfx; a.yfx = (const R*)p.yfx;
+  a.mfx = (const R*)p.mfx; a.mfy = (const R*)p.mfy;
+  a.fx = (R*)p.fx; a.fy = (R*)p.fy;
+  a.damp = p.damp;
+  const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
+  const int nwork = c.n_items_hz * kz;
+  const size_t sm = blk_smem(c, 18);
+#define FV3_TP(X, Y)                                                                   \
+  set_smem(k_fv_tp_2d<R, X, Y>, sm);                                                   \
+  k_fv_tp_2d<R, X, Y><<<work_grid(c, k_fv_tp_2d<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
+  FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TP);
+#undef FV3_TP
+  ++c.launches;
+}
+#if FV3_TU_F64
+void enqueue_fv_tp_2d_f64(Ctx& c, const TpPtrs& p, cudaStream_t st) { fv_tp_2d_t<double>(c, p, st); }
+#endif
+#if FV3_TU_F32
+void enqueue_fv_tp_2d_f32(Ctx& c, const TpPtrs& p, cudaStream_t st) { fv_tp_2d_t<float>(c, p, st); }
+#endif
+
+#if FV3_TU_MAIN
+void enqueue_fv_tp_2d(Ctx& c, const TpPtrs& p, cudaStream_t st) {
+  std::vector<HaloField> F;
+  F.push_back(hf(c, K_CELL3, p.q, nullptr, c.nz, 0));
+  F.push_back(hf(c, K_CGRID, p.crx, p.cry, c.nz, 0));
+  F.push_back(hf(c, K_CGRID, p.xfx, p.yfx, c.nz, 0));
+  if (p.mfx) F.push_back(hf(c, K_CGRID, p.mfx, p.mfy, c.nz, 0));
+  enqueue_halo_fields(c, F, st);
+  if (c.prec == 0) enqueue_fv_tp_2d_f64(c, p, st);
+  else enqueue_fv_tp_2d_f32(c, p, st);
 }
 
+void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
+  if (s.nq <= 0) return;
+  if (c.prec == 0) enqueue_tracers_f64(c, s, P, st);
+  else enqueue_tracers_f32(c, s, P, st);
+}
+#endif
+
+#if FV3_TU_MAIN
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st) {
   if (c.prec == 0)
     k_mass_partial<double><<<c.n_planes, 256, 0, st>>>(c.geo_d, c.planes, (const double*)delp, c.Md.area,
@@ -1359,5 +1549,7 @@ void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padde
                                                    (float*)dense, dir);
   }
 }
+
+#endif
 
 }  // namespace fv3

@@ -91,6 +91,7 @@ struct Ctx {
   int plan_n[K_NUM] = {};
   // work lists
   int BX = 32, BY = 8, BXc = 30, BYc = 6, kchunk = 8;
+  int persistent = 0;  // 1: horizontal kernels run on a GPU-filling persistent grid
   Item* items_hz = nullptr;
   int n_items_hz = 0;
   Item* items_dz = nullptr;
@@ -139,7 +140,31 @@ struct ParamView {
 void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
                      cudaStream_t st, int stop_after = 99, int only = -1);
+void enqueue_substep_f64(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                     cudaStream_t st, int stop_after, int only);
+void enqueue_substep_f32(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                     cudaStream_t st, int stop_after, int only);
+void enqueue_tracers_f64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
+void enqueue_tracers_f32(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
+
+// standalone fv_tp_2d: caller's fields in the library layout
+struct TpPtrs {
+  void *q, *crx, *cry, *xfx, *yfx, *mfx, *mfy, *fx, *fy;
+  double damp;
+};
+template <typename R>
+struct TpArgs {
+  const Geo* geo;
+  const Item* items;
+  Metric<R> M;
+  const R *q, *crx, *cry, *xfx, *yfx, *mfx, *mfy;
+  R *fx, *fy;
+  double damp;
+};
+void enqueue_fv_tp_2d(Ctx& c, const TpPtrs& p, cudaStream_t st);
+void enqueue_fv_tp_2d_f64(Ctx& c, const TpPtrs& p, cudaStream_t st);
+void enqueue_fv_tp_2d_f32(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st);
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
                   int dir, cudaStream_t st);

@@ -30,7 +30,8 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_run_dyn", "fv3_mass_sum", "fv3_check_status", "fv3_get_metric", "fv3_stage",
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
-           "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam")
+           "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
+           "fv3_get_persistent", "fv3_fv_tp_2d")
 
 
 class GridDesc(C.Structure):
@@ -112,6 +113,12 @@ def load(path=LIB_PATH):
     L.fv3_calibrate.argtypes = [vp, i, vp, C.POINTER(d)]
     L.fv3_set_tiles.restype = st
     L.fv3_set_tiles.argtypes = [vp, i, i, i]
+    L.fv3_set_persistent.restype = st
+    L.fv3_set_persistent.argtypes = [vp, i]
+    L.fv3_get_persistent.restype = st
+    L.fv3_get_persistent.argtypes = [vp, C.POINTER(i)]
+    L.fv3_fv_tp_2d.restype = st
+    L.fv3_fv_tp_2d.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, vp, vp, vp]
     L.fv3_get_tiles.restype = st
     L.fv3_get_tiles.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     L.fv3_autotune.restype = st
@@ -313,6 +320,14 @@ class Grid:
     def set_tiles(self, bx, by, kchunk):
         self.check(self.L.fv3_set_tiles(self.ptr, bx, by, kchunk))
 
+    def set_persistent(self, on=True):
+        self.check(self.L.fv3_set_persistent(self.ptr, int(on)))
+
+    def persistent(self):
+        on = C.c_int()
+        self.check(self.L.fv3_get_persistent(self.ptr, C.byref(on)))
+        return bool(on.value)
+
     def tiles(self):
         bx, by, kc = C.c_int(), C.c_int(), C.c_int()
         self.check(self.L.fv3_get_tiles(self.ptr, C.byref(bx), C.byref(by), C.byref(kc)))
@@ -324,6 +339,16 @@ class Grid:
         best = C.c_double()
         self.check(self.L.fv3_autotune(self.ptr, C.byref(s), C.byref(prm), _stream(stream), C.byref(best)))
         return self.tiles(), best.value
+
+    def fv_tp_2d(self, q, crx, cry, xfx, yfx, mfx=None, mfy=None, damp=0.0, fx=None, fy=None, stream=None):
+        """fluxes (fx, fy) of q (library-layout tensors of this context);
+        fills the halo rings of the inputs"""
+        fx = self.alloc(KIND_XFACE) if fx is None else fx
+        fy = self.alloc(KIND_YFACE) if fy is None else fy
+        ptr = lambda t: None if t is None else t.data_ptr()
+        self.check(self.L.fv3_fv_tp_2d(self.ptr, ptr(q), ptr(crx), ptr(cry), ptr(xfx), ptr(yfx), ptr(mfx), ptr(mfy),
+                                       float(damp), ptr(fx), ptr(fy), _stream(stream)))
+        return fx, fy
 
     def check_status(self, stream=None):
         return self.L.fv3_check_status(self.ptr, _stream(stream))

@@ -173,6 +173,46 @@ def periodic_state(n=48, nz=8, seed=0, dx=1.0e5):
     return dict(u=u, v=v, w=w, delp=delp, pt=pt, delz=delz)
 
 
+def _perturb(delp, u, v, cen, mid_u, dir_u, mid_v, dir_v, member_seed, pert_delp, pert_wind):
+    """In place: delp *= 1 + pert_delp N_m (N_m smooth, unit RMS) and a smooth
+    non-divergent wind of amplitude pert_wind m/s added to u, v, all drawn
+    from ``member_seed``."""
+    mrng = np.random.default_rng(member_seed)
+    f = _fourier3d(mrng, 3, cen)
+    f /= math.sqrt(float(np.mean(f * f)))
+    delp *= (1.0 + pert_delp * f)[:, None]
+    if pert_wind:
+        # smooth perturbation wind: the gradient-free field axis' x r
+        ax2 = mrng.standard_normal(3)
+        ax2 /= np.linalg.norm(ax2)
+
+        def vel2(p):
+            return np.cross(ax2, p)
+        pu = np.sum(vel2(mid_u) * dir_u, axis=-1)
+        pv = np.sum(vel2(mid_v) * dir_v, axis=-1)
+        u += pert_wind * pu[:, None]
+        v += pert_wind * pv[:, None]
+
+
+def perturb_member(st, member_seed, pert_delp=0.01, pert_wind=1.0):
+    """A batched-ensemble member from an unperturbed ``cubed_state`` ``st``:
+    the same result as ``cubed_state(..., pert_delp, pert_wind,
+    member_seed)`` without redrawing the base state (copies; ``st`` is kept)."""
+    nt, nz, n, _ = st["delp"].shape
+    cen = np.stack([centre_points(t, n) for t in range(nt)])
+    cor = np.stack([corner_points(t, n) for t in range(nt)])
+    mid_u, dir_u = _edge_dirs(cor[:, :, :-1], cor[:, :, 1:])
+    mid_v, dir_v = _edge_dirs(cor[:, :-1, :], cor[:, 1:, :])
+    out = dict(st)
+    out["delp"] = st["delp"].copy()
+    out["u"] = st["u"].copy()
+    out["v"] = st["v"].copy()
+    _perturb(out["delp"], out["u"], out["v"], cen, mid_u, dir_u, mid_v, dir_v, member_seed, pert_delp, pert_wind)
+    out["delz"] = hydrostatic_delz(out["delp"], st["pt"])
+    out["q"] = list(st["q"])
+    return out
+
+
 def cubed_state(n=96, nz=80, seed=0, ntracers=8, wind=20.0, tilt_deg=30.0,
                 pert_delp=0.0, pert_wind=0.0, member_seed=None):
     """Six-tile cubed sphere: delp_k = (1e5 - 100)/nz (1 + 0.01 N), a 5 K
@@ -217,21 +257,7 @@ def cubed_state(n=96, nz=80, seed=0, ntracers=8, wind=20.0, tilt_deg=30.0,
     v = np.broadcast_to(v2[:, None], (nt, nz, n, n + 1)).copy()
 
     if member_seed is not None and (pert_delp or pert_wind):
-        mrng = np.random.default_rng(member_seed)
-        f = _fourier3d(mrng, 3, cen)
-        f /= math.sqrt(float(np.mean(f * f)))
-        delp *= (1.0 + pert_delp * f)[:, None]
-        if pert_wind:
-            # smooth perturbation wind: the gradient-free field axis' x r
-            ax2 = mrng.standard_normal(3)
-            ax2 /= np.linalg.norm(ax2)
-
-            def vel2(p):
-                return np.cross(ax2, p)
-            pu = np.sum(vel2(mid_u) * dir_u, axis=-1)
-            pv = np.sum(vel2(mid_v) * dir_v, axis=-1)
-            u += pert_wind * pu[:, None]
-            v += pert_wind * pv[:, None]
+        _perturb(delp, u, v, cen, mid_u, dir_u, mid_v, dir_v, member_seed, pert_delp, pert_wind)
 
     w = np.zeros((nt, nz, n, n))
     delz = hydrostatic_delz(delp, pt)

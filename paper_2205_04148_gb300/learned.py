@@ -1,0 +1,303 @@
+"""Training and evaluation of the learned face values (reading R14).
+
+The paper has no learned component (it motivates coupling machine-learned
+models to the dynamical core, Section III-B).  The experiment here:
+
+* truth: plain FP64 runs on a fine cubed sphere (C192 by default), coarsened
+  4x to the coarse grid (C48): area-weighted delp, delp-weighted pt and
+  tracers;
+* training samples: coarse six-cell stencils along x and y at interior coarse
+  faces, and as target the coarse-face value the fine grid resolves -- the
+  fine PPM edge values on the fine faces that make up the coarse face,
+  averaged with face-length (delp, for pt and tracers: face-mass) weights;
+  inputs and target are normalised by the stencil's mean and standard
+  deviation;
+* training: Adam on the mirror-symmetric objective with the library's
+  tensor-core gradient kernel (fv3_mlp_grad, fv3_mlp_adam);
+* evaluation: coarse runs with plain PPM and with learned face values from
+  seeds disjoint from the training seeds, against the coarsened fine run,
+  with their wall times.
+
+Array handling (views of the library layout, coarse-graining, sampling) uses
+PyTorch on the device; every substep runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+from . import fv3
+from . import inputs as I
+
+POSITIVE_FIELDS = ("delp", "pt")
+
+
+def interior(g, t, member=0, nlev=None):
+    """[nt][nz][n][n] view of a cell field in the library layout."""
+    import torch
+    lay = g.layout(member)
+    nz = lay.nz if nlev is None else nlev
+    return torch.as_strided(t, (lay.ntiles, nz, lay.n, lay.n), (nz * lay.plane, lay.plane, lay.pitch, 1),
+                            lay.offset3 + 3 * lay.pitch + lay.ox)
+
+
+def edge_values(q, dim):
+    """fine PPM edge values (clamped 4th-order interpolation) between cells
+    i-1 and i along `dim` (last = x, -2 = y), for i = 2 .. n-2"""
+    import torch
+    qm2, qm1, q0, qp1 = (q.narrow(dim, s, q.shape[dim] - 3) for s in range(4))
+    al = 7.0 / 12.0 * (qm1 + q0) - 1.0 / 12.0 * (qm2 + qp1)
+    return torch.minimum(torch.maximum(al, torch.minimum(qm1, q0)), torch.maximum(qm1, q0))
+
+
+def coarsen(fine, area, r, weight=None):
+    """r x r block means over the last two axes, area (and weight) weighted"""
+    w = area if weight is None else area * weight
+    nt, nz, n, _ = fine.shape
+    m = n // r
+    num = (fine * w).reshape(nt, nz, m, r, m, r).sum((3, 5))
+    den = w.expand_as(fine).reshape(nt, nz, m, r, m, r).sum((3, 5))
+    return num / den
+
+
+def coarse_state(fields, area, r):
+    dp = fields["delp"]
+    out = {"delp": coarsen(dp, area, r)}
+    for k, v in fields.items():
+        if k != "delp":
+            out[k] = coarsen(v, area, r, dp)
+    return out
+
+
+def samples_from_snapshot(fields, area, dxf, dyf, r, rng, per_field):
+    """(x [S,6], t [S]) of normalised coarse stencils and coarse-face targets"""
+    import torch
+    dp = fields["delp"]
+    coarse = coarse_state(fields, area, r)
+    nt, nz, n, _ = dp.shape
+    m = n // r
+    xs, ts = [], []
+    dpe_x = edge_values(dp, -1)   # fine faces i = 2 .. n-2 along x
+    dpe_y = edge_values(dp, -2)
+    for name, q in fields.items():
+        qc = coarse[name]
+        for axis in ("x", "y"):
+            if axis == "x":
+                al = edge_values(q, -1)          # [.., n, n-3]: face i at index i-2
+                wgt = dyf[None, None, :, 2:n - 1].expand_as(al)
+                if name != "delp":
+                    wgt = wgt * dpe_x
+                # coarse faces I = 3 .. m-3 -> fine faces i = r I
+                I_ = torch.arange(3, m - 2, device=q.device)
+                fi = r * I_ - 2
+                a = al[..., fi]                  # [nt, nz, n, nI]
+                wv = wgt[..., fi]
+                a = (a * wv).reshape(nt, nz, m, r, -1).sum(3) / wv.reshape(nt, nz, m, r, -1).sum(3)
+                # stencils: coarse cells I-3 .. I+2 in row J
+                st = torch.stack([qc[..., :, I_ + s] for s in range(-3, 3)], -1)   # [nt, nz, m, nI, 6]
+            else:
+                al = edge_values(q, -2)          # [.., n-3, n]
+                wgt = dxf[None, None, 2:n - 1, :].expand_as(al)
+                if name != "delp":
+                    wgt = wgt * dpe_y
+                J_ = torch.arange(3, m - 2, device=q.device)
+                fj = r * J_ - 2
+                a = al[..., fj, :]               # [nt, nz, nJ, n]
+                wv = wgt[..., fj, :]
+                a = (a * wv).reshape(nt, nz, -1, m, r).sum(4) / wv.reshape(nt, nz, -1, m, r).sum(4)
+                st = torch.stack([qc[..., J_ + s, :] for s in range(-3, 3)], -1)   # [nt, nz, nJ, m, 6]
+            st = st.reshape(-1, 6)
+            a = a.reshape(-1)
+            sel = torch.as_tensor(rng.choice(st.shape[0], min(per_field, st.shape[0]), replace=False),
+                                  device=q.device)
+            st, a = st[sel], a[sel]
+            mu = ((st[:, 0] + st[:, 5]) + (st[:, 1] + st[:, 4]) + (st[:, 2] + st[:, 3])) / 6.0
+            d2 = (st - mu[:, None]) ** 2
+            sd = torch.sqrt(((d2[:, 0] + d2[:, 5]) + (d2[:, 1] + d2[:, 4]) + (d2[:, 2] + d2[:, 3])) / 6.0)
+            ok = sd > 1e-9 * mu.abs()
+            den = (sd + 1e-12 * mu.abs() + 1e-300)[:, None]
+            xs.append(((st - mu[:, None]) / den)[ok].float())
+            ts.append(((a - mu) / den[:, 0])[ok].float())
+    return torch.cat(xs), torch.cat(ts)
+
+
+def fine_run_samples(npx_fine, r, nz, seeds, snapshots, every, per_field, nq, rng_seed=0):
+    import torch
+    rng = np.random.default_rng(rng_seed)
+    g = fv3.Grid(fv3.GRID_CUBED, npx_fine, nz)
+    area = torch.as_tensor(g.metric("area"), device="cuda")[:, None]
+    dxf = torch.as_tensor(g.metric("dx")[0], device="cuda")   # y-face lengths of tile 0 (tiles alike)
+    dyf = torch.as_tensor(g.metric("dy")[0], device="cuda")   # x-face lengths
+    X, T = [], []
+    prm = fv3.params(n_split=every)
+    for sd in seeds:
+        st = I.cubed_state(npx_fine, nz, seed=sd, ntracers=nq)
+        gs = g.alloc_state(nq)
+        g.load(gs, st)
+        for _ in range(snapshots):
+            g.run_dyn(gs, prm, 1)
+            fields = {"delp": interior(g, gs["delp"]), "pt": interior(g, gs["pt"])}
+            for k in range(nq):
+                fields["q%d" % k] = interior(g, gs["q"][k])
+            x, t = samples_from_snapshot(fields, area, dxf, dyf, r, rng, per_field)
+            X.append(x)
+            T.append(t)
+    g.close()
+    return torch.cat(X), torch.cat(T)
+
+
+def init_params(seed=0, scale=1.0):
+    """Glorot-style random initial parameters (flat float64[1313])."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(fv3.MLP_NP)
+    w[0:192] = rng.standard_normal(192) * scale * np.sqrt(2.0 / 38)
+    w[224:1248] = rng.standard_normal(1024) * scale * np.sqrt(2.0 / 64)
+    w[1280:1312] = rng.standard_normal(32) * scale * np.sqrt(2.0 / 33) * 0.1
+    return w
+
+
+def fit(X, T, steps=3000, batch=65536, lr=2e-3, seed=0, log_every=500):
+    """Adam on mini-batches through the C-ABI training kernels."""
+    import torch
+    tr = fv3.MlpTrainer(init_params(seed), lr=lr)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    n = X.shape[0]
+    hist = []
+    for s in range(1, steps + 1):
+        idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
+        loss = tr.update(X[idx].contiguous(), T[idx].contiguous())
+        if s % log_every == 0 or s == 1:
+            hist.append((s, float(loss.item())))
+    return tr.w.clone(), hist
+
+
+def _coarse_run(npx, nz, seed, nq, init, prm, steps):
+    """Run a coarse model from the coarsened fine initial fields ``init``
+    (delp, pt, tracers; winds and delz from the generator on the coarse grid);
+    return the final interior fields (device tensors) and the wall time."""
+    import torch
+    stc = I.cubed_state(npx, nz, seed=seed, ntracers=nq)
+    stc["delp"] = init["delp"].cpu().numpy()
+    stc["pt"] = init["pt"].cpu().numpy()
+    stc["delz"] = I.hydrostatic_delz(stc["delp"], stc["pt"])
+    stc["q"] = [init["q%d" % k].cpu().numpy() for k in range(nq)]
+    g = fv3.Grid(fv3.GRID_CUBED, npx, nz)
+    gs = g.alloc_state(nq)
+    g.load(gs, stc)
+    g.run_dyn(gs, prm, 1)         # warm (graph capture) on a copy of the run
+    g.load(gs, stc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.run_dyn(gs, prm, steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {k: interior(g, gs[k]).clone() for k in ("delp", "pt")}
+    for k in range(nq):
+        out["q%d" % k] = interior(g, gs["q"][k]).clone()
+    area = torch.as_tensor(g.metric("area"), device="cuda")[:, None]
+    g.close()
+    return out, area, dt
+
+
+def _rel_rms(fields, truth):
+    import torch
+    errs = {}
+    for k in truth:
+        dev = truth[k] - truth[k].mean()
+        errs[k] = float(torch.sqrt(((fields[k] - truth[k]) ** 2).mean()) / torch.sqrt((dev ** 2).mean()))
+    return errs
+
+
+def coarse_eval(npx, r, nz, seed, substeps, nq, w=None):
+    """Fine truth (C{npx*r}) coarsened r x to C{npx}; plain and learned coarse
+    runs against it, and (r even) a plain run at twice the coarse resolution
+    coarsened 2x -- the plain model given more wall time than the learned
+    one.  Relative RMS errors (RMS difference over the truth's RMS deviation
+    from its mean) and wall times."""
+    import torch
+    n_split = 6 if substeps % 6 == 0 or substeps % 5 != 0 else 5
+    steps = max(1, substeps // n_split)
+    gf = fv3.Grid(fv3.GRID_CUBED, npx * r, nz)
+    area = torch.as_tensor(gf.metric("area"), device="cuda")[:, None]
+    stf = I.cubed_state(npx * r, nz, seed=seed, ntracers=nq)
+    gsf = gf.alloc_state(nq)
+    gf.load(gsf, stf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gf.run_dyn(gsf, fv3.params(n_split=n_split), steps)
+    torch.cuda.synchronize()
+    t_fine = time.perf_counter() - t0
+    fields = {"delp": interior(gf, gsf["delp"]), "pt": interior(gf, gsf["pt"])}
+    for k in range(nq):
+        fields["q%d" % k] = interior(gf, gsf["q"][k])
+    truth = {k: v.clone() for k, v in coarse_state(fields, area, r).items()}
+    init = {"delp": torch.as_tensor(stf["delp"], device="cuda"), "pt": torch.as_tensor(stf["pt"], device="cuda")}
+    for k in range(nq):
+        init["q%d" % k] = torch.as_tensor(stf["q"][k], device="cuda")
+    gf.close()
+    del gsf, fields
+    res = {}
+    runs = [("plain", npx, None)]
+    if w is not None:
+        runs.append(("learned", npx, w))
+    if r % 2 == 0:
+        runs.append(("plain_2x", 2 * npx, None))
+    for label, n, wt in runs:
+        prm = fv3.params(n_split=n_split) if wt is None else fv3.params(n_split=n_split, hord=1, mlp=wt)
+        out, area_c, dt = _coarse_run(n, nz, seed, nq, coarse_state(init, area, npx * r // n), prm, steps)
+        if n != npx:
+            out = coarse_state(out, area_c, n // npx)
+        res[label] = {"npx": n, "wall_s": dt, "rel_rms_err": _rel_rms(out, truth)}
+    res["t_fine"] = t_fine
+    res["substeps"] = steps * n_split
+    return res
+
+
+def experiment(npx=48, r=4, nz=80, train_seeds=(11, 12, 13, 14), snapshots=50, every=10, per_field=4000,
+               nq=8, eval_seeds=(1001,), substeps=500, steps=3000, out=None):
+    import torch
+    t0 = time.perf_counter()
+    X, T = fine_run_samples(npx * r, r, nz, train_seeds, snapshots, every, per_field, nq)
+    t_data = time.perf_counter() - t0
+    w, hist = fit(X, T, steps=steps)
+    t_fit = time.perf_counter() - t0 - t_data
+    # baseline of the fit: the plain 4th-order edge formula on the same samples
+    xx = X.double()
+    plain = (7.0 / 12.0 * (xx[:, 2] + xx[:, 3]) - 1.0 / 12.0 * (xx[:, 1] + xx[:, 4])).float()
+    pred = fv3.mlp_forward(w, X, symmetric=True)
+    mse_plain = float(((plain - T) ** 2).mean())
+    mse_net = float(((pred - T) ** 2).mean())
+    evals = [coarse_eval(npx, r, nz, sd, substeps, nq, w) for sd in eval_seeds]
+    res = {"samples": int(X.shape[0]), "t_data_s": t_data, "t_fit_s": t_fit, "loss_history": hist,
+           "sample_mse_plain_edge": mse_plain, "sample_mse_network": mse_net, "eval": evals,
+           "config": dict(npx=npx, r=r, nz=nz, train_seeds=list(train_seeds), snapshots=snapshots, every=every,
+                          per_field=per_field, nq=nq, eval_seeds=list(eval_seeds), substeps=substeps,
+                          steps=steps)}
+    if out:
+        with open(out, "w") as fh:
+            json.dump(res, fh, indent=1)
+        np.save(out.replace(".json", "_weights.npy"), w.cpu().numpy())
+    return res, w
+
+
+if __name__ == "__main__":
+    import argparse
+    p = argparse.ArgumentParser()
+    p.add_argument("--npx", type=int, default=48)
+    p.add_argument("--r", type=int, default=4)
+    p.add_argument("--nz", type=int, default=80)
+    p.add_argument("--snapshots", type=int, default=50)
+    p.add_argument("--every", type=int, default=10)
+    p.add_argument("--per-field", type=int, default=4000)
+    p.add_argument("--steps", type=int, default=3000)
+    p.add_argument("--substeps", type=int, default=500)
+    p.add_argument("--out", default=None)
+    a = p.parse_args()
+    import __graft_entry__
+    __graft_entry__.build()
+    res, _ = experiment(npx=a.npx, r=a.r, nz=a.nz, snapshots=a.snapshots, every=a.every, per_field=a.per_field,
+                        steps=a.steps, substeps=a.substeps, out=a.out)
+    print(json.dumps({k: v for k, v in res.items() if k != "loss_history"}, indent=1))
