@@ -124,10 +124,8 @@ class Clocks:
 
 # ---------------------------------------------------------------------------
 def dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2205_04148_gb300 import replicas
+    return replicas.world()
 
 
 def cpu_oracle_rate(npx, nz_sample, reps=1):
@@ -187,30 +185,16 @@ def ours(a):
     import numpy as np
     import torch
 
-    ws, rank, local = dist()
-    if ws > 1:
-        import torch.distributed as D
-        torch.cuda.set_device(local)
-        D.init_process_group("nccl", init_method="env://")
-    else:
+    from paper_2205_04148_gb300 import replicas
+    ws, rank, local = replicas.init("nccl")
+    if ws == 1:
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_04148_gb300 import fv3
     from paper_2205_04148_gb300 import inputs as I
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as D
-            D.barrier()
-
-    def allmax(x):
-        if ws > 1:
-            import torch.distributed as D
-            t = torch.tensor([x], device="cuda", dtype=torch.float64)
-            D.all_reduce(t, op=D.ReduceOp.MAX)
-            return float(t.item())
-        return x
+    barrier = replicas.barrier
+    allmax = replicas.max_over_ranks
 
     prec = fv3.FP64 if a.precision == "fp64" else fv3.FP32
     g = fv3.Grid(fv3.GRID_CUBED, a.npx, a.npz, precision=prec)
@@ -370,9 +354,7 @@ def ours(a):
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "status": status}
         print(json.dumps(out), flush=True)
-    if ws > 1:
-        import torch.distributed as D
-        D.destroy_process_group()
+    replicas.finish()
     return 0
 
 
@@ -403,12 +385,9 @@ def batched(a):
 
     import torch
 
-    ws, rank, local = dist()
-    if ws > 1:
-        import torch.distributed as D
-        torch.cuda.set_device(local)
-        D.init_process_group("nccl", init_method="env://")
-    else:
+    from paper_2205_04148_gb300 import replicas
+    ws, rank, local = replicas.init("nccl")
+    if ws == 1:
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
@@ -418,7 +397,7 @@ def batched(a):
     nz = a.npz
     sizes = BATCH_SIZES
     base = {n: I.cubed_state(n, nz, seed=0, ntracers=0) for n in sorted(set(sizes))}
-    members = [I.perturb_member(base[n], member_seed=100 * rank + m) for m, n in enumerate(sizes)]
+    members = [I.perturb_member(base[n], member_seed=replicas.member_seed(rank, m)) for m, n in enumerate(sizes)]
     prm = fv3.params(n_split=a.n_split)
     stream = torch.cuda.current_stream()
     sp = C.c_void_p(stream.cuda_stream)
@@ -446,21 +425,15 @@ def batched(a):
     smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
     clocks = Clocks(smi_index, enabled=not a.no_clocks)
     L = g.L
-    if ws > 1:
-        import torch.distributed as D
-        D.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     clocks.start()
     l0 = L.fv3_kernel_launches(g.ptr)
     ms_step = _time_steps(g, gs, prm, a.steps, stream)
-    if ws > 1:
-        D.barrier()
+    replicas.barrier()
     clk = clocks.stop()
     launches = L.fv3_kernel_launches(g.ptr) - l0
-    if ws > 1:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        D.all_reduce(t, op=D.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = replicas.max_over_ranks(ms_step)
     value = ws * a.n_split * cells / (ms_step / 1e3)
     status = g.check_status()
 
@@ -525,8 +498,7 @@ def batched(a):
                "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
                "clocks": clk, "status": status}
         print(json.dumps(out), flush=True)
-    if ws > 1:
-        D.destroy_process_group()
+    replicas.finish()
     return 0
 
 

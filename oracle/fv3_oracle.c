@@ -684,18 +684,26 @@ static float bf16r(float f) {
   return v.f;
 }
 
-/* mean and standard deviation of the six cells, summed in mirror pairs so
-   that the reversed stencil gives the same bits */
-static void mlp_normalise(const double* q6, double* mu, double* sig, double* x) {
-  double m = ((q6[0] + q6[5]) + (q6[1] + q6[4]) + (q6[2] + q6[3])) / 6.0;
-  double d[6];
-  for (int i = 0; i < 6; i++) d[i] = (q6[i] - m) * (q6[i] - m);
-  double v = (d[0] + d[5]) + (d[1] + d[4]) + (d[2] + d[3]);
-  double sd = sqrt(v / 6.0);
-  double eps = 1e-12 * fabs(m) + 1e-300;
-  for (int i = 0; i < 6; i++) x[i] = (q6[i] - m) / (sd + eps);
-  *mu = m;
-  *sig = sd;
+/* network inputs of the six cells (reading R14): offsets d_i = q_i - r from
+   the mean r of the two cells next to the face (FP64, rounded to float),
+   then in float their mean m, the deviations e_i = d_i - m, the standard
+   deviation sig = sqrt(mean e_i^2) and x_i = e_i / (sig + 1e-30).  Sums are
+   taken in mirror pairs (i, 5 - i) so that the reversed stencil gives the
+   reversed inputs bit for bit.  Returns sig. */
+static float mlp_normalise(const double* q6, float* x) {
+  const double r = 0.5 * (q6[2] + q6[3]);
+  float d[6], e[6];
+  for (int i = 0; i < 6; i++) d[i] = (float)(q6[i] - r);
+  const float sixth = 1.0f / 6.0f;
+  const float m = ((d[0] + d[5]) + (d[1] + d[4]) + (d[2] + d[3])) * sixth;
+  for (int i = 0; i < 6; i++) e[i] = d[i] - m;
+  float sq[6];
+  for (int i = 0; i < 6; i++) sq[i] = e[i] * e[i];
+  const float v = ((sq[0] + sq[5]) + (sq[1] + sq[4]) + (sq[2] + sq[3])) * sixth;
+  const float sig = sqrtf(v);
+  const float inv = 1.0f / (sig + 1e-30f);
+  for (int i = 0; i < 6; i++) x[i] = e[i] * inv;
+  return sig;
 }
 
 /* FP64 forward; h1, h2 (32 each) returned for the backward pass */
@@ -785,20 +793,26 @@ double orc_mlp_forward_bf16(const double* w, const double* x) {
 }
 
 /* learned face value at the face between q6[2] and q6[3] (cells q_{i-3..i+2}
-   of the PPM face-value stencil), with the plain PPM face value as the
-   fallback when the network leaves the range of the two cells or, for a
+   of the PPM face-value stencil): the plain PPM face value plus the
+   network's correction sig * y, y = (N(x) + N(reversed x)) / 2 in float; the
+   plain value alone where the sum leaves the range of the two cells or, for a
    positive field, goes negative */
 static double learned_value(const double* mlp, int bf16, const double* q6, int positive, double plain) {
-  double mu, sig, x[6], xr[6], h1[32], h2[32];
-  mlp_normalise(q6, &mu, &sig, x);
-  for (int i = 0; i < 6; i++) xr[i] = x[5 - i];
+  float x[6];
+  double xd[6], xr[6], h1[32], h2[32];
+  const float sig = mlp_normalise(q6, x);
+  for (int i = 0; i < 6; i++) {
+    xd[i] = (double)x[i];
+    xr[5 - i] = (double)x[i];
+  }
   /* mirror-symmetric evaluation: the two tiles that share a cube edge see
      the stencil in opposite orders and must compute the same flux */
-  double y1 = bf16 ? orc_mlp_forward_bf16(mlp, x) : orc_mlp_forward(mlp, x, h1, h2);
-  double y2 = bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2);
-  double y = 0.5 * (y1 + y2);
-  double a = mu + sig * y;
-  double lo = fmin(q6[2], q6[3]), hi = fmax(q6[2], q6[3]);
+  const float y1 = (float)(bf16 ? orc_mlp_forward_bf16(mlp, xd) : orc_mlp_forward(mlp, xd, h1, h2));
+  const float y2 = (float)(bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2));
+  const float y = 0.5f * (y1 + y2);
+  const float corr = y * sig;
+  const double a = plain + (double)corr;
+  const double lo = fmin(q6[2], q6[3]), hi = fmax(q6[2], q6[3]);
   if (!(a >= lo && a <= hi)) return plain;
   if (positive && a < 0.0) return plain;
   return a;

@@ -388,12 +388,17 @@ def learned_face(w, q6, c, positive=1, bf16=0):
 
 
 def mlp_normalise(q6):
-    """inputs of the network: the six cells minus their mean over their standard
-    deviation (mirror-pair sums, as in the C oracle)"""
+    """network inputs and sigma of six-cell stencils [..., 6] (reading R14, as
+    in the C oracle): float offsets from the mean of the two centre cells,
+    mirror-pair sums in float"""
     q = np.asarray(q6, dtype=np.float64)
-    mu = ((q[..., 0] + q[..., 5]) + (q[..., 1] + q[..., 4]) + (q[..., 2] + q[..., 3])) / 6.0
-    d = (q - mu[..., None]) ** 2
-    v = (d[..., 0] + d[..., 5]) + (d[..., 1] + d[..., 4]) + (d[..., 2] + d[..., 3])
-    sd = np.sqrt(v / 6.0)
-    eps = 1e-12 * np.abs(mu) + 1e-300
-    return (q - mu[..., None]) / (sd + eps)[..., None], mu, sd
+    r = 0.5 * (q[..., 2] + q[..., 3])
+    d = (q - r[..., None]).astype(np.float32)
+    sixth = np.float32(1.0) / np.float32(6.0)
+    m = ((d[..., 0] + d[..., 5]) + (d[..., 1] + d[..., 4]) + (d[..., 2] + d[..., 3])) * sixth
+    e = d - m[..., None]
+    sq = e * e
+    v = ((sq[..., 0] + sq[..., 5]) + (sq[..., 1] + sq[..., 4]) + (sq[..., 2] + sq[..., 3])) * sixth
+    sig = np.sqrt(v)
+    inv = np.float32(1.0) / (sig + np.float32(1e-30))
+    return e * inv[..., None], sig

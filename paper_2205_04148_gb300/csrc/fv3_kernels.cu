@@ -165,10 +165,41 @@ struct Blk {
   __device__ __forceinline__ int L(int i, int j) const { return (j - y0 + 3) * SX + (i - x0 + 3); }
 };
 
+// 2-D loop over [ilo, ihi) x [jlo, jhi), flattened over all threads of the
+// block so that every warp but the last is full (the ranges are a few cells
+// wider than a warp; a row-per-warp loop would leave most lanes of a second
+// pass idle, and on this GPU an FP64 warp instruction costs its full pipe
+// time whatever its active lanes).  Row j = floor((e + 1/2) / w) from a float
+// reciprocal: the fractional part of (e + 1/2) / w is at least 1/(2w) away
+// from an integer, far more than the float error for these sizes.
 template <typename F>
 __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
-  for (int j = jlo + (int)threadIdx.y; j < jhi; j += (int)blockDim.y)
-    for (int i = ilo + (int)threadIdx.x; i < ihi; i += (int)blockDim.x) f(i, j);
+  const int w = ihi - ilo, h = jhi - jlo;
+  if (w <= 0 || h <= 0) return;
+  const int total = w * h, nthr = (int)(blockDim.x * blockDim.y);
+  const float rw = 1.0f / (float)w;
+  for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < total; e += nthr) {
+    const int j = (int)(((float)e + 0.5f) * rw);
+    f(ilo + (e - j * w), jlo + j);
+  }
+}
+
+// 1 / x.  FP64: a float reciprocal refined by two Newton-Raphson steps
+// r <- r + r (1 - x r), each of which squares the relative error (about 2^-23
+// -> 2^-46 -> 2^-92): within an ulp of the quotient, for the positive,
+// float-range denominators of the transport (cell areas plus area fluxes,
+// pressure thicknesses).  The float path divides.
+template <typename R>
+__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ double rcp<double>(double x) {
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(__double2float_rn(x)));
+  double r = (double)r0;
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Cube corners (reading R3): rewrite the 3x3 missing-quadrant cells of a
@@ -254,10 +285,11 @@ __device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, 
 }
 
 // Learned face values (reading R14) over a 2-D range of faces with stride s
-// along the sweep: the mirror-symmetric network value mu + sigma * y, or the
-// plain PPM value where it leaves the range of the two cells or is negative
-// (every learned field is positive).  All lanes of a warp take part in the
-// tensor-core evaluation; padding lanes repeat a valid face and do not store.
+// along the sweep: the plain PPM face value plus the mirror-symmetric
+// network's correction sig * y, or the plain value alone where the sum leaves
+// the range of the two cells or is negative (every learned field is
+// positive).  All lanes of a warp take part in the tensor-core evaluation;
+// padding lanes repeat a valid face and do not store.
 template <typename R>
 __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int ilo, int ihi, int jlo, int jhi,
                               int s, const Blk& B, const MlpFrag& F) {
@@ -274,13 +306,12 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
     R q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) q[k] = Q[l + (k - 3) * s];
-    R mu, sd;
     float x[6], xr[6];
-    mlp_inputs(q, mu, sd, x, xr);
+    const float sig = mlp_inputs(q, x, xr);
     const float y1 = mlp_warp(F, x);
     const float y2 = mlp_warp(F, xr);
-    const R ys = (R)(0.5f * (y1 + y2));
-    const R a = mu + sd * ys;
+    const float corr = __fmul_rn(__fmul_rn(0.5f, __fadd_rn(y1, y2)), sig);
+    const R a = plain + (R)corr;
     const R lo = q[2] < q[3] ? q[2] : q[3], hi = q[2] < q[3] ? q[3] : q[2];
     const R res = (a >= lo && a <= hi && a >= R(0)) ? a : plain;
     if (valid) OUT[l] = res;
@@ -442,11 +473,11 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
   __syncthreads();
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+    S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
   });
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+    S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
   });
   (void)scaled;
   (void)fr;
@@ -515,7 +546,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
-      DPN[l] = R(1) / d;  // reciprocal, used by pt and w
+      DPN[l] = rcp(d);  // reciprocal, used by pt and w
       dpo[G(j, i)] = d;
     });
     // pt and w with the mass fluxes and mass-weighted damping
@@ -586,7 +617,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
 // c_sw (reading R7)
 // ------------------------------------------------------------------------
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256) k_c_sw(StepArgs<R> a, int kchunk, int nwork) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
@@ -948,18 +979,18 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
     __syncthreads();
     for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+      S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
     });
     for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+      S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
     });
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
       const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
       D0[l] = d0;
-      D1[l] = d1;
+      D1[l] = rcp(d1);  // reciprocal, shared by every tracer
       a.dp1[o + G(j, i)] = d1;
     });
     for (int tq = 0; tq < a.nq; ++tq) {
@@ -970,7 +1001,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
       R* qo = a.q_o[tq] + o;
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
-        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) / D1[l];
+        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) * D1[l];
       });
     }
     __syncthreads();
@@ -1027,11 +1058,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
     __syncthreads();
     for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDYd[l] = R(1) / (MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+      S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
     });
     for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDXd[l] = R(1) / (MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+      S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
     });
     transport<R, false>(Q, S, B, m, n, cc, mass ? MFX : (const R*)nullptr, mass ? MFY : (const R*)nullptr, damp,
                         (const R*)nullptr, FXO, FYO);

@@ -148,52 +148,52 @@ __device__ __forceinline__ float mlp_warp(const MlpFrag& F, const float (&x)[6],
   return y + F.c3;
 }
 
-// normalised network inputs of a six-cell stencil (mirror-pair sums, no
-// contraction, so the reversed stencil gives the same bits); returns mu and
-// sigma.  Both orders of the stencil are returned (x and reversed xr).
-template <typename R>
-__device__ __forceinline__ void mlp_inputs(const R (&q)[6], R& mu, R& sd, float (&x)[6], float (&xr)[6]);
-
-template <>
-__device__ __forceinline__ void mlp_inputs<double>(const double (&q)[6], double& mu, double& sd, float (&x)[6],
-                                                   float (&xr)[6]) {
-  const double s = __dadd_rn(__dadd_rn(__dadd_rn(q[0], q[5]), __dadd_rn(q[1], q[4])), __dadd_rn(q[2], q[3]));
-  mu = __ddiv_rn(s, 6.0);
-  double d[6];
+// network inputs of a six-cell stencil (reading R14): offsets from the mean
+// of the two centre cells in the stencil's precision, rounded to float; then
+// in float the mean, deviations, standard deviation sig and x = dev / (sig +
+// 1e-30), all sums in mirror pairs and without contraction so the reversed
+// stencil gives the reversed inputs bit for bit.  Returns sig; xr = reversed x.
+__device__ __forceinline__ float mlp_offsets_to_inputs(const float (&d)[6], float (&x)[6], float (&xr)[6]) {
+  const float sixth = 1.0f / 6.0f;
+  const float m =
+      __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(d[0], d[5]), __fadd_rn(d[1], d[4])), __fadd_rn(d[2], d[3])), sixth);
+  float e[6], sq[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const double e = __dsub_rn(q[i], mu);
-    d[i] = __dmul_rn(e, e);
+    e[i] = __fsub_rn(d[i], m);
+    sq[i] = __fmul_rn(e[i], e[i]);
   }
-  const double v = __dadd_rn(__dadd_rn(__dadd_rn(d[0], d[5]), __dadd_rn(d[1], d[4])), __dadd_rn(d[2], d[3]));
-  sd = __dsqrt_rn(__ddiv_rn(v, 6.0));
-  const double den = __dadd_rn(sd, __dadd_rn(__dmul_rn(1e-12, fabs(mu)), 1e-300));
+  const float v =
+      __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(sq[0], sq[5]), __fadd_rn(sq[1], sq[4])), __fadd_rn(sq[2], sq[3])), sixth);
+  const float sig = __fsqrt_rn(v);
+  const float inv = __fdiv_rn(1.0f, __fadd_rn(sig, 1e-30f));
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    x[i] = (float)__ddiv_rn(__dsub_rn(q[i], mu), den);
+    x[i] = __fmul_rn(e[i], inv);
     xr[5 - i] = x[i];
   }
+  return sig;
+}
+
+template <typename R>
+__device__ __forceinline__ float mlp_inputs(const R (&q)[6], float (&x)[6], float (&xr)[6]);
+
+template <>
+__device__ __forceinline__ float mlp_inputs<double>(const double (&q)[6], float (&x)[6], float (&xr)[6]) {
+  const double r = __dmul_rn(0.5, __dadd_rn(q[2], q[3]));
+  float d[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = __double2float_rn(__dsub_rn(q[i], r));
+  return mlp_offsets_to_inputs(d, x, xr);
 }
 
 template <>
-__device__ __forceinline__ void mlp_inputs<float>(const float (&q)[6], float& mu, float& sd, float (&x)[6],
-                                                  float (&xr)[6]) {
-  const float s = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[5]), __fadd_rn(q[1], q[4])), __fadd_rn(q[2], q[3]));
-  mu = __fdiv_rn(s, 6.0f);
+__device__ __forceinline__ float mlp_inputs<float>(const float (&q)[6], float (&x)[6], float (&xr)[6]) {
+  const float r = __fmul_rn(0.5f, __fadd_rn(q[2], q[3]));
   float d[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float e = __fsub_rn(q[i], mu);
-    d[i] = __fmul_rn(e, e);
-  }
-  const float v = __fadd_rn(__fadd_rn(__fadd_rn(d[0], d[5]), __fadd_rn(d[1], d[4])), __fadd_rn(d[2], d[3]));
-  sd = __fsqrt_rn(__fdiv_rn(v, 6.0f));
-  const float den = __fadd_rn(sd, __fadd_rn(__fmul_rn(1e-12f, fabsf(mu)), 1e-37f));
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    x[i] = __fdiv_rn(__fsub_rn(q[i], mu), den);
-    xr[5 - i] = x[i];
-  }
+  for (int i = 0; i < 6; ++i) d[i] = __fsub_rn(q[i], r);
+  return mlp_offsets_to_inputs(d, x, xr);
 }
 
 }  // namespace fv3

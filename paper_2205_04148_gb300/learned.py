@@ -1,25 +1,30 @@
 """Training and evaluation of the learned face values (reading R14).
 
 The paper has no learned component (it motivates coupling machine-learned
-models to the dynamical core, Section III-B).  The experiment here:
+models to the dynamical core, Section III-B).  The learned face value is the
+plain PPM face value plus a correction sigma * y from a small network of the
+six normalised cells around the face.  The experiment here:
 
 * truth: plain FP64 runs on a fine cubed sphere (C192 by default), coarsened
   4x to the coarse grid (C48): area-weighted delp, delp-weighted pt and
   tracers;
 * training samples: coarse six-cell stencils along x and y at interior coarse
-  faces, and as target the coarse-face value the fine grid resolves -- the
-  fine PPM edge values on the fine faces that make up the coarse face,
-  averaged with face-length (delp, for pt and tracers: face-mass) weights;
-  inputs and target are normalised by the stencil's mean and standard
-  deviation;
+  faces of coarsened fine snapshots.  The face value the fine grid resolves
+  is the mean of the fine PPM edge values on the r fine faces that make up
+  the coarse face (face-length weights for delp; face-length x face-mass
+  weights for pt and tracers); the target is its difference from the plain
+  coarse PPM face value (for the flow direction of the coarsened fine winds)
+  over sigma, the standard deviation of the six cells;
 * training: Adam on the mirror-symmetric objective with the library's
-  tensor-core gradient kernel (fv3_mlp_grad, fv3_mlp_adam);
-* evaluation: coarse runs with plain PPM and with learned face values from
-  seeds disjoint from the training seeds, against the coarsened fine run,
-  with their wall times.
+  tensor-core gradient kernel (fv3_mlp_grad, fv3_mlp_adam), cosine learning
+  rate decay;
+* evaluation: coarse runs with plain PPM and with learned face values, and a
+  plain run at twice the coarse resolution, from seeds disjoint from the
+  training seeds, against the coarsened fine run, with their wall times.
 
-Array handling (views of the library layout, coarse-graining, sampling) uses
-PyTorch on the device; every substep runs in the library's kernels.
+Array handling (views of the library layout, coarse-graining, sampling, the
+training targets) uses PyTorch on the device; every substep runs in the
+library's kernels.
 """
 from __future__ import annotations
 
@@ -41,6 +46,55 @@ def interior(g, t, member=0, nlev=None):
     nz = lay.nz if nlev is None else nlev
     return torch.as_strided(t, (lay.ntiles, nz, lay.n, lay.n), (nz * lay.plane, lay.plane, lay.pitch, 1),
                             lay.offset3 + 3 * lay.pitch + lay.ox)
+
+
+def interior_face(g, t, kind, member=0):
+    """[nt][nz][n+1][n] (y-faces, u) or [nt][nz][n][n+1] (x-faces, v) view"""
+    import torch
+    lay = g.layout(member)
+    nj, ni = (lay.n + 1, lay.n) if kind == fv3.KIND_YFACE else (lay.n, lay.n + 1)
+    return torch.as_strided(t, (lay.ntiles, lay.nz, nj, ni), (lay.nz * lay.plane, lay.plane, lay.pitch, 1),
+                            lay.offset3 + 3 * lay.pitch + lay.ox)
+
+
+def normalise(st):
+    """network inputs x [S, 6] (float) and sigma [S] of six-cell stencils
+    st [S, 6] (float64), as the kernels form them (reading R14)"""
+    import torch
+    r = 0.5 * (st[:, 2] + st[:, 3])
+    d = (st - r[:, None]).float()
+    sixth = torch.tensor(1.0 / 6.0, dtype=torch.float32, device=st.device)
+    m = ((d[:, 0] + d[:, 5]) + (d[:, 1] + d[:, 4]) + (d[:, 2] + d[:, 3])) * sixth
+    e = d - m[:, None]
+    sq = e * e
+    v = ((sq[:, 0] + sq[:, 5]) + (sq[:, 1] + sq[:, 4]) + (sq[:, 2] + sq[:, 3])) * sixth
+    sig = torch.sqrt(v)
+    return e / (sig + 1e-30)[:, None], sig
+
+
+def plain_face(st, c):
+    """plain PPM face value (reading R4) between st[:, 2] and st[:, 3] for
+    Courant numbers c [S] (float64)"""
+    import torch
+
+    def edge(qm, q0, q1, qp):
+        al = 7.0 / 12.0 * (q0 + q1) - 1.0 / 12.0 * (qm + qp)
+        return torch.minimum(torch.maximum(al, torch.minimum(q0, q1)), torch.maximum(q0, q1))
+
+    aL = edge(st[:, 0], st[:, 1], st[:, 2], st[:, 3])
+    aC = edge(st[:, 1], st[:, 2], st[:, 3], st[:, 4])
+    aR = edge(st[:, 2], st[:, 3], st[:, 4], st[:, 5])
+    pos = c > 0
+    qu = torch.where(pos, st[:, 2], st[:, 3])
+    bl = torch.where(pos, aL, aC) - qu
+    br = torch.where(pos, aC, aR) - qu
+    flat = bl * br >= 0
+    cut_l = ~flat & (bl.abs() > 2 * br.abs())
+    cut_r = ~flat & ~cut_l & (br.abs() > 2 * bl.abs())
+    bl, br = torch.where(flat, 0.0, torch.where(cut_l, -2 * br, bl)), torch.where(flat, 0.0, torch.where(cut_r, -2 * bl, br))
+    ac = c.abs()
+    x = torch.where(pos, br, bl)
+    return qu + (1 - ac) * (x - ac * (bl + br))
 
 
 def edge_values(q, dim):
@@ -71,16 +125,25 @@ def coarse_state(fields, area, r):
     return out
 
 
-def samples_from_snapshot(fields, area, dxf, dyf, r, rng, per_field):
-    """(x [S,6], t [S]) of normalised coarse stencils and coarse-face targets"""
+def samples_from_snapshot(fields, winds, area, dxf, dyf, r, rng, per_field, dt=20.0):
+    """(x [S,6], t [S]) of normalised coarse stencils and correction targets"""
     import torch
     dp = fields["delp"]
+    u, v = winds
     coarse = coarse_state(fields, area, r)
     nt, nz, n, _ = dp.shape
     m = n // r
+    dxc = r * float(torch.sqrt(area.mean()))      # coarse cell width for the Courant estimate
     xs, ts = [], []
     dpe_x = edge_values(dp, -1)   # fine faces i = 2 .. n-2 along x
     dpe_y = edge_values(dp, -2)
+    # normal winds on fine x-faces (from u) and y-faces (from v), coarse-face means
+    I_ = torch.arange(3, m - 2, device=dp.device)
+    fi = r * I_
+    ucx = 0.25 * (u[..., :-1, fi - 1] + u[..., :-1, fi] + u[..., 1:, fi - 1] + u[..., 1:, fi])   # [nt,nz,n,nI]
+    ucx = ucx.reshape(nt, nz, m, r, -1).mean(3)                                                    # [nt,nz,m,nI]
+    vcy = 0.25 * (v[..., fi - 1, :-1] + v[..., fi - 1, 1:] + v[..., fi, :-1] + v[..., fi, 1:])     # [nt,nz,nJ,n]
+    vcy = vcy.reshape(nt, nz, -1, m, r).mean(4)                                                    # [nt,nz,nJ,m]
     for name, q in fields.items():
         qc = coarse[name]
         for axis in ("x", "y"):
@@ -89,37 +152,40 @@ def samples_from_snapshot(fields, area, dxf, dyf, r, rng, per_field):
                 wgt = dyf[None, None, :, 2:n - 1].expand_as(al)
                 if name != "delp":
                     wgt = wgt * dpe_x
-                # coarse faces I = 3 .. m-3 -> fine faces i = r I
-                I_ = torch.arange(3, m - 2, device=q.device)
-                fi = r * I_ - 2
-                a = al[..., fi]                  # [nt, nz, n, nI]
-                wv = wgt[..., fi]
+                a = al[..., fi - 2]              # [nt, nz, n, nI]
+                wv = wgt[..., fi - 2]
                 a = (a * wv).reshape(nt, nz, m, r, -1).sum(3) / wv.reshape(nt, nz, m, r, -1).sum(3)
-                # stencils: coarse cells I-3 .. I+2 in row J
                 st = torch.stack([qc[..., :, I_ + s] for s in range(-3, 3)], -1)   # [nt, nz, m, nI, 6]
+                c = dt * ucx / dxc
             else:
                 al = edge_values(q, -2)          # [.., n-3, n]
                 wgt = dxf[None, None, 2:n - 1, :].expand_as(al)
                 if name != "delp":
                     wgt = wgt * dpe_y
-                J_ = torch.arange(3, m - 2, device=q.device)
-                fj = r * J_ - 2
-                a = al[..., fj, :]               # [nt, nz, nJ, n]
-                wv = wgt[..., fj, :]
+                a = al[..., fi - 2, :]           # [nt, nz, nJ, n]
+                wv = wgt[..., fi - 2, :]
                 a = (a * wv).reshape(nt, nz, -1, m, r).sum(4) / wv.reshape(nt, nz, -1, m, r).sum(4)
-                st = torch.stack([qc[..., J_ + s, :] for s in range(-3, 3)], -1)   # [nt, nz, nJ, m, 6]
+                st = torch.stack([qc[..., I_ + s, :] for s in range(-3, 3)], -1)   # [nt, nz, nJ, m, 6]
+                c = dt * vcy / dxc
             st = st.reshape(-1, 6)
             a = a.reshape(-1)
-            sel = torch.as_tensor(rng.choice(st.shape[0], min(per_field, st.shape[0]), replace=False),
-                                  device=q.device)
-            st, a = st[sel], a[sel]
-            mu = ((st[:, 0] + st[:, 5]) + (st[:, 1] + st[:, 4]) + (st[:, 2] + st[:, 3])) / 6.0
-            d2 = (st - mu[:, None]) ** 2
-            sd = torch.sqrt(((d2[:, 0] + d2[:, 5]) + (d2[:, 1] + d2[:, 4]) + (d2[:, 2] + d2[:, 3])) / 6.0)
-            ok = sd > 1e-9 * mu.abs()
-            den = (sd + 1e-12 * mu.abs() + 1e-300)[:, None]
-            xs.append(((st - mu[:, None]) / den)[ok].float())
-            ts.append(((a - mu) / den[:, 0])[ok].float())
+            c = c.reshape(-1)
+            # half of the faces uniformly, half in proportion to the stencil's
+            # relative variation (where the face values, and their errors, matter)
+            nsel = min(per_field, st.shape[0])
+            uni = torch.as_tensor(rng.choice(st.shape[0], nsel - nsel // 2, replace=False), device=q.device)
+            rel = (st.std(1) / st[:, 2:4].abs().mean(1).clamp_min(1e-300)).float()
+            gen = torch.Generator(device=q.device)
+            gen.manual_seed(int(rng.integers(1 << 62)))
+            imp = torch.multinomial(rel + 1e-30, nsel // 2, replacement=False, generator=gen)
+            sel = torch.cat([uni, imp])
+            st, a, c = st[sel], a[sel], c[sel]
+            x, sig = normalise(st)
+            ok = sig.double() > 1e-9 * (0.5 * (st[:, 2] + st[:, 3])).abs()
+            t = (a - plain_face(st, c)) / sig.double().clamp_min(1e-300)
+            ok = ok & (t.abs() < 10.0)
+            xs.append(x[ok])
+            ts.append(t[ok].float())
     return torch.cat(xs), torch.cat(ts)
 
 
@@ -141,7 +207,8 @@ def fine_run_samples(npx_fine, r, nz, seeds, snapshots, every, per_field, nq, rn
             fields = {"delp": interior(g, gs["delp"]), "pt": interior(g, gs["pt"])}
             for k in range(nq):
                 fields["q%d" % k] = interior(g, gs["q"][k])
-            x, t = samples_from_snapshot(fields, area, dxf, dyf, r, rng, per_field)
+            winds = (interior_face(g, gs["u"], fv3.KIND_YFACE), interior_face(g, gs["v"], fv3.KIND_XFACE))
+            x, t = samples_from_snapshot(fields, winds, area, dxf, dyf, r, rng, per_field)
             X.append(x)
             T.append(t)
     g.close()
@@ -158,20 +225,32 @@ def init_params(seed=0, scale=1.0):
     return w
 
 
-def fit(X, T, steps=3000, batch=65536, lr=2e-3, seed=0, log_every=500):
-    """Adam on mini-batches through the C-ABI training kernels."""
+def fit(X, T, steps=3000, batch=65536, lr=2e-3, seed=0, log_every=500, holdout=0.05):
+    """Adam on mini-batches through the C-ABI training kernels, cosine
+    learning-rate decay; the parameters with the lowest loss on a held-out
+    part of the samples are returned."""
     import torch
-    tr = fv3.MlpTrainer(init_params(seed), lr=lr)
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
+    perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+    nh = max(1, int(holdout * X.shape[0]))
+    Xh, Th = X[perm[:nh]].contiguous(), T[perm[:nh]].contiguous()
+    X, T = X[perm[nh:]], T[perm[nh:]]
+    tr = fv3.MlpTrainer(init_params(seed), lr=lr)
     n = X.shape[0]
     hist = []
+    best, best_w = float("inf"), tr.w.clone()
     for s in range(1, steps + 1):
+        tr.lr = 0.5 * lr * (1 + np.cos(np.pi * (s - 1) / steps))
         idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
         loss = tr.update(X[idx].contiguous(), T[idx].contiguous())
-        if s % log_every == 0 or s == 1:
-            hist.append((s, float(loss.item())))
-    return tr.w.clone(), hist
+        if s % log_every == 0 or s == 1 or s == steps:
+            yh = fv3.mlp_forward(tr.w, Xh, symmetric=True)
+            lh = float(0.5 * ((yh - Th) ** 2).mean())
+            hist.append((s, float(loss.item()), lh))
+            if lh < best:
+                best, best_w = lh, tr.w.clone()
+    return best_w, hist
 
 
 def _coarse_run(npx, nz, seed, nq, init, prm, steps):
@@ -264,15 +343,13 @@ def experiment(npx=48, r=4, nz=80, train_seeds=(11, 12, 13, 14), snapshots=50, e
     t_data = time.perf_counter() - t0
     w, hist = fit(X, T, steps=steps)
     t_fit = time.perf_counter() - t0 - t_data
-    # baseline of the fit: the plain 4th-order edge formula on the same samples
-    xx = X.double()
-    plain = (7.0 / 12.0 * (xx[:, 2] + xx[:, 3]) - 1.0 / 12.0 * (xx[:, 1] + xx[:, 4])).float()
+    # baseline of the fit: no correction (plain PPM), y = 0
     pred = fv3.mlp_forward(w, X, symmetric=True)
-    mse_plain = float(((plain - T) ** 2).mean())
+    mse_plain = float((T ** 2).mean())
     mse_net = float(((pred - T) ** 2).mean())
     evals = [coarse_eval(npx, r, nz, sd, substeps, nq, w) for sd in eval_seeds]
     res = {"samples": int(X.shape[0]), "t_data_s": t_data, "t_fit_s": t_fit, "loss_history": hist,
-           "sample_mse_plain_edge": mse_plain, "sample_mse_network": mse_net, "eval": evals,
+           "sample_mse_plain": mse_plain, "sample_mse_network": mse_net, "eval": evals,
            "config": dict(npx=npx, r=r, nz=nz, train_seeds=list(train_seeds), snapshots=snapshots, every=every,
                           per_field=per_field, nq=nq, eval_seeds=list(eval_seeds), substeps=substeps,
                           steps=steps)}

@@ -44,7 +44,8 @@ def errors(x, ref):
         d = a - b
         dev = b - b.mean()
         rms_dev = float(np.sqrt((dev * dev).mean()))
-        out[f] = {"rel_max": float(np.abs(d).max() / max(np.abs(b).max(), 1e-300)),
+        out[f] = {"n_differ": int(np.count_nonzero(d)), "max_abs": float(np.abs(d).max()),
+                  "rel_max": float(np.abs(d).max() / max(np.abs(b).max(), 1e-300)),
                   "rel_rms": float(np.sqrt((d * d).mean()) / rms_dev) if rms_dev > 0 else None}
     return out
 

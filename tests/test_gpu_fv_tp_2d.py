@@ -111,7 +111,7 @@ def test_fv_tp_2d_courant_one_translation():
 
 def test_fv_tp_2d_invalid_arguments():
     from paper_2205_04148_gb300 import fv3
-    g = fv3.Grid(fv3.GRID_PERIODIC, 16, 1)
+    g = fv3.Grid(fv3.GRID_PERIODIC, 16, 2)
     c, x, y = g.alloc(fv3.KIND_CELL), g.alloc(fv3.KIND_XFACE), g.alloc(fv3.KIND_YFACE)
     with pytest.raises(fv3.Fv3Error, match="ARG"):
         g.fv_tp_2d(c, x, y, x, y, mfx=x)

@@ -98,3 +98,21 @@ def test_learned_substep_close_to_oracle(orc):
     m0 = orc.State(d)
     m0.load(st)
     assert abs(g.mass(gs)[0] - m0.mass()) <= 1e-14 * m0.mass()
+
+
+def test_zero_network_is_plain_ppm():
+    """a network that outputs zero adds no correction: the learned substep is
+    the plain one"""
+    from paper_2205_04148_gb300 import build, fv3
+    build.build()
+    n, nz = 12, 3
+    st = seeded(True, n, nz, seed=43)
+    out = []
+    for prm in (fv3.params(), fv3.params(mlp=cuda(np.zeros(fv3.MLP_NP)), hord=1)):
+        g = fv3.Grid(fv3.GRID_CUBED, n, nz)
+        gs = g.alloc_state()
+        g.load(gs, st)
+        g.substep(gs, prm)
+        out.append({f: g.read(gs, f) for f in FIELDS})
+    for f in FIELDS:
+        assert relerr(out[1][f], out[0][f]) <= 1e-15, f

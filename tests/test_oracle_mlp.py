@@ -50,12 +50,41 @@ def test_closed_forms(orc):
     assert orc.mlp_forward(w2, x) == -1.5
 
 
-def test_zero_network_gives_stencil_mean(orc):
-    # y = 0 -> the face value is the six-cell mean when that lies between the
-    # two cells next to the face
+def test_zero_network_gives_plain_ppm(orc):
+    # y = 0 -> no correction: exactly the plain PPM face value, either flow sign
     w = np.zeros(orc.MLP_NP)
-    q6 = np.array([1.0, 2.0, 2.5, 3.5, 4.0, 5.0])
-    assert abs(orc.learned_face(w, q6, 0.3) - q6.mean()) < 1e-15
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        q6 = 10 + rng.standard_normal(6)
+        c = rng.uniform(-0.9, 0.9)
+        assert orc.learned_face(w, q6, c) == orc.ppm_face(q6, c)
+
+
+def test_constant_output_correction_closed_form(orc):
+    # only the output bias: y = beta, correction beta * sigma with sigma the
+    # standard deviation of the six cells (sqrt(35/12) for 1..6)
+    w = np.zeros(orc.MLP_NP)
+    w[1312] = 0.1
+    q6 = np.arange(1.0, 7.0)
+    for c in (0.3, -0.3):
+        plain = orc.ppm_face(q6, c)
+        want = plain + 0.1 * math.sqrt(35.0 / 12.0)
+        assert 3.0 <= want <= 4.0
+        assert abs(orc.learned_face(w, q6, c) - want) <= 1e-6
+
+
+def test_normalised_inputs(orc):
+    rng = np.random.default_rng(22)
+    q = 1000.0 + rng.standard_normal((200, 6)) * 10.0 ** rng.uniform(-6, 2, (200, 1))
+    x, sig = orc.mlp_normalise(q)
+    assert np.abs(x.mean(-1)).max() < 1e-5
+    assert np.abs(np.sqrt((x.astype(np.float64) ** 2).mean(-1)) - 1).max() < 1e-5
+    assert np.allclose(sig, q.std(-1), rtol=1e-4)
+    xr, sigr = orc.mlp_normalise(q[:, ::-1])
+    assert np.array_equal(xr, x[:, ::-1]) and np.array_equal(sigr, sig)
+    # a constant stencil has no deviation and zero inputs
+    x0, s0 = orc.mlp_normalise(np.full((1, 6), 3.7))
+    assert s0[0] == 0 and not x0.any()
 
 
 def test_fallbacks(orc):
