@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default block shape (32 x 8, 8 levels per CTA, one CTA per item)")
+    p.add_argument("--tiles", default=None,
+                   help="BX,BY,KCHUNK,PERSISTENT: set the block shape, level chunk and launch mode instead of "
+                        "autotuning")
     return p.parse_args()
 
 
@@ -216,7 +219,12 @@ def ours(a):
 
     # --- autotune (outside the timed region), warm-up, timed region ------
     tuned = None
-    if not a.no_autotune:
+    if a.tiles:
+        bx, by, kc, pm = (int(x) for x in a.tiles.split(","))
+        g.set_tiles(bx, by, kc)
+        g.set_persistent(bool(pm))
+        tuned = {"bx": bx, "by": by, "kchunk": kc, "persistent": bool(pm), "set": "by --tiles"}
+    elif not a.no_autotune:
         (bx, by, kc), tuned_ms = g.autotune(gs, prm)
         tuned = {"bx": bx, "by": by, "kchunk": kc, "persistent": g.persistent(), "c_sw+d_sw_ms": tuned_ms}
         g.load(gs, st)

@@ -710,8 +710,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
       const R ra = MT(rarea, j, i);
       const R d = DP[l] + (fm[0] - fm[1] + fm[2] - fm[3]) * ra;
       dpc[G(j, i)] = d;
-      ptc[G(j, i)] = (PT[l] * DP[l] + (fp[0] - fp[1] + fp[2] - fp[3]) * ra) / d;
-      wcc[G(j, i)] = (W[l] * DP[l] + (fw[0] - fw[1] + fw[2] - fw[3]) * ra) / d;
+      const R rdn = rcp(d);
+      ptc[G(j, i)] = (PT[l] * DP[l] + (fp[0] - fp[1] + fp[2] - fp[3]) * ra) * rdn;
+      wcc[G(j, i)] = (W[l] * DP[l] + (fw[0] - fw[1] + fw[2] - fw[3]) * ra) * rdn;
     });
     R *uco = a.uc + o, *vco = a.vc + o;
     for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
   const bool valid = i >= x0 - 1 && i <= x1 && j >= y0 - 1 && j <= y1 && !(ring && ringy);
   const bool inner = i >= x0 && i < x1 && j >= y0 && j < y1;
   const TM<R> m = tile_metric(a.M, g, it.t);
-  const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min;
+  const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min, rgrav = (R)(1.0 / a.P.grav);
   const long long q = (long long)j * P + i;
   R gzr = R(0), gzn_below = R(0);
   const int l = ty * TXW + tx;
@@ -774,8 +775,8 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
         Gf[f] = F[f] * (F[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
       }
       const R ar = MT(area, j, i);
-      const R gzn = (GZ[l] * ar + Gf[0] - Gf[1] + Gf[2] - Gf[3]) / (ar + F[0] - F[1] + F[2] - F[3]);
-      a.delzc[o + q] = fmin((gzn_below - gzn) / grav, -dzmin);
+      const R gzn = (GZ[l] * ar + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar + F[0] - F[1] + F[2] - F[3]);
+      a.delzc[o + q] = fmin((gzn_below - gzn) * rgrav, -dzmin);
       gzn_below = gzn;
     }
     __syncthreads();
@@ -805,30 +806,36 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
   double* s_pe = a.scratch + 4LL * nz * NC;
   const double dt = 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
   const double kappa = a.P.rdgas / a.P.cp_air, gama = 1.0 / (1.0 - kappa);
+  // the loop-invariant quotients once; per level the reciprocals of the
+  // thickness, the interface pressure, the log ratio and the pivot (FP64 here
+  // is 2 lanes per SM per clock, and a quotient costs several of them)
+  const double rgrav = 1.0 / grav, rdt = 1.0 / dt, cC = aimp * dt * gama, rd_g = rd / grav;
   const long long q = (long long)r.j * g.pitch + i;
-  double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
+  double pe = a.P.ptop, rpe = 1.0 / pe, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
   for (int k = 0; k < nz; ++k) {
     const long long o = fld0(g, g.off3, nz, r.t, k) + q;
     const double dpk = (double)a.delpc[o], ptk = (double)a.ptc[o], wck = (double)a.wc[o], dzk = (double)a.delzc[o];
-    const double pen = pe + dpk;
-    const double p = -dpk * rd * ptk / (grav * dzk);
-    const double ph = dpk / log(pen / pe);
+    const double pen = pe + dpk, rpen = rcp(pen);
+    const double rdz = rcp(dzk);
+    const double p = -dpk * rd_g * ptk * rdz;
+    const double ph = dpk * rcp(log(pen * rpe));
     const double pp = p - ph;
-    const double C = aimp * dt * gama * p / (-dzk);
-    const double mm = k == 0 ? 0.5 * dpk / grav : 0.5 * (dpp + dpk) / grav;
+    const double C = -cC * p * rdz;
+    const double mm = k == 0 ? 0.5 * dpk * rgrav : 0.5 * (dpp + dpk) * rgrav;
     const double wn = k == 0 ? wck : 0.5 * (wcp + wck);
     const double la = -Cp;                    // lower (layer above the interface)
-    const double di = mm / dt + Cp + C;       // diagonal
+    const double di = mm * rdt + Cp + C;      // diagonal
     const double up = k < nz - 1 ? -C : 0.0;  // upper
-    const double rhs = mm / dt * wn + pp - ppp;
+    const double rhs = mm * rdt * wn + pp - ppp;
     double cpk, dpt;
     if (k == 0) {
-      cpk = up / di;
-      dpt = rhs / di;
+      const double rden = rcp(di);
+      cpk = up * rden;
+      dpt = rhs * rden;
     } else {
-      const double den = di - la * cpp;
-      cpk = up / den;
-      dpt = (rhs - la * dpv) / den;
+      const double rden = rcp(di - la * cpp);
+      cpk = up * rden;
+      dpt = (rhs - la * dpv) * rden;
     }
     const long long sidx = (long long)k * NC + col;
     s_cp[sidx] = cpk;
@@ -837,6 +844,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     s_pp[sidx] = pp;
     s_pe[sidx] = pe;
     pe = pen;
+    rpe = rpen;
     dpp = dpk;
     wcp = wck;
     Cp = C;
@@ -845,7 +853,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     dpv = dpt;
   }
   // bottom-up
-  const double pe_bot = pe;
+  const double pe_bot = pe, raimp = 1.0 / aimp;
   double Wn = 0.0, gzv = 0.0, ppn_below = 0.0;
   {
     const long long ob = fld0(g, g.offi, nz + 1, r.t, nz) + q;
@@ -857,7 +865,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     const long long o = fld0(g, g.off3, nz, r.t, k) + q;
     const double dzk = (double)a.delzc[o];
     const double dzn = dzk + dt * (Wn - Wk);
-    const double ppn = s_pp[sidx] + s_C[sidx] * (Wn - Wk) / aimp;
+    const double ppn = s_pp[sidx] + s_C[sidx] * (Wn - Wk) * raimp;
     gzv = gzv - grav * dzn;
     const long long oi = fld0(g, g.offi, nz + 1, r.t, k) + q;
     const long long oib = fld0(g, g.offi, nz + 1, r.t, k + 1) + q;
@@ -879,7 +887,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
 // ------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R pgrad(R gA0, R gA1, R gB0, R gB1, R pA0, R pA1, R pB0, R pB1) {
-  return ((gA1 - gB0) * (pB1 - pA0) + (gA0 - gB1) * (pA1 - pB0)) / (pA1 - pA0 + pB1 - pB0);
+  return ((gA1 - gB0) * (pB1 - pA0) + (gA0 - gB1) * (pA1 - pB0)) * rcp(pA1 - pA0 + pB1 - pB0);
 }
 
 template <typename R>
