@@ -233,6 +233,14 @@ long long fv3_kernel_launches(const fv3_ctx* ctx);
  * in *work_per_launch; time it with events on the same stream. */
 fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work_per_launch);
 
+/* Accuracy check of the kernels' FP64 helpers (no counterpart in the paper;
+ * for tests).  Device arrays of n doubles.  what = 0: out = 1/x by the
+ * Newton-refined hardware reciprocal the transport and the column solve use;
+ * what = 1: out = ln((x + y) / x), the log pressure ratio of the column solve
+ * (atanh series for small y / (2x + y)).  FV3_ERR_ARG for an unknown `what`,
+ * n < 0 or a NULL array; FV3_ERR_CUDA if the launch fails. */
+fv3_status fv3_math_check(int what, const double* x, const double* y, double* out, int n, fv3_stream stream);
+
 /* Block shape (bx x by cells) and level chunk of the horizontal kernels
  * (c_sw, d_sw, tracer_2d).  Compiled shapes: 32x8, 32x16, 64x8, 16x16;
  * 1 <= kchunk <= npz.  Drops the cached remapping-step graph. */

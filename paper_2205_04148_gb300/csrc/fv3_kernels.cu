@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "fv3_kernels.cuh"
+#include "fv3_math.cuh"
 #include "fv3_mlp.cuh"
 
 // The file is compiled as three translation units so that the two
@@ -184,24 +185,6 @@ __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
   }
 }
 
-// 1 / x.  FP64: a float reciprocal refined by two Newton-Raphson steps
-// r <- r + r (1 - x r), each of which squares the relative error (about 2^-23
-// -> 2^-46 -> 2^-92): within an ulp of the quotient, for the positive,
-// float-range denominators of the transport (cell areas plus area fluxes,
-// pressure thicknesses).  The float path divides.
-template <typename R>
-__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
-template <>
-__device__ __forceinline__ double rcp<double>(double x) {
-  float r0;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(__double2float_rn(x)));
-  double r = (double)r0;
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
 // Cube corners (reading R3): rewrite the 3x3 missing-quadrant cells of a
 // shared-memory scalar from the block's own strips, turned about the corner:
 // role 0 for sweeps along x (from the W/E strip), 1 along y (S/N strip).
@@ -284,6 +267,20 @@ __device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, 
   return qu + (R(1) - ac) * (x - ac * (bl + br));
 }
 
+// a lies in [min(qa, qb), max(qa, qb)] and is not negative (FP64: on the
+// integer pipe, with the order-preserving keys of the bit patterns)
+template <typename R>
+__device__ __forceinline__ bool within_cells(R a, R qa, R qb) {
+  const R lo = qa < qb ? qa : qb, hi = qa < qb ? qb : qa;
+  return a >= lo && a <= hi && a >= R(0);
+}
+template <>
+__device__ __forceinline__ bool within_cells<double>(double a, double qa, double qb) {
+  const long long ka = okey(a), k0 = okey(qa), k1 = okey(qb);
+  const long long lo = k0 < k1 ? k0 : k1, hi = k0 < k1 ? k1 : k0;
+  return ka >= lo && ka <= hi && ka >= 0;
+}
+
 // Learned face values (reading R14) over a 2-D range of faces with stride s
 // along the sweep: the plain PPM face value plus the mirror-symmetric
 // network's correction sig * y, or the plain value alone where the sum leaves
@@ -312,9 +309,7 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
     const float y2 = mlp_warp(F, xr);
     const float corr = __fmul_rn(__fmul_rn(0.5f, __fadd_rn(y1, y2)), sig);
     const R a = plain + (R)corr;
-    const R lo = q[2] < q[3] ? q[2] : q[3], hi = q[2] < q[3] ? q[3] : q[2];
-    const R res = (a >= lo && a <= hi && a >= R(0)) ? a : plain;
-    if (valid) OUT[l] = res;
+    if (valid) OUT[l] = within_cells(a, q[2], q[3]) ? a : plain;
   }
 }
 
@@ -811,14 +806,14 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
   // is 2 lanes per SM per clock, and a quotient costs several of them)
   const double rgrav = 1.0 / grav, rdt = 1.0 / dt, cC = aimp * dt * gama, rd_g = rd / grav;
   const long long q = (long long)r.j * g.pitch + i;
-  double pe = a.P.ptop, rpe = 1.0 / pe, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
+  double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
   for (int k = 0; k < nz; ++k) {
     const long long o = fld0(g, g.off3, nz, r.t, k) + q;
     const double dpk = (double)a.delpc[o], ptk = (double)a.ptc[o], wck = (double)a.wc[o], dzk = (double)a.delzc[o];
-    const double pen = pe + dpk, rpen = rcp(pen);
+    const double pen = pe + dpk;
     const double rdz = rcp(dzk);
     const double p = -dpk * rd_g * ptk * rdz;
-    const double ph = dpk * rcp(log(pen * rpe));
+    const double ph = dpk * rcp(log_ratio(pen, pe, dpk));
     const double pp = p - ph;
     const double C = -cC * p * rdz;
     const double mm = k == 0 ? 0.5 * dpk * rgrav : 0.5 * (dpp + dpk) * rgrav;
@@ -844,7 +839,6 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     s_pp[sidx] = pp;
     s_pe[sidx] = pe;
     pe = pen;
-    rpe = rpen;
     dpp = dpk;
     wcp = wck;
     Cp = C;

@@ -31,7 +31,7 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
-           "fv3_get_persistent", "fv3_fv_tp_2d")
+           "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check")
 
 
 class GridDesc(C.Structure):
@@ -117,6 +117,8 @@ def load(path=LIB_PATH):
     L.fv3_set_persistent.argtypes = [vp, i]
     L.fv3_get_persistent.restype = st
     L.fv3_get_persistent.argtypes = [vp, C.POINTER(i)]
+    L.fv3_math_check.restype = st
+    L.fv3_math_check.argtypes = [i, vp, vp, vp, i, vp]
     L.fv3_fv_tp_2d.restype = st
     L.fv3_fv_tp_2d.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, vp, vp, vp]
     L.fv3_get_tiles.restype = st
