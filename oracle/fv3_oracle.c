@@ -67,6 +67,7 @@ typedef struct {
   double d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air;
   const double* mlp;       /* 1313 network parameters (hord 1) */
   int mlp_bf16;            /* 1: inference with bfloat16 inputs/weights, float sums */
+  int remap;               /* 1: vertical remapping after each remapping step (R16) */
 } OParams;
 
 typedef struct {
@@ -1585,6 +1586,140 @@ static void tracer_2d(OState* s, const double* dp_start, const OParams* P) {
   free(crx); free(cry); free(xfx); free(yfx); free(mfx); free(mfy); free(Fx); free(Fy); free(dp0); free(dp1);
 }
 
+/* ------------------------------------------------------------------ */
+/* vertical remapping (reading R16; Section II: the model integrates on  */
+/* Lagrangian surfaces and remaps them to reference levels)              */
+/* ------------------------------------------------------------------ */
+/* Edge values of the layer means q[0..nz) (edge k between layers k-1 and k):
+   the top and bottom edges take the outermost layer values, the edges next
+   to them the mean of their two layers, the others the fourth-order formula of
+   R4 clamped into the range of their two layers. */
+static void remap_edges(int nz, const double* q, double* al) {
+  al[0] = q[0];
+  al[nz] = q[nz - 1];
+  for (int k = 1; k < nz; k++) {
+    double a;
+    if (k == 1 || k == nz - 1)
+      a = 0.5 * (q[k - 1] + q[k]);
+    else
+      a = 7.0 / 12.0 * (q[k - 1] + q[k]) - 1.0 / 12.0 * (q[k - 2] + q[k + 1]);
+    double lo = fmin(q[k - 1], q[k]), hi = fmax(q[k - 1], q[k]);
+    al[k] = fmin(fmax(a, lo), hi);
+  }
+}
+
+/* Mean of the limited parabola of a layer (mean qb, edge deviations bl, br
+   after the R4 limiter) over the fraction [x1, x2] of the layer (0 = upper
+   edge, 1 = lower edge): the parabola is q(x) = aL + x (aR - aL + a6 (1 - x))
+   with aL = qb + bl, aR = qb + br, a6 = -3 (bl + br). */
+static double parabola_mean(double qb, double bl, double br, double x1, double x2) {
+  double aL = qb + bl, aR = qb + br, a6 = -3.0 * (bl + br);
+  return aL + 0.5 * (aR - aL + a6) * (x1 + x2) - a6 / 3.0 * (x1 * x1 + x1 * x2 + x2 * x2);
+}
+
+/* Conservative remap of layer means q on interfaces pe[0..nz] to interfaces
+   pn[0..nz] (both increasing, same end points): each new layer gets the mean
+   of the piecewise-parabolic reconstruction over it, summed over the old
+   layers it overlaps. */
+static void remap_column(int nz, const double* pe, const double* pn, const double* q, double* out) {
+  double* al = zalloc(nz + 1);
+  remap_edges(nz, q, al);
+  for (int k = 0; k < nz; k++) {
+    double lo = pn[k], hi = pn[k + 1], mass = 0.0;
+    for (int m = 0; m < nz; m++) {
+      double a = fmax(lo, pe[m]), b = fmin(hi, pe[m + 1]);
+      if (!(b > a)) continue;
+      double dp = pe[m + 1] - pe[m];
+      double bl = al[m] - q[m], br = al[m + 1] - q[m];
+      ppm_limit(&bl, &br);
+      double x1 = (a - pe[m]) / dp, x2 = (b - pe[m]) / dp;
+      mass += (b - a) * parabola_mean(q[m], bl, br, x1, x2);
+    }
+    out[k] = mass / (hi - lo);
+  }
+  free(al);
+}
+
+double orc_remap_column(int nz, const double* pe, const double* pn, const double* q, double* out) {
+  remap_column(nz, pe, pn, q, out);
+  return 0.0;
+}
+
+/* reference interfaces of a column: equally spaced in pressure between the
+   model top and the column's surface pressure ps = pe[nz] */
+static void reference_interfaces(int nz, const double* pe, double* pn) {
+  for (int k = 0; k <= nz; k++) pn[k] = pe[0] + (pe[nz] - pe[0]) * ((double)k / nz);
+  pn[nz] = pe[nz];
+}
+
+static void column_interfaces(const OState* s, int t, long c, double ptop, double* pe) {
+  const ODom* d = s->d;
+  pe[0] = ptop;
+  for (int k = 0; k < d->nz; k++) pe[k + 1] = pe[k] + s->delp[((long)t * d->nz + k) * d->pc + c];
+}
+
+/* Remap every column of the state: delp to the reference layers; pt, w and
+   the tracers as mass-weighted means; delz through delz / delp; u and v on
+   their face columns, whose interfaces are the means of the two adjacent
+   cell columns' interfaces (old and new). */
+void orc_remap(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  const int nz = d->nz, n = d->n;
+  fill_cells(d, s->delp, nz, H);
+  double *pe = zalloc(nz + 1), *pn = zalloc(nz + 1), *pe2 = zalloc(nz + 1), *pn2 = zalloc(nz + 1);
+  double *fa = zalloc(nz + 1), *fb = zalloc(nz + 1), *col = zalloc(nz), *res = zalloc(nz);
+  long nc = (long)d->nt * nz * d->pc;
+  double* ndelp = zalloc(nc);
+  memcpy(ndelp, s->delp, sizeof(double) * nc);
+  double** cf = (double**)malloc(sizeof(double*) * (3 + s->nq));
+  cf[0] = s->pt;
+  cf[1] = s->w;
+  cf[2] = s->delz;
+  for (int q = 0; q < s->nq; q++) cf[3 + q] = s->q[q];
+  /* u and v first: they need the old delp of the neighbouring cells */
+  for (int t = 0; t < d->nt; t++)
+    for (int dir = 0; dir < 2; dir++) /* 0: u on y-faces, 1: v on x-faces */
+      for (int j = 0; j < n + (dir == 0); j++)
+        for (int i = 0; i < n + (dir == 1); i++) {
+          long ca = dir == 0 ? IC(d, j - 1, i) : IC(d, j, i - 1), cb = IC(d, j, i);
+          column_interfaces(s, t, ca, P->ptop, pe);
+          column_interfaces(s, t, cb, P->ptop, pe2);
+          reference_interfaces(nz, pe, pn);
+          reference_interfaces(nz, pe2, pn2);
+          for (int k = 0; k <= nz; k++) {
+            fa[k] = 0.5 * (pe[k] + pe2[k]);
+            fb[k] = 0.5 * (pn[k] + pn2[k]);
+          }
+          double* f = dir == 0 ? s->u : s->v;
+          long pl = dir == 0 ? d->py : d->px;
+          long c = dir == 0 ? IY(d, j, i) : IX(d, j, i);
+          for (int k = 0; k < nz; k++) col[k] = f[((long)t * nz + k) * pl + c];
+          remap_column(nz, fa, fb, col, res);
+          for (int k = 0; k < nz; k++) f[((long)t * nz + k) * pl + c] = res[k];
+        }
+  for (int t = 0; t < d->nt; t++)
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) {
+        long c = IC(d, j, i);
+        column_interfaces(s, t, c, P->ptop, pe);
+        reference_interfaces(nz, pe, pn);
+        for (int fi = 0; fi < 3 + s->nq; fi++) {
+          for (int k = 0; k < nz; k++) {
+            long o = ((long)t * nz + k) * d->pc + c;
+            col[k] = fi == 2 ? cf[fi][o] / s->delp[o] : cf[fi][o];
+          }
+          remap_column(nz, pe, pn, col, res);
+          for (int k = 0; k < nz; k++) {
+            long o = ((long)t * nz + k) * d->pc + c;
+            cf[fi][o] = fi == 2 ? res[k] * (pn[k + 1] - pn[k]) : res[k];
+          }
+        }
+        for (int k = 0; k < nz; k++) ndelp[((long)t * nz + k) * d->pc + c] = pn[k + 1] - pn[k];
+      }
+  memcpy(s->delp, ndelp, sizeof(double) * nc);
+  free(ndelp); free(cf); free(pe); free(pn); free(pe2); free(pn2); free(fa); free(fb); free(col); free(res);
+}
+
 int orc_run_dyn(OState* s, const OParams* P, int n_steps) {
   ODom* d = s->d;
   long nc = (long)d->nt * d->nz * d->pc;
@@ -1597,6 +1732,7 @@ int orc_run_dyn(OState* s, const OParams* P, int n_steps) {
     memset(s->acry, 0, sizeof(double) * ny); memset(s->ayfx, 0, sizeof(double) * ny);
     for (int it = 0; it < P->n_split; it++) orc_substep(s, P, -1, 1);
     if (s->nq > 0) tracer_2d(s, dp_start, P);
+    if (P->remap) orc_remap(s, P);
   }
   free(dp_start);
   return 0;

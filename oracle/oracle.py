@@ -35,7 +35,8 @@ class OParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double),
                 ("ptop", C.c_double), ("grav", C.c_double), ("rdgas", C.c_double),
-                ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int)]
+                ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int),
+                ("remap", C.c_int)]
 
 
 def _load():
@@ -86,6 +87,10 @@ def _load():
     L.orc_mlp_sym_backward.argtypes = [dp, dp, C.c_double, C.c_double, dp]
     L.orc_mlp_sym_forward.restype = C.c_double
     L.orc_mlp_sym_forward.argtypes = [dp, dp]
+    L.orc_remap_column.restype = C.c_double
+    L.orc_remap_column.argtypes = [C.c_int, dp, dp, dp, dp]
+    L.orc_remap.restype = None
+    L.orc_remap.argtypes = [C.c_void_p, C.POINTER(OParams)]
     L.orc_learned_face.restype = C.c_double
     L.orc_learned_face.argtypes = [dp, C.c_int, dp, C.c_double, C.c_int]
     _lib = L
@@ -107,7 +112,8 @@ def params(mlp=None, mlp_bf16=0, **kw):
     p = default_params()
     p.update(kw)
     prm = OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
-                  p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16))
+                  p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16),
+                  int(p.get("remap", 0)))
     if mlp is not None:
         w = _c(mlp)
         prm._w = w
@@ -231,6 +237,11 @@ class State:
     def substep(self, prm=None, stop_after=-1, accumulate=0):
         prm = prm or params()
         self.L.orc_substep(self.ptr, C.byref(prm), stop_after, accumulate)
+
+    def remap(self, prm=None):
+        """vertical remapping of every column to the reference layers (R16)"""
+        prm = prm or params()
+        self.L.orc_remap(self.ptr, C.byref(prm))
 
     def run_dyn(self, prm=None, n_steps=1):
         prm = prm or params()
@@ -402,3 +413,13 @@ def mlp_normalise(q6):
     sig = np.sqrt(v)
     inv = np.float32(1.0) / (sig + np.float32(1e-30))
     return e * inv[..., None], sig
+
+
+def remap_column(pe, pn, q):
+    """conservative piecewise-parabolic remap of layer means q from interfaces
+    pe to interfaces pn (reading R16)"""
+    L = _load()
+    pe, pn, q = _c(pe), _c(pn), _c(q)
+    out = np.empty(len(q))
+    L.orc_remap_column(len(q), _p(pe), _p(pn), _p(q), _p(out))
+    return out
