@@ -109,6 +109,7 @@ typedef struct {
   double ptop;   /* model-top pressure (Pa) */
   double grav, rdgas, cp_air;
   const void* mlp; /* hord 1: device float[1313] network parameters (see fv3_mlp_forward) */
+  int remap;       /* 1: fv3_run_dyn ends every remapping step with fv3_vertical_remap */
 } fv3_params;
 
 typedef struct {
@@ -166,6 +167,21 @@ fv3_status fv3_acoustic_substep(fv3_ctx* ctx, const fv3_state* state, const fv3_
  * as a CUDA graph (per state pointers and parameters) and replayed. */
 fv3_status fv3_run_dyn(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int n_steps,
                        fv3_stream stream);
+
+/* Vertical remapping (Section II: the model integrates on Lagrangian
+ * surfaces and remaps them to reference levels; reading R16).  Every column of
+ * every member: the reference layers are equally spaced in pressure between
+ * params->ptop and the column's surface pressure (ptop + sum of delp, kept);
+ * each field is reconstructed per layer as a monotone-limited parabola and
+ * integrated exactly over the overlaps of the old and new layers.  delp
+ * becomes the reference thickness; pt, w and the tracers are remapped as
+ * mass-weighted means, delz through delz / delp (column height kept); u and v
+ * on their face columns, whose interfaces are the means of the two adjacent
+ * cell columns' interfaces.  Column mass, tracer and momentum integrals are
+ * conserved to round-off.  The state is updated in place (the halo rings of
+ * delp are filled, the other halos are left stale).  FP64 arithmetic for
+ * both precisions.  Errors as fv3_acoustic_substep. */
+fv3_status fv3_vertical_remap(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream);
 
 /* fv_tp_2d alone (Section IX-C, "2-D mass-conserving flux-form transport";
  * readings R4-R6): the face fluxes of the scalar q for the given Courant

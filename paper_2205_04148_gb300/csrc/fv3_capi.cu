@@ -89,6 +89,7 @@ fv3_status check_params(fv3_ctx* x, const fv3_params* p) {
   if (p->nord != 1) return fail(x, FV3_ERR_UNSUPPORTED, "only nord = 1 (del-4 damping) is built");
   if (p->hord != 0 && p->hord != 1) return fail(x, FV3_ERR_UNSUPPORTED, "hord must be 0 (PPM) or 1 (learned)");
   if (p->hord == 1 && !p->mlp) return fail(x, FV3_ERR_ARG, "hord = 1 needs the network parameters (mlp)");
+  if (p->remap != 0 && p->remap != 1) return fail(x, FV3_ERR_ARG, "remap must be 0 or 1");
   if (!(p->a_imp > 0) || !(p->grav > 0) || !(p->rdgas > 0) || !(p->cp_air > p->rdgas) || !(p->ptop > 0) ||
       !(p->dz_min >= 0) || !(p->d4_bg >= 0))
     return fail(x, FV3_ERR_ARG, "physical constant out of range");
@@ -107,7 +108,7 @@ Params to_params(const fv3_params* p) {
   Params P{};
   P.dt = p->dt; P.d4_bg = p->d4_bg; P.a_imp = p->a_imp; P.dz_min = p->dz_min; P.ptop = p->ptop;
   P.grav = p->grav; P.rdgas = p->rdgas; P.cp_air = p->cp_air;
-  P.n_split = p->n_split; P.nord = p->nord; P.hord = p->hord;
+  P.n_split = p->n_split; P.nord = p->nord; P.hord = p->hord; P.remap = p->remap;
   P.mlp = (const float*)p->mlp;
   return P;
 }
@@ -263,7 +264,7 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
   // work lists
   {
     std::vector<Item> hz, dz;
-    std::vector<RowItem> rows;
+    std::vector<RowItem> rows, rows_f;
     std::vector<int4> planes;
     std::vector<int> mfirst;
     for (int m = 0; m < c.nmem; ++m) {
@@ -273,6 +274,7 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
         for (int y0 = 0; y0 < g.n; y0 += c.BYc)
           for (int x0 = 0; x0 < g.n; x0 += c.BXc) dz.push_back({m, t, x0, y0});
         for (int j = 0; j < g.n; ++j) rows.push_back({m, t, j, 0});
+        for (int j = 0; j <= g.n; ++j) rows_f.push_back({m, t, j, 0});
         for (int k = 0; k < c.nz; ++k) planes.push_back(make_int4(m, t, k, 0));
       }
     }
@@ -281,8 +283,9 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
     c.n_items_hz = (int)hz.size();
     c.n_items_dz = (int)dz.size();
     c.n_rows = (int)rows.size();
+    c.n_rows_f = (int)rows_f.size();
     c.n_planes = (int)planes.size();
-    if (c.n_rows > 65535 || c.n_planes > 65535) {
+    if (c.n_rows_f > 65535 || c.n_planes > 65535) {
       c.err = "too many tiles x levels for one launch";
       fv3_destroy(x);
       return FV3_ERR_SHAPE;
@@ -293,6 +296,8 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
     FAIL_INIT(cudaMemcpy(c.items_dz, dz.data(), sizeof(Item) * dz.size(), cudaMemcpyHostToDevice));
     FAIL_INIT(dalloc(c, &c.rows, rows.size()));
     FAIL_INIT(cudaMemcpy(c.rows, rows.data(), sizeof(RowItem) * rows.size(), cudaMemcpyHostToDevice));
+    FAIL_INIT(dalloc(c, &c.rows_f, rows_f.size()));
+    FAIL_INIT(cudaMemcpy(c.rows_f, rows_f.data(), sizeof(RowItem) * rows_f.size(), cudaMemcpyHostToDevice));
     FAIL_INIT(dalloc(c, &c.planes, planes.size()));
     FAIL_INIT(cudaMemcpy(c.planes, planes.data(), sizeof(int4) * planes.size(), cudaMemcpyHostToDevice));
     FAIL_INIT(dalloc(c, &c.mass_first, mfirst.size()));
@@ -467,6 +472,21 @@ static void enqueue_remap_step(Ctx& c, const StateView& in, const Params& P, cud
   }
   if (P.n_split % 2 == 1) enqueue_copy_state(c, in, nx, st);
   enqueue_tracers(c, in, P, st);
+  if (P.remap) enqueue_remap(c, in, P, st);
+}
+
+extern "C" fv3_status fv3_vertical_remap(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream) {
+  if (!x) return FV3_ERR_ARG;
+  fv3_status r = check_state(x, s, true);
+  if (r != FV3_OK) return r;
+  r = check_params(x, p);
+  if (r != FV3_OK) return r;
+  Ctx& c = x->c;
+  for (int q = 0; q < s->nq; ++q)
+    if (!c.qtmp[q]) CK(x, dalloc_bytes(c, &c.qtmp[q], c.elems3 * c.esize));
+  enqueue_remap(c, view(s), to_params(p), (cudaStream_t)stream);
+  CK(x, cudaGetLastError());
+  return FV3_OK;
 }
 
 extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_params* p, int n_steps,

@@ -22,6 +22,7 @@
 // produce, separated by barriers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "fv3_kernels.cuh"
@@ -78,23 +79,7 @@ __device__ __forceinline__ R ppm_face(const R* q, int s, R c) {
   return qu + (R(1) - ac) * (x - ac * (bl + br));
 }
 
-// FP64 specialisation.  On this GPU the FP64 pipe has 2 lanes per SM and per
-// clock, and FP64 compares, min/max and |x| occupy it like arithmetic does.
-// They are done here on the integer pipe instead, on the IEEE bit patterns:
-// x -> b ^ ((b >> 63) & 0x7fff...f) is an order-preserving signed integer
-// key, the magnitude bits of non-negative doubles order like the values, and
-// 2|x| is |x| with the exponent raised by one (twice the bits below the
-// normal range).  Results are the same as the generic version except for the
-// sign of zero in ties of the clamp, and except when bl*br underflows to zero
-// (opposite-signed slopes below 1e-162), neither of which changes a value.
-__device__ __forceinline__ long long okey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ long long twice_mag(long long m) {
-  return m < (1LL << 52) ? (m << 1) : m + (1LL << 52);
-}
-
+// FP64 specialisations (order-preserving integer keys, fv3_math.cuh)
 template <>
 __device__ __forceinline__ double ppm_edge<double>(double qm, double q0, double q1, double qp) {
   const double al = (7.0 / 12.0) * (q0 + q1) - (1.0 / 12.0) * (qm + qp);
@@ -215,33 +200,6 @@ struct TS {
   R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL, *GX, *GY;
 };
 
-// monotone limiter on the cell's deviations (generic, then FP64 on the
-// integer pipe -- see okey / twice_mag above)
-template <typename R>
-__device__ __forceinline__ void ppm_limit(R& bl, R& br) {
-  if (bl * br >= R(0)) {
-    bl = R(0);
-    br = R(0);
-  } else if (fabs(bl) > R(2) * fabs(br)) {
-    bl = R(-2) * br;
-  } else if (fabs(br) > R(2) * fabs(bl)) {
-    br = R(-2) * bl;
-  }
-}
-template <>
-__device__ __forceinline__ void ppm_limit<double>(double& bl, double& br) {
-  const long long sb = __double_as_longlong(bl), sr = __double_as_longlong(br);
-  const long long MAG = 0x7fffffffffffffffLL;
-  const long long mb = sb & MAG, mr = sr & MAG;
-  if ((sb ^ sr) >= 0 || mb == 0 || mr == 0) {
-    bl = 0.0;
-    br = 0.0;
-  } else if (mb > twice_mag(mr)) {
-    bl = __longlong_as_double(twice_mag(mr) | (~sr & ~MAG));
-  } else if (mr > twice_mag(mb)) {
-    br = __longlong_as_double(twice_mag(mb) | (~sb & ~MAG));
-  }
-}
 template <typename R>
 __device__ __forceinline__ bool positive(R c) { return c > R(0); }
 template <>
@@ -1427,6 +1385,23 @@ static void copy_planes(Ctx& c, const std::vector<std::pair<void*, const void*>>
 void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cudaStream_t st) {
   copy_planes(c, {{dst.u, src.u}, {dst.v, src.v}, {dst.w, src.w}, {dst.delp, src.delp}, {dst.pt, src.pt}}, nullptr,
               0, st);
+}
+
+// vertical remapping (reading R16): delp halo for the face columns, the
+// column kernel into the context's buffers, then back into the state
+void enqueue_remap(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
+  std::vector<HaloField> F;
+  F.push_back(hf(c, K_CELL3, s.delp, nullptr, c.nz, 0));
+  enqueue_halo_fields(c, F, st);
+  enqueue_remap_kernel(c, s, P.ptop, st);
+  std::vector<std::pair<void*, const void*>> pairs = {{s.u, c.nu},   {s.v, c.nv},   {s.w, c.nw},
+                                                      {s.delp, c.ndelp}, {s.pt, c.npt}, {s.delz, c.delzc}};
+  for (int q = 0; q < s.nq; ++q) pairs.push_back({s.q[q], c.qtmp[q]});
+  for (size_t b = 0; b < pairs.size(); b += MAX_TRACERS + 1) {
+    std::vector<std::pair<void*, const void*>> part(pairs.begin() + b,
+                                                    pairs.begin() + std::min(pairs.size(), b + MAX_TRACERS + 1));
+    copy_planes(c, part, nullptr, 0, st);
+  }
 }
 
 void enqueue_zero_acc(Ctx& c, cudaStream_t st) {

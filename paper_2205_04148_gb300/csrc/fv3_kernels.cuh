@@ -98,6 +98,8 @@ struct Ctx {
   int n_items_dz = 0;
   RowItem* rows = nullptr;
   int n_rows = 0;
+  RowItem* rows_f = nullptr;  // rows j = 0 .. n (face columns of the remap)
+  int n_rows_f = 0;
   int max_n = 0;
   int4* planes = nullptr;  // (m, t, k) of every level plane
   int n_planes = 0;
@@ -147,6 +149,22 @@ void enqueue_substep_f32(Ctx& c, const StateView& in, const StateView& out, cons
 void enqueue_tracers_f64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_tracers_f32(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
+
+// vertical remapping (fv3_remap.cu): caller's state in, context buffers out
+template <typename R>
+struct RemapArgs {
+  const Geo* geo;
+  double ptop;
+  const R* delp;
+  R* delp_o;
+  const R* in[3 + MAX_TRACERS];  // pt, w, delz, tracers
+  R* out[3 + MAX_TRACERS];
+  int nf;
+  const R *u, *v;
+  R *u_o, *v_o;
+};
+void enqueue_remap_kernel(Ctx& c, const StateView& s, double ptop, cudaStream_t st);
+void enqueue_remap(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 
 // standalone fv_tp_2d: caller's fields in the library layout
 struct TpPtrs {

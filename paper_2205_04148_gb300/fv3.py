@@ -31,7 +31,7 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
-           "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check")
+           "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap")
 
 
 class GridDesc(C.Structure):
@@ -48,7 +48,8 @@ class State(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double), ("ptop", C.c_double),
-                ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double), ("mlp", C.c_void_p)]
+                ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double), ("mlp", C.c_void_p),
+                ("remap", C.c_int)]
 
 
 class Layout(C.Structure):
@@ -117,6 +118,8 @@ def load(path=LIB_PATH):
     L.fv3_set_persistent.argtypes = [vp, i]
     L.fv3_get_persistent.restype = st
     L.fv3_get_persistent.argtypes = [vp, C.POINTER(i)]
+    L.fv3_vertical_remap.restype = st
+    L.fv3_vertical_remap.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp]
     L.fv3_math_check.restype = st
     L.fv3_math_check.argtypes = [i, vp, vp, vp, i, vp]
     L.fv3_fv_tp_2d.restype = st
@@ -146,7 +149,7 @@ def params(mlp=None, **kw):
     p = default_params()
     p.update(kw)
     prm = Params(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"], p["dz_min"],
-                 p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None)
+                 p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(p.get("remap", 0)))
     if mlp is not None:
         prm.mlp = C.c_void_p(mlp.data_ptr())
         prm._keep = mlp
@@ -281,6 +284,12 @@ class Grid:
         s = self.cstate(st)
         prm = prm or params()
         self.check(self.L.fv3_run_dyn(self.ptr, C.byref(s), C.byref(prm), n_steps, _stream(stream)))
+
+    def remap(self, st, prm=None, stream=None):
+        """vertical remapping of every column to the reference layers"""
+        s = self.cstate(st)
+        prm = prm or params()
+        self.check(self.L.fv3_vertical_remap(self.ptr, C.byref(s), C.byref(prm), _stream(stream)))
 
     def stage(self, st, stop_after, prm=None, stream=None):
         s = self.cstate(st)

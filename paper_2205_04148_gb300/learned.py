@@ -329,7 +329,10 @@ def coarse_eval(npx, r, nz, seed, substeps, nq, w=None):
         out, area_c, dt = _coarse_run(n, nz, seed, nq, coarse_state(init, area, npx * r // n), prm, steps)
         if n != npx:
             out = coarse_state(out, area_c, n // npx)
-        res[label] = {"npx": n, "wall_s": dt, "rel_rms_err": _rel_rms(out, truth)}
+        err = _rel_rms(out, truth)
+        qs = [v for k, v in err.items() if k.startswith("q")]
+        res[label] = {"npx": n, "wall_s": dt, "rel_rms_err": err,
+                      "tracer_mean_rel_rms_err": float(np.mean(qs)) if qs else None}
     res["t_fine"] = t_fine
     res["substeps"] = steps * n_split
     return res
