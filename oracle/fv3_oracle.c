@@ -68,6 +68,7 @@ typedef struct {
   const double* mlp;       /* 1313 network parameters (hord 1) */
   int mlp_bf16;            /* 1: inference with bfloat16 inputs/weights, float sums */
   int remap;               /* 1: vertical remapping after each remapping step (R16) */
+  int nh_full;             /* 1: close the substep: update_dz_d, riem_solver3, D-grid p_grad (R17) */
 } OParams;
 
 typedef struct {
@@ -79,6 +80,8 @@ typedef struct {
   double *uc, *vc, *delpc, *ptc, *wc, *delzc, *fx1, *fy1, *pef, *gze;
   /* flux accumulators over a remapping step */
   double *amfx, *amfy, *acrx, *acry, *axfx, *ayfx;
+  /* D-grid area fluxes of the last d_sw, layer thickness after update_dz_d */
+  double *xfxd, *yfxd, *delzd;
 } OState;
 
 /* ------------------------------------------------------------------ */
@@ -970,6 +973,7 @@ OState* orc_state_create(ODom* d, int nq) {
   s->delzc = nalloc(nc); s->fx1 = nalloc(nx); s->fy1 = nalloc(ny); s->pef = nalloc(ni); s->gze = nalloc(ni);
   s->amfx = zalloc(nx); s->amfy = zalloc(ny); s->acrx = zalloc(nx); s->acry = zalloc(ny);
   s->axfx = zalloc(nx); s->ayfx = zalloc(ny);
+  s->xfxd = zalloc(nx); s->yfxd = zalloc(ny); s->delzd = nalloc(nc);
   return s;
 }
 
@@ -977,7 +981,7 @@ void orc_state_free(OState* s) {
   if (!s) return;
   double* arr[] = {s->u, s->v, s->w, s->delp, s->pt, s->delz, s->uc, s->vc, s->delpc, s->ptc, s->wc,
                    s->delzc, s->fx1, s->fy1, s->pef, s->gze, s->amfx, s->amfy, s->acrx, s->acry,
-                   s->axfx, s->ayfx};
+                   s->axfx, s->ayfx, s->xfxd, s->yfxd, s->delzd};
   for (size_t i = 0; i < sizeof(arr) / sizeof(arr[0]); i++) free(arr[i]);
   for (int m = 0; m < s->nq; m++) free(s->q[m]);
   free(s->q);
@@ -993,7 +997,8 @@ static double* field_ptr(OState* s, const char* name, int* kind, int* nlev) {
       {"delz", s->delz, 0}, {"uc", s->uc, 1}, {"vc", s->vc, 2}, {"delpc", s->delpc, 0}, {"ptc", s->ptc, 0},
       {"wc", s->wc, 0}, {"delzc", s->delzc, 0}, {"fx1", s->fx1, 1}, {"fy1", s->fy1, 2}, {"pef", s->pef, 3},
       {"gz", s->gze, 3}, {"mfx", s->amfx, 1}, {"mfy", s->amfy, 2}, {"crx", s->acrx, 1}, {"cry", s->acry, 2},
-      {"xfx", s->axfx, 1}, {"yfx", s->ayfx, 2}};
+      {"xfx", s->axfx, 1}, {"yfx", s->ayfx, 2}, {"xfxd", s->xfxd, 1}, {"yfxd", s->yfxd, 2},
+      {"delzd", s->delzd, 0}};
   for (size_t i = 0; i < sizeof(tab) / sizeof(tab[0]); i++)
     if (!strcmp(tab[i].nm, name)) {
       *kind = tab[i].k;
@@ -1139,7 +1144,16 @@ static void c_sw(OState* s, const OParams* P) {
 /* ------------------------------------------------------------------ */
 /* update_dz_c (reading R8)                                            */
 /* ------------------------------------------------------------------ */
-static void update_dz_c(OState* s, const OParams* P) {
+/* The upwind flux-form update of the interface geopotential (reading R8)
+   with the area fluxes fx, fy (layer values; interfaces take the mean of the
+   two layers, the top interface the top layer's), new layer thickness into
+   dz_out, clamped to -dz_min.  update_dz_c uses the C-grid fluxes of c_sw
+   (dt/2), update_dz_d the D-grid fluxes of d_sw (dt; reading R17). */
+static void update_dz(OState* s, const OParams* P, const double* fx, const double* fy, double* dz_out);
+
+static void update_dz_c(OState* s, const OParams* P) { update_dz(s, P, s->fx1, s->fy1, s->delzc); }
+
+static void update_dz(OState* s, const OParams* P, const double* fx, const double* fy, double* dz_out) {
   ODom* d = s->d;
   int n = d->n, nz = d->nz;
   double g = P->grav;
@@ -1159,10 +1173,10 @@ static void update_dz_c(OState* s, const OParams* P) {
       }
     for (int K = 0; K < nz; K++) {
       const double* g0 = gz + (long)K * d->pc;
-      const double *fxa = s->fx1 + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->px,
-                   *fxb = s->fx1 + ((long)t * nz + K) * d->px;
-      const double *fya = s->fy1 + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->py,
-                   *fyb = s->fy1 + ((long)t * nz + K) * d->py;
+      const double *fxa = fx + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->px,
+                   *fxb = fx + ((long)t * nz + K) * d->px;
+      const double *fya = fy + ((long)t * nz + (K > 0 ? K - 1 : 0)) * d->py,
+                   *fyb = fy + ((long)t * nz + K) * d->py;
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
           long c = IC(d, j, i);
@@ -1186,7 +1200,7 @@ static void update_dz_c(OState* s, const OParams* P) {
         gzn[(long)nz * d->pc + c] = 0.0;
         for (int k = 0; k < nz; k++) {
           double dz = (gzn[(long)(k + 1) * d->pc + c] - gzn[(long)k * d->pc + c]) / g;
-          s->delzc[((long)t * nz + k) * d->pc + c] = fmin(dz, -P->dz_min);
+          dz_out[((long)t * nz + k) * d->pc + c] = fmin(dz, -P->dz_min);
         }
       }
   }
@@ -1360,6 +1374,98 @@ static void p_grad_c(OState* s, const OParams* P) {
 }
 
 /* ------------------------------------------------------------------ */
+/* closing the substep (reading R17, Fig. 2's update_dz_d, riem_solver3 */
+/* and nonhydrostatic D-grid pressure gradient)                        */
+/* ------------------------------------------------------------------ */
+/* riem_solver3: the column solve of R9 over the whole substep dt on the
+   state after d_sw (delp, pt, w) and the thickness of update_dz_d; new
+   layer w = mean of its two interface values, new delz = delzd + dt (W_{k+1}
+   - W_k); pef, gz as in R9. */
+static void riem_solver3(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  double *dp = zalloc(nz), *pt = zalloc(nz), *w = zalloc(nz), *dz = zalloc(nz), *pef = zalloc(nz + 1),
+         *gz = zalloc(nz + 1), *W = zalloc(nz + 1);
+  for (int t = 0; t < d->nt; t++)
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++) {
+        long c = IC(d, j, i);
+        for (int k = 0; k < nz; k++) {
+          long o = ((long)t * nz + k) * d->pc + c;
+          dp[k] = s->delp[o]; pt[k] = s->pt[o]; w[k] = s->w[o]; dz[k] = s->delzd[o];
+        }
+        orc_riem_column(nz, dp, pt, w, dz, P->dt, P->ptop, P->grav, P->rdgas, P->cp_air, P->a_imp, pef, gz, NULL,
+                        0, W);
+        for (int k = 0; k < nz; k++) {
+          long o = ((long)t * nz + k) * d->pc + c;
+          s->w[o] = 0.5 * (W[k] + W[k + 1]);
+          s->delz[o] = dz[k] + P->dt * (W[k + 1] - W[k]);
+        }
+        for (int K = 0; K <= nz; K++) {
+          long o = ((long)t * (nz + 1) + K) * d->pc + c;
+          s->pef[o] = pef[K];
+          s->gze[o] = gz[K];
+        }
+      }
+  free(dp); free(pt); free(w); free(dz); free(pef); free(gz); free(W);
+}
+
+/* interface field f (pef or gz, ring 1 filled) at corner (i, j) of tile t,
+   level K: the mean of the surrounding cells (three at a cube corner) */
+static double corner_value(const ODom* d, const double* f, int t, int K, int j, int i) {
+  const double* p = f + ((long)t * (d->nz + 1) + K) * d->pc;
+  int n = d->n;
+  if (d->cubed && (i == 0 || i == n) && (j == 0 || j == n)) {
+    /* the cell diagonal to the tile outside the corner does not exist */
+    int mi = i == 0 ? -1 : n, mj = j == 0 ? -1 : n;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int dj = -1; dj <= 0; dj++)
+      for (int di = -1; di <= 0; di++) {
+        int ci = i + di, cj = j + dj;
+        if (ci == mi && cj == mj) continue;
+        sum += p[IC(d, cj, ci)];
+        cnt++;
+      }
+    return sum / cnt;
+  }
+  return 0.25 * ((p[IC(d, j - 1, i - 1)] + p[IC(d, j - 1, i)]) + (p[IC(d, j, i - 1)] + p[IC(d, j, i)]));
+}
+
+/* D-grid pressure gradient: the contour form of R10 along each cell edge,
+   between its two corners A (first) and B, over dt */
+static void p_grad_d(OState* s, const OParams* P) {
+  ODom* d = s->d;
+  int n = d->n, nz = d->nz;
+  for (int t = 0; t < d->nt; t++) {
+    const double* rdx = d->rdx + t * d->py;
+    const double* rdy = d->rdy + t * d->px;
+    for (int k = 0; k < nz; k++) {
+      double* u = s->u + ((long)t * nz + k) * d->py;
+      double* v = s->v + ((long)t * nz + k) * d->px;
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) {
+          double gA0 = corner_value(d, s->gze, t, k, j, i), gA1 = corner_value(d, s->gze, t, k + 1, j, i);
+          double gB0 = corner_value(d, s->gze, t, k, j, i + 1), gB1 = corner_value(d, s->gze, t, k + 1, j, i + 1);
+          double pA0 = corner_value(d, s->pef, t, k, j, i), pA1 = corner_value(d, s->pef, t, k + 1, j, i);
+          double pB0 = corner_value(d, s->pef, t, k, j, i + 1), pB1 = corner_value(d, s->pef, t, k + 1, j, i + 1);
+          long o = IY(d, j, i);
+          u[o] += P->dt * rdx[o] * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
+        }
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) {
+          double gA0 = corner_value(d, s->gze, t, k, j, i), gA1 = corner_value(d, s->gze, t, k + 1, j, i);
+          double gB0 = corner_value(d, s->gze, t, k, j + 1, i), gB1 = corner_value(d, s->gze, t, k + 1, j + 1, i);
+          double pA0 = corner_value(d, s->pef, t, k, j, i), pA1 = corner_value(d, s->pef, t, k + 1, j, i);
+          double pB0 = corner_value(d, s->pef, t, k, j + 1, i), pB1 = corner_value(d, s->pef, t, k + 1, j + 1, i);
+          long o = IX(d, j, i);
+          v[o] += P->dt * rdy[o] * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
+        }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* d_sw (reading R11)                                                  */
 /* ------------------------------------------------------------------ */
 static void d_sw(OState* s, const OParams* P, int accumulate) {
@@ -1455,6 +1561,10 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
           long o = IX(d, j, i);
           v_n[ox + o] = v[o] + (-Fx[o] + ke[IK(d, j, i)] - ke[IK(d, j + 1, i)]) * rdy[o];
         }
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i <= n; i++) s->xfxd[ox + IX(d, j, i)] = xfx[IX(d, j, i)];
+      for (int j = 0; j <= n; j++)
+        for (int i = 0; i < n; i++) s->yfxd[oy + IY(d, j, i)] = yfx[IY(d, j, i)];
       if (accumulate) {
         for (int j = 0; j < n; j++)
           for (int i = 0; i <= n; i++) {
@@ -1517,6 +1627,14 @@ int orc_substep(OState* s, const OParams* P, int stop_after, int accumulate) {
   if (stop_after == 4) return 0;
   fill_faces(d, s->uc, s->vc, d->nz, H, 2, 0);
   d_sw(s, P, accumulate);
+  if (!P->nh_full || stop_after == 5) return 0;
+  update_dz(s, P, s->xfxd, s->yfxd, s->delzd);
+  if (stop_after == 6) return 0;
+  riem_solver3(s, P);
+  if (stop_after == 7) return 0;
+  fill_cells(d, s->pef, d->nz + 1, 1);
+  fill_cells(d, s->gze, d->nz + 1, 1);
+  p_grad_d(s, P);
   return 0;
 }
 

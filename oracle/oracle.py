@@ -36,7 +36,7 @@ class OParams(C.Structure):
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double),
                 ("ptop", C.c_double), ("grav", C.c_double), ("rdgas", C.c_double),
                 ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int),
-                ("remap", C.c_int)]
+                ("remap", C.c_int), ("nh_full", C.c_int)]
 
 
 def _load():
@@ -113,7 +113,7 @@ def params(mlp=None, mlp_bf16=0, **kw):
     p.update(kw)
     prm = OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
                   p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16),
-                  int(p.get("remap", 0)))
+                  int(p.get("remap", 0)), int(p.get("nh_full", 0)))
     if mlp is not None:
         w = _c(mlp)
         prm._w = w
@@ -207,9 +207,9 @@ class State:
     def _shape(self, name):
         d = self.dom
         n, nz, nt = d.n, d.nz, d.nt
-        if name in ("u", "vc", "fy1", "mfy", "cry", "yfx"):
+        if name in ("u", "vc", "fy1", "mfy", "cry", "yfx", "yfxd"):
             return (nt, nz, n + 1, n)
-        if name in ("v", "uc", "fx1", "mfx", "crx", "xfx"):
+        if name in ("v", "uc", "fx1", "mfx", "crx", "xfx", "xfxd"):
             return (nt, nz, n, n + 1)
         if name in ("pef", "gz"):
             return (nt, nz + 1, n, n)

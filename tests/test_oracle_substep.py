@@ -125,3 +125,101 @@ def test_cubed_solid_body_rotation_stays_smooth(orc):
         s.substep()
     u = s.get("u")
     assert np.isfinite(u).all() and np.abs(u).max() < 30.0
+
+
+# --- the closed substep (reading R17: update_dz_d, riem_solver3, D-grid p_grad)
+def rest(n, nz, periodic=True):
+    delp = np.full((1, nz, n, n), 1000.0)
+    pt = np.full((1, nz, n, n), 280.0)
+    return dict(u=np.zeros((1, nz, n + 1, n)), v=np.zeros((1, nz, n, n + 1)), w=np.zeros((1, nz, n, n)),
+                delp=delp, pt=pt, delz=I.hydrostatic_delz(delp, pt))
+
+
+def test_closed_substep_rest_state(orc):
+    n, nz = 12, 5
+    st = rest(n, nz)
+    d, s = make(orc, st, False, n, nz)
+    for _ in range(3):
+        s.substep(orc.params(nh_full=1))
+    assert np.abs(s.get("u")).max() <= 1e-10 and np.abs(s.get("v")).max() <= 1e-10
+    assert np.abs(s.get("w")).max() <= 1e-10
+    assert np.abs(s.get("delz") - st["delz"]).max() <= 1e-10 * np.abs(st["delz"]).max()
+    assert np.array_equal(s.get("delp"), st["delp"])
+
+
+def test_closed_substep_horizontally_uniform(orc):
+    # a vertical perturbation of w, the same in every column: the pressure
+    # gradient adds nothing, every column evolves the same way
+    n, nz = 10, 6
+    st = rest(n, nz)
+    st["w"] = np.broadcast_to(np.sin(np.arange(nz) * 0.9)[None, :, None, None], (1, nz, n, n)).copy()
+    st["u"][:] = 4.0
+    d, s = make(orc, st, False, n, nz)
+    s.substep(orc.params(nh_full=1))
+    w, dz = s.get("w"), s.get("delz")
+    assert np.abs(w - w[:, :, :1, :1]).max() <= 1e-12
+    assert np.abs(dz - dz[:, :, :1, :1]).max() <= 1e-12 * np.abs(dz).max()
+    assert np.abs(s.get("u") - 4.0).max() <= 1e-12 * 4.0 and np.abs(s.get("v")).max() <= 1e-12
+    assert np.abs(w - st["w"]).max() > 1e-3          # the column solve acted
+    # update_dz_d of uniform columns with uniform fluxes returns delz
+    _, s2 = make(orc, st, False, n, nz)
+    s2.substep(orc.params(nh_full=1), stop_after=6)
+    assert np.abs(s2.get("delzd") - st["delz"]).max() <= 1e-12 * np.abs(st["delz"]).max()
+
+
+def test_closed_substep_conserves_mass_and_stays_bounded(orc):
+    st = I.cubed_state(10, 5, seed=12, ntracers=0)
+    rng = np.random.default_rng(13)
+    st["w"] = 0.5 * rng.standard_normal(st["w"].shape)
+    d, s = make(orc, st, True, 10, 5)
+    m0 = s.mass()
+    for _ in range(30):
+        s.substep(orc.params(nh_full=1))
+    assert abs(s.mass() - m0) <= 1e-13 * m0
+    w = s.get("w")
+    assert np.isfinite(w).all() and np.abs(w).max() < 2.0      # implicit vertical waves do not grow
+    assert np.isfinite(s.get("delz")).all() and (s.get("delz") < 0).all()
+    assert np.abs(s.get("u")).max() < 40.0
+
+
+def test_closed_substep_transpose_symmetry(orc):
+    st = I.periodic_state(14, 3, seed=9)
+    rng = np.random.default_rng(10)
+    st["w"] = 0.3 * rng.standard_normal(st["w"].shape)
+    tr = dict(u=np.swapaxes(st["v"], 2, 3).copy(), v=np.swapaxes(st["u"], 2, 3).copy())
+    for f in ("w", "delp", "pt", "delz"):
+        tr[f] = np.swapaxes(st[f], 2, 3).copy()
+    d, s = make(orc, st, False, 14, 3)
+    _, s2 = make(orc, tr, False, 14, 3)
+    s.substep(orc.params(nh_full=1))
+    s2.substep(orc.params(nh_full=1))
+    for f in ("delp", "pt", "w", "delz"):
+        a, b = s.get(f), np.swapaxes(s2.get(f), 2, 3)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max(), f
+    a, b = s.get("u"), np.swapaxes(s2.get("v"), 2, 3)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_d_grid_pressure_gradient_closed_form(orc):
+    # isothermal hydrostatic air, surface pressure raised by a smooth bump in x:
+    # below the top layer the levels follow the surface pressure, so the
+    # pressure-gradient acceleration is -R T d ln(ps)/dx; the closed substep's
+    # u minus the open substep's u is dt times it, to discretisation error
+    n, nz, dx, T, eps, wd = 48, 4, 1.0e5, 280.0, 0.02, 0.15
+    x = (np.arange(n) + 0.5) / n
+    bump = np.exp(-((x - 0.5) / wd) ** 2)
+    delp = np.broadcast_to((1000.0 * (1 + eps * bump))[None, None, None, :], (1, nz, n, n)).copy()
+    pt = np.full((1, nz, n, n), T)
+    st = dict(u=np.zeros((1, nz, n + 1, n)), v=np.zeros((1, nz, n, n + 1)), w=np.zeros((1, nz, n, n)),
+              delp=delp, pt=pt, delz=I.hydrostatic_delz(delp, pt))
+    u = {}
+    for nh in (0, 1):
+        _, s = make(orc, st, False, n, nz)
+        s.substep(orc.params(nh_full=nh))
+        u[nh] = s.get("u")
+    du = u[1] - u[0]
+    dbump = -2 * (x - 0.5) / wd ** 2 * bump / (n * dx)
+    want = -20.0 * I.RDGAS * T * eps * dbump / (1 + eps * bump)
+    for k in range(1, nz):
+        for j in (0, 7, n):
+            assert np.abs(du[0, k, j] - want).max() <= 0.05 * np.abs(want).max(), (k, j)
