@@ -110,6 +110,8 @@ typedef struct {
   double grav, rdgas, cp_air;
   const void* mlp; /* hord 1: device float[1313] network parameters (see fv3_mlp_forward) */
   int remap;       /* 1: fv3_run_dyn ends every remapping step with fv3_vertical_remap */
+  int nh_full;     /* 1: each acoustic substep ends with update_dz_d, riem_solver3 and the
+                      D-grid nonhydrostatic pressure gradient (reading R17; Fig. 2) */
 } fv3_params;
 
 typedef struct {

@@ -545,6 +545,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
       const int l = B.L(i, j);
       vo[G(j, i)] = V[l] + (-FXO[l] + KE[l] - KE[l + SX]) * MT(rdy, j, i);
     });
+    if (a.xfxd) {  // the D-grid area fluxes for update_dz_d (reading R17)
+      for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
+      for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
+    }
     if (a.amfx) {
       for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
@@ -743,7 +747,10 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
 // bottom-up: back-substitution, new thickness, perturbation pressure, pef and
 // gz.  Scratch layout [5][nz][ncol], coalesced across the warp along i.
 // ------------------------------------------------------------------------
-template <typename R>
+// FULL (riem_solver3, reading R17): the whole substep dt instead of dt/2,
+// and the new layer w (mean of its two interface values) and delz written
+// back (w_o, delz_o)
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* rows) {
   const RowItem r = rows[blockIdx.y];
   const Geo g = a.geo[r.m];
@@ -757,7 +764,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
   double* s_C = a.scratch + 2LL * nz * NC;
   double* s_pp = a.scratch + 3LL * nz * NC;
   double* s_pe = a.scratch + 4LL * nz * NC;
-  const double dt = 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
+  const double dt = FULL ? a.P.dt : 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
   const double kappa = a.P.rdgas / a.P.cp_air, gama = 1.0 / (1.0 - kappa);
   // the loop-invariant quotients once; per level the reciprocals of the
   // thickness, the interface pressure, the log ratio and the pivot (FP64 here
@@ -818,6 +825,10 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     const double dzk = (double)a.delzc[o];
     const double dzn = dzk + dt * (Wn - Wk);
     const double ppn = s_pp[sidx] + s_C[sidx] * (Wn - Wk) * raimp;
+    if (FULL) {
+      a.w_o[o] = (R)(0.5 * (Wk + Wn));
+      a.delz_o[o] = (R)dzn;
+    }
     gzv = gzv - grav * dzn;
     const long long oi = fld0(g, g.offi, nz + 1, r.t, k) + q;
     const long long oib = fld0(g, g.offi, nz + 1, r.t, k + 1) + q;
@@ -865,6 +876,57 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
   if (i < n) {
     const long long A = B - g.pitch;
     a.vc[o + B] += dt2 * MT(rdyc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]);
+  }
+}
+
+// ------------------------------------------------------------------------
+// D-grid nonhydrostatic pressure gradient (reading R17): the contour form of
+// R10 along each cell edge between its corners A and B, with pef and gz at
+// the corners the means of the surrounding cells (three at a cube corner).
+// One thread per (i, j): the y-face (u) and the x-face (v) at (i, j).
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R corner_mean(const R* p, const Geo& g, int j, int i) {
+  const int n = g.n, P = g.pitch;
+  auto C = [&](int jj, int ii) { return p[(long long)jj * P + ii]; };
+  if (g.cubed && (i == 0 || i == n) && (j == 0 || j == n)) {
+    const int mi = i == 0 ? -1 : n, mj = j == 0 ? -1 : n;
+    R sum = R(0);
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        const int ci = i + di, cj = j + dj;
+        if (ci == mi && cj == mj) continue;
+        sum += C(cj, ci);
+      }
+    return sum / R(3);
+  }
+  return R(0.25) * ((C(j - 1, i - 1) + C(j - 1, i)) + (C(j, i - 1) + C(j, i)));
+}
+
+template <typename R>
+__global__ void k_p_grad_d(StepArgs<R> a, const int4* planes) {
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = a.geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = g.n;
+  if (i > n || j > n) return;
+  const int t = pl.y, k = pl.z;
+  const long long oi0 = fld0(g, g.offi, g.nz + 1, t, k), oi1 = fld0(g, g.offi, g.nz + 1, t, k + 1);
+  const R *p0 = a.pef + oi0, *p1 = a.pef + oi1, *g0 = a.gz + oi0, *g1 = a.gz + oi1;
+  const TM<R> m = tile_metric(a.M, g, t);
+  const long long o = fld0(g, g.off3, g.nz, t, k) + (long long)j * g.pitch + i;
+  const R dt = (R)a.P.dt;
+  const R pA0 = corner_mean(p0, g, j, i), pA1 = corner_mean(p1, g, j, i);
+  const R gA0 = corner_mean(g0, g, j, i), gA1 = corner_mean(g1, g, j, i);
+  if (i < n) {  // u on the y-face (i, j): corners (i, j) and (i + 1, j)
+    const R pB0 = corner_mean(p0, g, j, i + 1), pB1 = corner_mean(p1, g, j, i + 1);
+    const R gB0 = corner_mean(g0, g, j, i + 1), gB1 = corner_mean(g1, g, j, i + 1);
+    a.u_o[o] += dt * MT(rdx, j, i) * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
+  }
+  if (j < n) {  // v on the x-face (i, j): corners (i, j) and (i, j + 1)
+    const R pB0 = corner_mean(p0, g, j + 1, i), pB1 = corner_mean(p1, g, j + 1, i);
+    const R gB0 = corner_mean(g0, g, j + 1, i), gB1 = corner_mean(g1, g, j + 1, i);
+    a.v_o[o] += dt * MT(rdy, j, i) * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
   }
 }
 
@@ -1290,11 +1352,18 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   const int nwork = c.n_items_hz * kz;
   // stage ids: 0 halo fill, 1 c_sw, 2 update_dz_c, 3 riem_solver_c,
   // 4 pef/gz halo + p_grad_c, 5 C-grid halo, 6 d_sw
+  // 7 update_dz_d, 8 riem_solver3, 9 pef/gz halo + D-grid p_grad (nh_full)
   auto run = [&](int stage) {
+    if (stage >= 7 && !P.nh_full) return false;
     if (only >= 0) return stage == only;
-    const int last = stop_after >= 5 ? 6 : stop_after;
+    const int last = (stop_after == 5 || stop_after == 6) ? 6 : stop_after;
     return stage <= last;
   };
+  if (P.nh_full) {
+    a.xfxd = (R*)c.fx1;  // c_sw's fluxes are dead once update_dz_c has run
+    a.yfxd = (R*)c.fy1;
+    a.delz_o = (R*)out.delz;
+  }
   if (run(0)) enqueue_halo_prognostics(c, in, st);
   if (run(1)) {  // c_sw
     const size_t sm = blk_smem(c, 13);
@@ -1312,7 +1381,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     ++c.launches;
   }
   if (run(3)) {  // riem_solver_c
-    k_riem_c<R><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
+    k_riem_c<R, false><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
     ++c.launches;
   }
   if (run(4)) {  // pef, gz one ring into the halo, then p_grad_c
@@ -1336,6 +1405,31 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
 #undef FV3_DSW
+    ++c.launches;
+  }
+  if (run(7)) {  // update_dz_d: the D-grid area fluxes of d_sw over the state delz
+    StepArgs<R> b = a;
+    b.items = c.items_dz;
+    k_update_dz_c<R><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    ++c.launches;
+  }
+  if (run(8)) {  // riem_solver3 on the state after d_sw
+    StepArgs<R> b = a;
+    b.delpc = (R*)out.delp;
+    b.ptc = (R*)out.pt;
+    b.wc = (R*)out.w;
+    k_riem_c<R, true><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(b, c.rows);
+    ++c.launches;
+  }
+  if (run(9)) {  // pef, gz into the halo, then the D-grid pressure gradient
+    // (the corner means need the diagonal halo cells too, which the depth-1
+    // plan of p_grad_c leaves out: the full plan fills them)
+    std::vector<HaloField> F;
+    F.push_back(hf(c, K_CELL3, c.pef, nullptr, c.nz + 1, 1));
+    F.push_back(hf(c, K_CELL3, c.gz, nullptr, c.nz + 1, 1));
+    enqueue_halo_fields(c, F, st);
+    const int nb = (c.max_n + 1 + 15) / 16;
+    k_p_grad_d<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
     ++c.launches;
   }
 }

@@ -28,6 +28,9 @@ struct StepArgs {
   long long ncol;        // columns of all members
   // flux accumulators of the remapping step (null: not accumulating)
   R *amfx, *amfy, *acrx, *acry, *axfx, *ayfx;
+  // closed substep (reading R17): d_sw's area fluxes out (null: not kept),
+  // the column solve's new delz
+  R *xfxd, *yfxd, *delz_o;
   unsigned* status;
   const float* mlp;      // face-value network (hord 1), float[1313] on the device
 };
