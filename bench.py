@@ -45,6 +45,11 @@ DSW_FLOPS_PER_CELL = 655
 # uc, vc and writes u, v, w, delp, pt (12 words).
 DSW_WORDS_PER_CELL = 12
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
+# DRAM bytes (read + write) per cell of one d_sw launch, from an ncu capture of
+# the kernel in this launch configuration (profiles/k_d_sw_fp64_c96x24.md:
+# C96 x 24, FP64, 16 x 16 blocks, one level per work item, persistent grid);
+# scaled by the cells of the timed launch.  Other configurations report null.
+DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 199.0}
 
 
 def parse():
@@ -279,10 +284,13 @@ def ours(a):
     torch.cuda.synchronize()
     fp64_meas = work.value * 3 / (c0.elapsed_time(c1) / 1e3) / 1e9
     esize = 8 if prec == fv3.FP64 else 4
+    bx, by, kc = g.tiles()
+    tkey = ("f64" if prec == fv3.FP64 else "f32", bx, by, kc, g.persistent())
+    traffic = DSW_TRAFFIC_BYTES_PER_CELL[tkey] * cells if tkey in DSW_TRAFFIC_BYTES_PER_CELL else None
     if prec == fv3.FP64:
         ach = DSW_FLOPS_PER_CELL * cells / t_dsw / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
-                "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": None, "kernel": "k_d_sw<double>",
+                "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": traffic, "kernel": "k_d_sw<double>",
                 "ms_per_launch": t_dsw * 1e3, "flops_per_cell": DSW_FLOPS_PER_CELL,
                 "peak_measured_fma": fp64_meas,
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it"}
@@ -294,7 +302,7 @@ def ours(a):
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         ach = DSW_WORDS_PER_CELL * esize * cells / t_dsw / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
                 "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3}
 
     # --- end to end through the C-ABI with host buffers ------------------
