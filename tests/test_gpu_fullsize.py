@@ -1,0 +1,84 @@
+"""Parity at the benchmark's sizes, in the launch configuration bench.py
+times (autotuned block shape and launch mode): the C96 x 80 FP64 substep and
+remapping step against the oracle on every element, members of the 24-member
+FP32 ensemble against the oracle, and the edge cases of the interface (zero
+steps, size limits)."""
+import numpy as np
+import pytest
+
+from gpu_common import FIELDS, TOL64, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def test_c96x80_fp64_substep_and_step(orc):
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+    n, nz, nq = 96, 80, 8
+    st = I.cubed_state(n, nz, seed=0, ntracers=nq)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz)
+    gs = g.alloc_state(nq)
+    g.load(gs, st)
+    g.autotune(gs)
+    g.load(gs, st)
+    g.substep(gs)
+    s = orc.State(orc.Domain(True, n, nz), nq)
+    s.load(st)
+    s.substep()
+    for f in FIELDS:
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= TOL64, (f, e)
+    # a whole remapping step with the tracers, from the same start
+    g.load(gs, st)
+    g.run_dyn(gs, fv3.params(n_split=6), 1)
+    s2 = orc.State(orc.Domain(True, n, nz), nq)
+    s2.load(st)
+    s2.run_dyn(orc.params(n_split=6), 1)
+    for f in FIELDS + tuple("q%d" % k for k in range(nq)):
+        e = relerr(g.read(gs, f), s2.get(f))
+        assert e <= 10 * TOL64, (f, e)
+
+
+def test_batched_ensemble_members(orc):
+    """the 8 x C48 + 8 x C96 + 8 x C128 x 80 FP32 ensemble, one substep in
+    one launch per stage; one member of each size against the oracle"""
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+    sizes, nz = [48] * 8 + [96] * 8 + [128] * 8, 80
+    base = {n: I.cubed_state(n, nz, seed=0, ntracers=0) for n in (48, 96, 128)}
+    g = fv3.Grid(fv3.GRID_CUBED, 128, nz, n_members=24, member_npx=sizes, precision=fv3.FP32)
+    gs = g.alloc_state()
+    members = {}
+    for m, n in enumerate(sizes):
+        st = I.perturb_member(base[n], m)
+        if m in (3, 11, 19):
+            members[m] = st
+        g.load(gs, st, member=m)
+    g.set_tiles(32, 8, 4)
+    g.set_persistent(True)
+    g.substep(gs)
+    for m, st in members.items():
+        n = sizes[m]
+        s = orc.State(orc.Domain(True, n, nz))
+        s.load(st)
+        s.substep()
+        for f in ("u", "v", "delp", "pt"):
+            e = relerr(g.read(gs, f, member=m), s.get(f))
+            assert e <= 2e-4, (m, f, e)
+
+
+def test_zero_steps_and_limits():
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+    st = I.cubed_state(8, 3, seed=1, ntracers=1)
+    g = fv3.Grid(fv3.GRID_CUBED, 8, 3)
+    gs = g.alloc_state(1)
+    g.load(gs, st)
+    before = {f: g.read(gs, f) for f in FIELDS + ("q0",)}
+    g.run_dyn(gs, fv3.params(), 0)
+    for f, a in before.items():
+        assert np.array_equal(g.read(gs, f), a), f
+    with pytest.raises(fv3.Fv3Error, match="SHAPE"):
+        fv3.Grid(fv3.GRID_CUBED, 8, 1025)                       # levels beyond the limit
+    with pytest.raises(fv3.Fv3Error, match="SHAPE"):
+        fv3.Grid(fv3.GRID_CUBED, 64, 2, n_members=200)          # rows beyond one launch's grid
