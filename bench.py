@@ -15,9 +15,17 @@ stream, barrier + synchronize on both sides, max over ranks.  The state
 L2, so no flush is needed.  SM clocks are sampled with nvidia-smi during the
 timed region.
 
+Before timing, the block shape, level chunk and launch mode are autotuned
+(fv3_autotune; --tiles or --no-autotune to fix them).  Beside the timed
+region: the dominant kernel (d_sw) timed alone for the roofline object, an
+end-to-end pass through the C-ABI with host buffers (e2e), and the CPU oracle
+on a level subset of the same remapping step (cpu_baseline).  Other
+workloads: --precision fp32 --npx 192 (FP32 bulk), --workload batched (the
+24-member ensemble), --workload modules (riem_solver_c and fv_tp_2d alone).
+
 --impl reference times the CPU oracle (oracle/, plain C, one thread) on a
-bounded sample of the same workload (a level subset of C96, one acoustic
-substep per step), on the host cores of this machine.
+bounded sample of the same workload (one remapping step on a level subset of
+C96 per step), on the host cores of this machine.
 """
 from __future__ import annotations
 
@@ -136,49 +144,45 @@ def dist():
     return replicas.world()
 
 
-def cpu_oracle_rate(npx, nz_sample, reps=1):
-    """Oracle (plain C, one thread) time of one acoustic substep on C{npx} x
-    nz_sample levels; returns (cell-substeps/s, seconds)."""
+def _oracle_step_rate(npx, nz_sample, nq, n_split, steps, warmup):
+    """Oracle (plain C, one thread) remapping steps -- n_split acoustic
+    substeps and tracer_2d of nq tracers -- on C{npx} x nz_sample levels;
+    returns (cell-substeps/s, seconds per step)."""
     from oracle import oracle as O
     from paper_2205_04148_gb300 import inputs as I
-    st = I.cubed_state(npx, nz_sample, seed=0, ntracers=0)
-    d = O.Domain(True, npx, nz_sample)
-    s = O.State(d)
+    st = I.cubed_state(npx, nz_sample, seed=0, ntracers=nq)
+    s = O.State(O.Domain(True, npx, nz_sample), nq)
     s.load(st)
+    prm = O.params(n_split=n_split)
+    for _ in range(warmup):
+        s.run_dyn(prm, 1)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        s.substep()
-    dt = (time.perf_counter() - t0) / reps
-    return 6 * npx * npx * nz_sample / dt, dt
+    for _ in range(steps):
+        s.run_dyn(prm, 1)
+    dt = (time.perf_counter() - t0) / max(1, steps)
+    return n_split * 6 * npx * npx * nz_sample / dt, dt
 
 
 def reference_arm(a):
+    """The reference arm: the FP64 oracle timed on this machine's host cores on
+    the same workload as ours (one remapping step of n_split substeps and the
+    tracer step per bench step) over a level subset sized so that all the
+    warm-up and timed steps take about two minutes."""
     ws, rank, _ = dist()
     if rank != 0:
         return 0
-    # size the per-step sample so that (K + W) steps take about two minutes
-    rate1, t1 = cpu_oracle_rate(a.npx, 2)
-    per_level = t1 / 2
+    _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0)
+    per_level = t2 / 2
     budget = 120.0 / max(1, a.steps + a.warmup)
-    nzs = int(max(1, min(a.npz, budget / per_level)))
-    from oracle import oracle as O
-    from paper_2205_04148_gb300 import inputs as I
-    st = I.cubed_state(a.npx, nzs, seed=0, ntracers=0)
-    d = O.Domain(True, a.npx, nzs)
-    s = O.State(d)
-    s.load(st)
-    for _ in range(a.warmup):
-        s.substep()
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        s.substep()
-    dt = (time.perf_counter() - t0) / max(1, a.steps)
-    value = 6 * a.npx * a.npx * nzs / dt
-    sample = "one acoustic substep of C%d x %d levels (of %d) per step, FP64 oracle, 1 thread" % (a.npx, nzs, a.npz)
+    nzs = int(max(2, min(a.npz, budget / per_level)))
+    value, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, a.steps, a.warmup)
+    sample = ("one remapping step (%d acoustic substeps + tracer_2d of %d tracers) of C%d x %d levels (of %d) "
+              "per step, FP64 oracle, 1 thread" % (a.n_split, a.nq, a.npx, nzs, a.npz))
     out = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "cubed-sphere C%d x %d levels, FP64, n_split %d" % (a.npx, a.npz, a.n_split),
+           "config": {"workload": "cubed-sphere C%d x %d levels, FP64, n_split %d, %d tracers, one remapping "
+                                  "step per bench step" % (a.npx, a.npz, a.n_split, a.nq),
                       "sample_levels": nzs},
            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -352,11 +356,13 @@ def ours(a):
     # --- CPU oracle baseline (rank 0, N = 1) -----------------------------
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        nzs, reps = a.npz, 3
-        rate, dt = cpu_oracle_rate(a.npx, nzs, reps)
+        # the same remapping step on a level subset sized to about 15 s
+        _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0)
+        nzs = int(max(2, min(a.npz, 15.0 / (t2 / 2))))
+        rate, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, 1, 0)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": "%d acoustic substeps of C%d x %d levels, FP64 oracle, 1 thread (%.1f s each)"
-                         % (reps, a.npx, nzs, dt)}
+               "sample": "one remapping step (%d acoustic substeps + tracer_2d of %d tracers) of C%d x %d levels "
+                         "(of %d), FP64 oracle, 1 thread (%.1f s)" % (a.n_split, a.nq, a.npx, nzs, a.npz, dt)}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps,
