@@ -300,6 +300,15 @@ size_t fv3_mlp_work_floats(int n);
 fv3_status fv3_mlp_grad(const float* w, const float* x, const float* t, int n, float weight, float* work,
                         float* grad, float* loss, fv3_stream stream);
 
+/* The same gradient in float arithmetic without bfloat16 rounding (SIMT,
+ * library tanhf): the reference the tensor-core gradient and the float
+ * training path are checked against (no counterpart in the paper).  Work:
+ * fv3_mlp_work_floats_fp32(n) floats.  Deterministic; slow (one thread per
+ * parameter sums over the samples), meant for checks, not training. */
+size_t fv3_mlp_work_floats_fp32(int n);
+fv3_status fv3_mlp_grad_fp32(const float* w, const float* x, const float* t, int n, float weight, float* work,
+                             float* grad, float* loss, fv3_stream stream);
+
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected, step >= 1) on
  * float master weights w with moments m, v. */
 fv3_status fv3_mlp_adam(float* w, float* m, float* v, const float* grad, int step, float lr, fv3_stream stream);

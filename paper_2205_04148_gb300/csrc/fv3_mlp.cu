@@ -225,6 +225,82 @@ __global__ void k_mlp_adam(float* w, float* m, float* v, const float* g, float l
   w[p] -= lr * (mp / c1) / (sqrtf(vp / c2) + eps);
 }
 
+// FP32 reference gradient (SIMT, float arithmetic, library tanhf): the same
+// objective as k_mlp_grad without bfloat16 rounding, for checking the
+// tensor-core gradient and the float training path against the FP64 oracle.
+// Pass 1 stores per sample and stencil order the inputs, activations and
+// pre-activation gradients; pass 2 sums every parameter's gradient over the
+// samples in a fixed order (one thread per parameter, deterministic).
+constexpr int kAct = 6 + 32 + 32 + 32 + 32 + 1;  // x, h1, h2, d2, d1, dy per order
+
+__global__ void k_mlp_fp32_act(const float* w, const float* x, const float* t, int n, float wt, float* act) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float* A = act + (long long)s * (2 * kAct + 1);
+  float y[2];
+  for (int o = 0; o < 2; ++o) {
+    float* xo = A + o * kAct;
+    float *h1 = xo + 6, *h2 = h1 + 32;
+    for (int i = 0; i < 6; ++i) xo[i] = x[6 * s + (o ? 5 - i : i)];
+    for (int j = 0; j < 32; ++j) {
+      float z = w[MLP_B1 + j];
+      for (int i = 0; i < 6; ++i) z = fmaf(xo[i], w[MLP_W1 + i * 32 + j], z);
+      h1[j] = tanhf(z);
+    }
+    for (int j = 0; j < 32; ++j) {
+      float z = w[MLP_B2 + j];
+      for (int i = 0; i < 32; ++i) z = fmaf(h1[i], w[MLP_W2 + i * 32 + j], z);
+      h2[j] = tanhf(z);
+    }
+    float v = w[MLP_B3];
+    for (int i = 0; i < 32; ++i) v = fmaf(h2[i], w[MLP_W3 + i], v);
+    y[o] = v;
+  }
+  const float ys = 0.5f * (y[0] + y[1]);
+  const float r = ys - t[s];
+  A[2 * kAct] = 0.5f * r * r * wt;
+  const float dy = 0.5f * r * wt;  // d loss / d y of each order
+  for (int o = 0; o < 2; ++o) {
+    float* xo = A + o * kAct;
+    float *h1 = xo + 6, *h2 = h1 + 32, *d2 = h2 + 32, *d1 = d2 + 32;
+    for (int j = 0; j < 32; ++j) d2[j] = dy * w[MLP_W3 + j] * (1.f - h2[j] * h2[j]);
+    for (int i = 0; i < 32; ++i) {
+      float a = 0.f;
+      for (int j = 0; j < 32; ++j) a = fmaf(w[MLP_W2 + i * 32 + j], d2[j], a);
+      d1[i] = a * (1.f - h1[i] * h1[i]);
+    }
+    d1[32] = dy;  // the output's gradient, after d1
+  }
+}
+
+__global__ void k_mlp_fp32_sum(const float* act, int n, float* grad, float* loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > MLP_NP) return;
+  float sum = 0.f;
+  for (int s = 0; s < n; ++s) {
+    const float* A = act + (long long)s * (2 * kAct + 1);
+    if (p == MLP_NP) {
+      sum += A[2 * kAct];
+      continue;
+    }
+    for (int o = 0; o < 2; ++o) {
+      const float* xo = A + o * kAct;
+      const float *h1 = xo + 6, *h2 = h1 + 32, *d2 = h2 + 32, *d1 = d2 + 32;
+      const float dy = d1[32];
+      float g;
+      if (p < MLP_B1) g = xo[p / 32] * d1[p % 32];
+      else if (p < MLP_W2) g = d1[p - MLP_B1];
+      else if (p < MLP_B2) g = h1[(p - MLP_W2) / 32] * d2[(p - MLP_W2) % 32];
+      else if (p < MLP_W3) g = d2[p - MLP_B2];
+      else if (p < MLP_B3) g = h2[p - MLP_W3] * dy;
+      else g = dy;
+      sum += g;
+    }
+  }
+  if (p < MLP_NP) grad[p] = sum;
+  else if (loss) *loss = sum;
+}
+
 int grad_blocks(int n) {
   const int per = kThreads;  // samples per block per pass
   int b = (n + per - 1) / per;
@@ -254,6 +330,17 @@ extern "C" fv3_status fv3_mlp_grad(const float* w, const float* x, const float* 
   cudaStream_t st = (cudaStream_t)stream;
   k_mlp_grad<<<blocks, kThreads, 0, st>>>(w, x, t, n, weight, work);
   k_mlp_reduce<<<(MLP_NP + 1 + 255) / 256, 256, 0, st>>>(work, blocks, grad, loss);
+  return cudaGetLastError() == cudaSuccess ? FV3_OK : FV3_ERR_CUDA;
+}
+
+extern "C" size_t fv3_mlp_work_floats_fp32(int n) { return (size_t)(n > 0 ? n : 0) * (2 * kAct + 1); }
+
+extern "C" fv3_status fv3_mlp_grad_fp32(const float* w, const float* x, const float* t, int n, float weight,
+                                        float* work, float* grad, float* loss, fv3_stream stream) {
+  if (!w || !x || !t || !work || !grad || n < 1) return FV3_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_mlp_fp32_act<<<(n + 127) / 128, 128, 0, st>>>(w, x, t, n, weight, work);
+  k_mlp_fp32_sum<<<(MLP_NP + 1 + 127) / 128, 128, 0, st>>>(work, n, grad, loss);
   return cudaGetLastError() == cudaSuccess ? FV3_OK : FV3_ERR_CUDA;
 }
 

@@ -31,7 +31,8 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
-           "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap")
+           "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap",
+           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32")
 
 
 class GridDesc(C.Structure):
@@ -134,6 +135,10 @@ def load(path=LIB_PATH):
     L.fv3_mlp_work_floats.argtypes = [i]
     L.fv3_mlp_grad.restype = st
     L.fv3_mlp_grad.argtypes = [vp, vp, vp, i, C.c_float, vp, vp, vp, vp]
+    L.fv3_mlp_work_floats_fp32.restype = C.c_size_t
+    L.fv3_mlp_work_floats_fp32.argtypes = [i]
+    L.fv3_mlp_grad_fp32.restype = st
+    L.fv3_mlp_grad_fp32.argtypes = [vp, vp, vp, i, C.c_float, vp, vp, vp, vp]
     L.fv3_mlp_adam.restype = st
     L.fv3_mlp_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
     L.fv3_riem_solver_c_noalloc.restype = st
@@ -415,6 +420,20 @@ class MlpTrainer:
                                  C.c_void_p(self.g.data_ptr()), C.c_void_p(self.loss.data_ptr()), _stream(None)),
              "fv3_mlp_grad")
         return self.g, self.loss
+
+    def grad_fp32(self, x, t, weight=None):
+        """the same gradient in float arithmetic (the check path, slow)"""
+        import torch
+        n = x.shape[0]
+        work = torch.empty(int(self.L.fv3_mlp_work_floats_fp32(n)), dtype=torch.float32, device="cuda")
+        g = torch.empty_like(self.g)
+        loss = torch.empty_like(self.loss)
+        wt = 1.0 / n if weight is None else weight
+        _chk(self.L.fv3_mlp_grad_fp32(C.c_void_p(self.w.data_ptr()), C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(t.data_ptr()), n, wt, C.c_void_p(work.data_ptr()),
+                                      C.c_void_p(g.data_ptr()), C.c_void_p(loss.data_ptr()), _stream(None)),
+             "fv3_mlp_grad_fp32")
+        return g, loss
 
     def update(self, x, t):
         self.grad(x, t)

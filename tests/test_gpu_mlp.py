@@ -53,6 +53,29 @@ def test_gradient_matches_oracle(orc):
         assert err <= 2e-2, (lo, hi, err)
 
 
+def test_fp32_gradient_matches_oracle(orc):
+    """the float check path: within 1e-5 of the FP64 gradient, and the
+    tensor-core gradient within 2e-2 of it"""
+    from paper_2205_04148_gb300 import build, fv3
+    build.build()
+    rng = np.random.default_rng(7)
+    w = orc.mlp_init(8)
+    n = 513
+    X = rng.standard_normal((n, 6))
+    T = rng.standard_normal(n) * 0.5
+    tr = fv3.MlpTrainer(w)
+    g32, loss32 = tr.grad_fp32(cuda(X), cuda(T), weight=1.0 / n)
+    g32 = g32.cpu().numpy()
+    l64, g64 = orc.mlp_sym_grad(w, X, T, 1.0 / n)
+    assert abs(float(loss32.item()) - l64) <= 1e-5 * l64
+    for lo, hi in ((0, 192), (192, 224), (224, 1248), (1248, 1280), (1280, 1312), (1312, 1313)):
+        err = np.abs(g32[lo:hi] - g64[lo:hi]).max() / np.abs(g64[lo:hi]).max()
+        assert err <= 1e-5, (lo, hi, err)
+    gbf, _ = tr.grad(cuda(X), cuda(T), weight=1.0 / n)
+    gbf = gbf.cpu().numpy()
+    assert np.abs(gbf - g32).max() <= 2e-2 * np.abs(g32).max()
+
+
 def test_adam_fits_a_smooth_target(orc):
     from paper_2205_04148_gb300 import build, fv3
     build.build()
