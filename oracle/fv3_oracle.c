@@ -69,6 +69,7 @@ typedef struct {
   int mlp_bf16;            /* 1: inference with bfloat16 inputs/weights, float sums */
   int remap;               /* 1: vertical remapping after each remapping step (R16) */
   int nh_full;             /* 1: close the substep: update_dz_d, riem_solver3, D-grid p_grad (R17) */
+  int d2c_ord;             /* C-grid winds from the D-grid: 2 (4-point means, R7) or 4 (R18) */
 } OParams;
 
 typedef struct {
@@ -1035,6 +1036,43 @@ int orc_state_io(OState* s, const char* name, double* dense, int dir) {
 /* ------------------------------------------------------------------ */
 /* c_sw (reading R7)                                                   */
 /* ------------------------------------------------------------------ */
+/* C-grid winds from the D-grid winds of one level (reading R7: the mean of
+   the four surrounding D-grid values; reading R18: fourth order, a four-point
+   Lagrange interpolation (-1, 9, 9, -1)/16 first along the D-grid component's
+   own direction to the face's line, then across).  uc0 on x-faces
+   j in [-1, n], i in [-1, n+1]; vc0 on y-faces j in [-1, n+1], i in [-1, n]. */
+static double lag4(double a, double b, double c, double d) { return 0.0625 * (9.0 * (b + c) - (a + d)); }
+
+static void d2c_winds(const ODom* d, const double* u, const double* v, int ord, double* uc0, double* vc0) {
+  int n = d->n;
+  for (int j = -1; j <= n; j++)
+    for (int i = -1; i <= n + 1; i++) {
+      if (ord == 4) {
+        double a[4];
+        for (int r = 0; r < 4; r++) {
+          int jj = j - 1 + r;
+          a[r] = lag4(u[IY(d, jj, i - 2)], u[IY(d, jj, i - 1)], u[IY(d, jj, i)], u[IY(d, jj, i + 1)]);
+        }
+        uc0[IX(d, j, i)] = lag4(a[0], a[1], a[2], a[3]);
+      } else {
+        uc0[IX(d, j, i)] = 0.25 * (u[IY(d, j, i - 1)] + u[IY(d, j, i)] + u[IY(d, j + 1, i - 1)] + u[IY(d, j + 1, i)]);
+      }
+    }
+  for (int j = -1; j <= n + 1; j++)
+    for (int i = -1; i <= n; i++) {
+      if (ord == 4) {
+        double b[4];
+        for (int r = 0; r < 4; r++) {
+          int ii = i - 1 + r;
+          b[r] = lag4(v[IX(d, j - 2, ii)], v[IX(d, j - 1, ii)], v[IX(d, j, ii)], v[IX(d, j + 1, ii)]);
+        }
+        vc0[IY(d, j, i)] = lag4(b[0], b[1], b[2], b[3]);
+      } else {
+        vc0[IY(d, j, i)] = 0.25 * (v[IX(d, j - 1, i)] + v[IX(d, j - 1, i + 1)] + v[IX(d, j, i)] + v[IX(d, j, i + 1)]);
+      }
+    }
+}
+
 static void c_sw(OState* s, const OParams* P) {
   ODom* d = s->d;
   int n = d->n, nz = d->nz;
@@ -1055,17 +1093,16 @@ static void c_sw(OState* s, const OParams* P) {
       long oc = ((long)t * nz + k) * d->pc, ox = ((long)t * nz + k) * d->px, oy = ((long)t * nz + k) * d->py;
       const double *u = s->u + oy, *v = s->v + ox;
       const double *delp = s->delp + oc, *pt = s->pt + oc, *w = s->w + oc;
-      /* 1-2. C-grid winds from the D-grid by 4-point averages; contravariant */
+      /* 1-2. C-grid winds from the D-grid (R7 / R18); contravariant */
+      d2c_winds(d, u, v, P->d2c_ord, uc0, vc0);
       for (int j = -1; j <= n; j++)
         for (int i = -1; i <= n + 1; i++) {
           long o = IX(d, j, i);
-          uc0[o] = 0.25 * (u[IY(d, j, i - 1)] + u[IY(d, j, i)] + u[IY(d, j + 1, i - 1)] + u[IY(d, j + 1, i)]);
           ut[o] = (uc0[o] - cosx[o] * v[o]) / (sinx[o] * sinx[o]);
         }
       for (int j = -1; j <= n + 1; j++)
         for (int i = -1; i <= n; i++) {
           long o = IY(d, j, i);
-          vc0[o] = 0.25 * (v[IX(d, j - 1, i)] + v[IX(d, j - 1, i + 1)] + v[IX(d, j, i)] + v[IX(d, j, i + 1)]);
           vt[o] = (vc0[o] - cosy[o] * u[o]) / (siny[o] * siny[o]);
         }
       /* 3. upwind half-step of delp, pt, w */
@@ -1932,6 +1969,27 @@ int orc_delnflux_dense(ODom* d, int t, const double* q, double damp, double* Fx_
     for (int i = 0; i < n; i++) Fy_out[(long)j * n + i] = Fy[IY(d, j, i)];
   work_free(&w);
   free(Q); free(Fx); free(Fy);
+  return 0;
+}
+
+/* C-grid winds of level 0 of tile t from dense D-grid winds of all tiles:
+   u [nt][n+1][n], v [nt][n][n+1] -> uc [n][n+1], vc [n+1][n] (interior) */
+int orc_d2c_dense(ODom* d, int t, const double* u, const double* v, int ord, double* uc_out, double* vc_out) {
+  int n = d->n, nt = d->nt;
+  double *U = nalloc(nt * d->py), *V = nalloc(nt * d->px), *UC = zalloc(d->px), *VC = zalloc(d->py);
+  for (int tt = 0; tt < nt; tt++) {
+    for (int j = 0; j <= n; j++)
+      for (int i = 0; i < n; i++) U[tt * d->py + IY(d, j, i)] = u[((long)tt * (n + 1) + j) * n + i];
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i <= n; i++) V[tt * d->px + IX(d, j, i)] = v[((long)tt * n + j) * (n + 1) + i];
+  }
+  fill_faces(d, V, U, 1, H, 1, 1);
+  d2c_winds(d, U + t * d->py, V + t * d->px, ord, UC, VC);
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i <= n; i++) uc_out[(long)j * (n + 1) + i] = UC[IX(d, j, i)];
+  for (int j = 0; j <= n; j++)
+    for (int i = 0; i < n; i++) vc_out[(long)j * n + i] = VC[IY(d, j, i)];
+  free(U); free(V); free(UC); free(VC);
   return 0;
 }
 

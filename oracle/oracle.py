@@ -36,7 +36,7 @@ class OParams(C.Structure):
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double),
                 ("ptop", C.c_double), ("grav", C.c_double), ("rdgas", C.c_double),
                 ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int),
-                ("remap", C.c_int), ("nh_full", C.c_int)]
+                ("remap", C.c_int), ("nh_full", C.c_int), ("d2c_ord", C.c_int)]
 
 
 def _load():
@@ -87,6 +87,8 @@ def _load():
     L.orc_mlp_sym_backward.argtypes = [dp, dp, C.c_double, C.c_double, dp]
     L.orc_mlp_sym_forward.restype = C.c_double
     L.orc_mlp_sym_forward.argtypes = [dp, dp]
+    L.orc_d2c_dense.restype = C.c_int
+    L.orc_d2c_dense.argtypes = [C.c_void_p, C.c_int, dp, dp, C.c_int, dp, dp]
     L.orc_remap_column.restype = C.c_double
     L.orc_remap_column.argtypes = [C.c_int, dp, dp, dp, dp]
     L.orc_remap.restype = None
@@ -113,7 +115,7 @@ def params(mlp=None, mlp_bf16=0, **kw):
     p.update(kw)
     prm = OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
                   p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16),
-                  int(p.get("remap", 0)), int(p.get("nh_full", 0)))
+                  int(p.get("remap", 0)), int(p.get("nh_full", 0)), int(p.get("d2c_ord", 2)))
     if mlp is not None:
         w = _c(mlp)
         prm._w = w
@@ -423,3 +425,15 @@ def remap_column(pe, pn, q):
     out = np.empty(len(q))
     L.orc_remap_column(len(q), _p(pe), _p(pn), _p(q), _p(out))
     return out
+
+
+def d2c(dom, tile, u, v, ord=2):
+    """C-grid winds (uc on x-faces, vc on y-faces) of tile ``tile`` from dense
+    level-0 D-grid winds of all tiles (readings R7, R18)"""
+    L = _load()
+    n = dom.n
+    u, v = _c(u), _c(v)
+    uc = np.empty((n, n + 1))
+    vc = np.empty((n + 1, n))
+    L.orc_d2c_dense(dom.ptr, tile, _p(u), _p(v), int(ord), _p(uc), _p(vc))
+    return uc, vc
