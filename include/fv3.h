@@ -112,6 +112,9 @@ typedef struct {
   int remap;       /* 1: fv3_run_dyn ends every remapping step with fv3_vertical_remap */
   int nh_full;     /* 1: each acoustic substep ends with update_dz_d, riem_solver3 and the
                       D-grid nonhydrostatic pressure gradient (reading R17; Fig. 2) */
+  int d2c_ord;     /* C-grid winds in c_sw from the D-grid winds: 2 (mean of the four
+                      surrounding values) or 4 (four-point Lagrange along, then across;
+                      reading R18); 0 means 2 */
 } fv3_params;
 
 typedef struct {

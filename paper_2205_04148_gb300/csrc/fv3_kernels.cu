@@ -596,8 +596,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
-    for2(x0 - 2, x1 + 2, y0 - 1, y1 + 2, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-    for2(x0 - 1, x1 + 2, y0 - 2, y1 + 2, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    const bool ord4 = a.P.d2c_ord == 4;
+    if (ord4) {  // the fourth-order stencils reach one ring further
+      for2(x0 - 3, x1 + 3, y0 - 2, y1 + 3, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+      for2(x0 - 2, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    } else {
+      for2(x0 - 2, x1 + 2, y0 - 1, y1 + 2, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+      for2(x0 - 1, x1 + 2, y0 - 2, y1 + 2, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    }
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = G(j, i);
@@ -606,15 +612,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
       W[l] = w[q];
     });
     __syncthreads();
+    // C-grid winds from the D-grid: the mean of the four surrounding values
+    // (reading R7) or four-point Lagrange interpolation (-1, 9, 9, -1) / 16
+    // along the component's direction, then across (reading R18)
+    auto lag4 = [](R a0, R a1, R a2, R a3) { return R(0.0625) * (R(9) * (a1 + a2) - (a0 + a3)); };
     for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R c0 = R(0.25) * (U[l - 1] + U[l] + U[l - 1 + SX] + U[l + SX]);
+      R c0;
+      if (ord4) {
+        auto ax = [&](int r) { return lag4(U[r - 2], U[r - 1], U[r], U[r + 1]); };
+        c0 = lag4(ax(l - SX), ax(l), ax(l + SX), ax(l + 2 * SX));
+      } else {
+        c0 = R(0.25) * (U[l - 1] + U[l] + U[l - 1 + SX] + U[l + SX]);
+      }
       UC0[l] = c0;
       UT[l] = (c0 - MT(cosx, j, i) * V[l]) * MT(rsin2x, j, i);
     });
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R c0 = R(0.25) * (V[l - SX] + V[l - SX + 1] + V[l] + V[l + 1]);
+      R c0;
+      if (ord4) {
+        auto by = [&](int r) { return lag4(V[r - 2 * SX], V[r - SX], V[r], V[r + SX]); };
+        c0 = lag4(by(l - 1), by(l), by(l + 1), by(l + 2));
+      } else {
+        c0 = R(0.25) * (V[l - SX] + V[l - SX + 1] + V[l] + V[l + 1]);
+      }
       VC0[l] = c0;
       VT[l] = (c0 - MT(cosy, j, i) * U[l]) * MT(rsin2y, j, i);
     });

@@ -292,3 +292,22 @@ def test_fp32_error_after_100_substeps():
         e = relerr(res[fv3.FP32][f], res[fv3.FP64][f])
         print(f, e)
         assert e <= 1e-3, (f, e)
+
+
+@pytest.mark.parametrize("cubed", [False, True])
+def test_fourth_order_c_grid_winds(orc, cubed):
+    """c_sw with the fourth-order C-grid winds (reading R18) on the GPU"""
+    from paper_2205_04148_gb300 import fv3
+    g, gs, d, s, st = pair(orc, cubed, 20, 4, seed=97, nq=1)
+    g.run_dyn(gs, fv3.params(n_split=2, d2c_ord=4), 1)
+    s.run_dyn(orc.params(n_split=2, d2c_ord=4), 1)
+    for f in FIELDS + ("q0",):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 3 * TOL64, (f, e)
+    g32, gs32, _, _, _ = pair(orc, cubed, 20, 4, seed=97, nq=1, precision=fv3.FP32)
+    g32.run_dyn(gs32, fv3.params(n_split=2, d2c_ord=4), 1)
+    for f in ("u", "v", "delp", "pt"):
+        e = relerr(g32.read(gs32, f), s.get(f))
+        assert e <= 5e-4, (f, e)
+    with pytest.raises(fv3.Fv3Error, match="ARG"):
+        g.substep(gs, fv3.params(d2c_ord=3))
