@@ -70,6 +70,7 @@ typedef struct {
   int remap;               /* 1: vertical remapping after each remapping step (R16) */
   int nh_full;             /* 1: close the substep: update_dz_d, riem_solver3, D-grid p_grad (R17) */
   int d2c_ord;             /* C-grid winds from the D-grid: 2 (4-point means, R7) or 4 (R18) */
+  double d2_bg, dddmp;     /* divergence damping: background and Smagorinsky coefficients (R19) */
 } OParams;
 
 typedef struct {
@@ -1514,6 +1515,7 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
   double *ut = zalloc(d->px), *vt = zalloc(d->py), *crx = zalloc(d->px), *cry = zalloc(d->py);
   double *xfx = zalloc(d->px), *yfx = zalloc(d->py), *mfx = zalloc(d->px), *mfy = zalloc(d->py);
   double *Fx = zalloc(d->px), *Fy = zalloc(d->py), *vort = nalloc(d->pc), *ke = zalloc(d->pk);
+  double* shear = nalloc(d->pc);
   long nc = (long)d->nt * nz * d->pc, nx = (long)d->nt * nz * d->px, ny = (long)d->nt * nz * d->py;
   double *u_n = nalloc(ny), *v_n = nalloc(nx), *w_n = nalloc(nc), *dp_n = nalloc(nc), *pt_n = nalloc(nc);
   for (int t = 0; t < d->nt; t++) {
@@ -1576,6 +1578,39 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
           double vb = ppm_face(&v[IX(d, j, i)], d->wx, cv);
           ke[IK(d, j, i)] = 0.5 * dt * (ub * ub_adv + vb * vb_adv);
         }
+      /* 4b. divergence damping (reading R19): at the corners, the divergence D
+         and tension T of the D-grid winds over the dual cell, the shear S at the
+         cell centres averaged to the corners, coefficient
+         da_min max(d2_bg, min(0.2, dddmp dt sqrt(T^2 + S^2))); the kinetic
+         energy loses coefficient x D, so the wind update's energy gradient
+         carries the divergence-diffusing term.  Nothing at the cube corners. */
+      if (P->d2_bg > 0.0 || P->dddmp > 0.0) {
+        for (int j = -1; j <= n; j++)
+          for (int i = -1; i <= n; i++) {
+            int inx = (i >= 0 && i < n), iny = (j >= 0 && j < n);
+            if (d->cubed && !inx && !iny) { shear[IC(d, j, i)] = NAN; continue; }
+            shear[IC(d, j, i)] = (u[IY(d, j + 1, i)] * dx[IY(d, j + 1, i)] - u[IY(d, j, i)] * dx[IY(d, j, i)] +
+                                  v[IX(d, j, i + 1)] * dy[IX(d, j, i + 1)] - v[IX(d, j, i)] * dy[IX(d, j, i)]) *
+                                 rarea[IC(d, j, i)];
+          }
+        const double* dyc = d->dyc + t * d->py;
+        const double* dxc = d->dxc + t * d->px;
+        const double* rareac = d->rareac + t * d->pk;
+        for (int j = 0; j <= n; j++)
+          for (int i = 0; i <= n; i++) {
+            if (d->cubed && (i == 0 || i == n) && (j == 0 || j == n)) continue;
+            double fe = u[IY(d, j, i)] * dyc[IY(d, j, i)] * siny[IY(d, j, i)];
+            double fw = u[IY(d, j, i - 1)] * dyc[IY(d, j, i - 1)] * siny[IY(d, j, i - 1)];
+            double fn = v[IX(d, j, i)] * dxc[IX(d, j, i)] * sinx[IX(d, j, i)];
+            double fs = v[IX(d, j - 1, i)] * dxc[IX(d, j - 1, i)] * sinx[IX(d, j - 1, i)];
+            double div = (fe - fw + fn - fs) * rareac[IK(d, j, i)];
+            double ten = (fe - fw - (fn - fs)) * rareac[IK(d, j, i)];
+            double sh = 0.25 * ((shear[IC(d, j - 1, i - 1)] + shear[IC(d, j - 1, i)]) +
+                                (shear[IC(d, j, i - 1)] + shear[IC(d, j, i)]));
+            double coef = fmax(P->d2_bg, fmin(0.2, P->dddmp * dt * sqrt(ten * ten + sh * sh)));
+            ke[IK(d, j, i)] -= d->da_min * coef * div;
+          }
+      }
       /* 5. cell-centre absolute vorticity from the edge circulation */
       for (int j = -H; j < n + H; j++)
         for (int i = -H; i < n + H; i++) {
@@ -1632,7 +1667,7 @@ static void d_sw(OState* s, const OParams* P, int accumulate) {
     }
   work_free(&w);
   free(ut); free(vt); free(crx); free(cry); free(xfx); free(yfx); free(mfx); free(mfy); free(Fx); free(Fy);
-  free(vort); free(ke); free(u_n); free(v_n); free(w_n); free(dp_n); free(pt_n);
+  free(vort); free(ke); free(shear); free(u_n); free(v_n); free(w_n); free(dp_n); free(pt_n);
 }
 
 /* ------------------------------------------------------------------ */

@@ -36,7 +36,8 @@ class OParams(C.Structure):
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double),
                 ("ptop", C.c_double), ("grav", C.c_double), ("rdgas", C.c_double),
                 ("cp_air", C.c_double), ("mlp", C.POINTER(C.c_double)), ("mlp_bf16", C.c_int),
-                ("remap", C.c_int), ("nh_full", C.c_int), ("d2c_ord", C.c_int)]
+                ("remap", C.c_int), ("nh_full", C.c_int), ("d2c_ord", C.c_int),
+                ("d2_bg", C.c_double), ("dddmp", C.c_double)]
 
 
 def _load():
@@ -115,7 +116,8 @@ def params(mlp=None, mlp_bf16=0, **kw):
     p.update(kw)
     prm = OParams(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"],
                   p["dz_min"], p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(mlp_bf16),
-                  int(p.get("remap", 0)), int(p.get("nh_full", 0)), int(p.get("d2c_ord", 2)))
+                  int(p.get("remap", 0)), int(p.get("nh_full", 0)), int(p.get("d2c_ord", 2)),
+                  float(p.get("d2_bg", 0.0)), float(p.get("dddmp", 0.0)))
     if mlp is not None:
         w = _c(mlp)
         prm._w = w
