@@ -115,6 +115,10 @@ typedef struct {
   int d2c_ord;     /* C-grid winds in c_sw from the D-grid winds: 2 (mean of the four
                       surrounding values) or 4 (four-point Lagrange along, then across;
                       reading R18); 0 means 2 */
+  double d2_bg;    /* divergence damping of the D-grid winds (reading R19): background
+                      coefficient (0: off) */
+  double dddmp;    /* and Smagorinsky coefficient on the deformation (0: off); the
+                      damping coefficient is min area x max(d2_bg, min(0.2, dddmp dt |def|)) */
 } fv3_params;
 
 typedef struct {

@@ -92,6 +92,8 @@ fv3_status check_params(fv3_ctx* x, const fv3_params* p) {
   if (p->remap != 0 && p->remap != 1) return fail(x, FV3_ERR_ARG, "remap must be 0 or 1");
   if (p->nh_full != 0 && p->nh_full != 1) return fail(x, FV3_ERR_ARG, "nh_full must be 0 or 1");
   if (p->d2c_ord != 0 && p->d2c_ord != 2 && p->d2c_ord != 4) return fail(x, FV3_ERR_ARG, "d2c_ord must be 2 or 4");
+  if (!(p->d2_bg >= 0.0) || !(p->dddmp >= 0.0) || !std::isfinite(p->d2_bg) || !std::isfinite(p->dddmp))
+    return fail(x, FV3_ERR_ARG, "d2_bg and dddmp must be finite and >= 0");
   if (!(p->a_imp > 0) || !(p->grav > 0) || !(p->rdgas > 0) || !(p->cp_air > p->rdgas) || !(p->ptop > 0) ||
       !(p->dz_min >= 0) || !(p->d4_bg >= 0))
     return fail(x, FV3_ERR_ARG, "physical constant out of range");
@@ -112,6 +114,8 @@ Params to_params(const fv3_params* p) {
   P.grav = p->grav; P.rdgas = p->rdgas; P.cp_air = p->cp_air;
   P.n_split = p->n_split; P.nord = p->nord; P.hord = p->hord; P.remap = p->remap; P.nh_full = p->nh_full;
   P.d2c_ord = p->d2c_ord == 0 ? 2 : p->d2c_ord;
+  P.d2_bg = p->d2_bg;
+  P.dddmp = p->dddmp;
   P.mlp = (const float*)p->mlp;
   return P;
 }

@@ -48,7 +48,7 @@ struct Metric {
 };
 
 struct Params {
-  double dt, d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air;
+  double dt, d4_bg, a_imp, dz_min, ptop, grav, rdgas, cp_air, d2_bg, dddmp;
   int n_split, nord, hord, remap, nh_full, d2c_ord;
   const float* mlp;  // face-value network parameters (hord 1)
 };

@@ -902,6 +902,57 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
 }
 
 // ------------------------------------------------------------------------
+// Divergence damping (reading R19), after d_sw: at every corner the
+// divergence and tension of the start-of-d_sw D-grid winds over the dual
+// cell, the shear at the four surrounding cell centres, the coefficient
+// c = da_min max(d2_bg, min(0.2, dddmp dt |deformation|)) and cd = c x div;
+// d_sw's corner kinetic energy minus cd enters the wind update, so
+// u += (cd(i+1, j) - cd(i, j)) rdx and v += (cd(i, j+1) - cd(i, j)) rdy.
+// None at the cube corners.  One thread per (i, j) of a level plane.
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R cell_shear(const R* u, const R* v, const TM<R>& m, const Geo& g, int j, int i) {
+  const long long P = g.pitch;
+  return (u[(j + 1) * P + i] * MT(dx, j + 1, i) - u[j * P + i] * MT(dx, j, i) + v[j * P + i + 1] * MT(dy, j, i + 1) -
+          v[j * P + i] * MT(dy, j, i)) * MT(rarea, j, i);
+}
+
+template <typename R>
+__device__ R corner_damping(const R* u, const R* v, const TM<R>& m, const Geo& g, int j, int i, R d2, R sm) {
+  const int n = g.n;
+  if (g.cubed && (i == 0 || i == n) && (j == 0 || j == n)) return R(0);
+  const long long P = g.pitch;
+  const R fe = u[j * P + i] * MT(dyc, j, i) * MT(siny, j, i);
+  const R fw = u[j * P + i - 1] * MT(dyc, j, i - 1) * MT(siny, j, i - 1);
+  const R fn = v[j * P + i] * MT(dxc, j, i) * MT(sinx, j, i);
+  const R fs = v[(j - 1) * P + i] * MT(dxc, j - 1, i) * MT(sinx, j - 1, i);
+  const R div = (fe - fw + fn - fs) * MT(rareac, j, i);
+  const R ten = (fe - fw - (fn - fs)) * MT(rareac, j, i);
+  const R sh = R(0.25) * ((cell_shear(u, v, m, g, j - 1, i - 1) + cell_shear(u, v, m, g, j - 1, i)) +
+                          (cell_shear(u, v, m, g, j, i - 1) + cell_shear(u, v, m, g, j, i)));
+  const R coef = fmax(d2, fmin(R(0.2), sm * sqrt(ten * ten + sh * sh)));
+  return (R)g.da_min * coef * div;
+}
+
+template <typename R>
+__global__ void k_div_damp(StepArgs<R> a, const int4* planes) {
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = a.geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = g.n;
+  if (i > n || j > n) return;
+  const int t = pl.y, k = pl.z;
+  const TM<R> m = tile_metric(a.M, g, t);
+  const long long o = fld0(g, g.off3, g.nz, t, k);
+  const R *u = a.u + o, *v = a.v + o;
+  const R d2 = (R)a.P.d2_bg, sm = (R)(a.P.dddmp * a.P.dt);
+  const R c0 = corner_damping(u, v, m, g, j, i, d2, sm);
+  const long long q = o + (long long)j * g.pitch + i;
+  if (i < n) a.u_o[q] += (corner_damping(u, v, m, g, j, i + 1, d2, sm) - c0) * MT(rdx, j, i);
+  if (j < n) a.v_o[q] += (corner_damping(u, v, m, g, j + 1, i, d2, sm) - c0) * MT(rdy, j, i);
+}
+
+// ------------------------------------------------------------------------
 // D-grid nonhydrostatic pressure gradient (reading R17): the contour form of
 // R10 along each cell edge between its corners A and B, with pef and gz at
 // the corners the means of the surrounding cells (three at a cube corner).
@@ -1427,6 +1478,11 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
 #undef FV3_DSW
+    ++c.launches;
+  }
+  if (run(6) && (P.d2_bg > 0.0 || P.dddmp > 0.0)) {  // divergence damping of d_sw's winds
+    const int nb = (c.max_n + 1 + 15) / 16;
+    k_div_damp<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
     ++c.launches;
   }
   if (run(7)) {  // update_dz_d: the D-grid area fluxes of d_sw over the state delz

@@ -50,7 +50,8 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_split", C.c_int), ("nord", C.c_int), ("hord", C.c_int),
                 ("d4_bg", C.c_double), ("a_imp", C.c_double), ("dz_min", C.c_double), ("ptop", C.c_double),
                 ("grav", C.c_double), ("rdgas", C.c_double), ("cp_air", C.c_double), ("mlp", C.c_void_p),
-                ("remap", C.c_int), ("nh_full", C.c_int), ("d2c_ord", C.c_int)]
+                ("remap", C.c_int), ("nh_full", C.c_int), ("d2c_ord", C.c_int),
+                ("d2_bg", C.c_double), ("dddmp", C.c_double)]
 
 
 class Layout(C.Structure):
@@ -155,7 +156,8 @@ def params(mlp=None, **kw):
     p.update(kw)
     prm = Params(p["dt"], p["n_split"], p["nord"], p["hord"], p["d4_bg"], p["a_imp"], p["dz_min"],
                  p["ptop"], p["grav"], p["rdgas"], p["cp_air"], None, int(p.get("remap", 0)),
-                 int(p.get("nh_full", 0)), int(p.get("d2c_ord", 2)))
+                 int(p.get("nh_full", 0)), int(p.get("d2c_ord", 2)), float(p.get("d2_bg", 0.0)),
+                 float(p.get("dddmp", 0.0)))
     if mlp is not None:
         prm.mlp = C.c_void_p(mlp.data_ptr())
         prm._keep = mlp

@@ -311,3 +311,18 @@ def test_fourth_order_c_grid_winds(orc, cubed):
         assert e <= 5e-4, (f, e)
     with pytest.raises(fv3.Fv3Error, match="ARG"):
         g.substep(gs, fv3.params(d2c_ord=3))
+
+
+@pytest.mark.parametrize("cubed", [False, True])
+def test_divergence_damping(orc, cubed):
+    """divergence damping with the Smagorinsky coefficient (reading R19)"""
+    from paper_2205_04148_gb300 import fv3
+    g, gs, d, s, st = pair(orc, cubed, 20, 4, seed=99)
+    for _ in range(2):
+        g.substep(gs, fv3.params(d2_bg=0.04, dddmp=0.3))
+        s.substep(orc.params(d2_bg=0.04, dddmp=0.3))
+    for f in FIELDS:
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 3 * TOL64, (f, e)
+    with pytest.raises(fv3.Fv3Error, match="ARG"):
+        g.substep(gs, fv3.params(d2_bg=-1.0))
