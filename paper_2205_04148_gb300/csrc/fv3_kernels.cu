@@ -266,7 +266,7 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
     const float y1 = mlp_warp(F, x);
     const float y2 = mlp_warp(F, xr);
     const float corr = __fmul_rn(__fmul_rn(0.5f, __fadd_rn(y1, y2)), sig);
-    const R a = plain + (R)corr;
+    const R a = plain + widen<R>(corr);
     if (valid) OUT[l] = within_cells(a, q[2], q[3]) ? a : plain;
   }
 }

@@ -178,12 +178,47 @@ __device__ __forceinline__ float mlp_offsets_to_inputs(const float (&d)[6], floa
 template <typename R>
 __device__ __forceinline__ float mlp_inputs(const R (&q)[6], float (&x)[6], float (&xr)[6]);
 
+// double -> float, round to nearest even (IEEE 754), on the integer pipe:
+// the FP64 pipe (2 lanes per SM per clock) is the bottleneck of the learned
+// transport.  Results below the float normal range flush to zero (the
+// offsets they would encode are far below any stencil's variation).
+__device__ __forceinline__ float to_float_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long m = b & 0xfffffffffffffULL;
+  unsigned f = ((unsigned)e << 23) | (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffULL, half = 0x10000000ULL;
+  f += (rem > half || (rem == half && (f & 1u))) ? 1u : 0u;  // a carry raises the exponent
+  return __uint_as_float(sign | f);
+}
+
+// float -> double (exact for normal floats), on the integer pipe; float
+// subnormals flush to zero
+__device__ __forceinline__ double to_double(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const int e = (int)((b >> 23) & 0xff);
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ee = e == 255 ? 0x7ffULL : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ee << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+template <typename R>
+__device__ __forceinline__ R widen(float x);
+template <>
+__device__ __forceinline__ double widen<double>(float x) { return to_double(x); }
+template <>
+__device__ __forceinline__ float widen<float>(float x) { return x; }
+
 template <>
 __device__ __forceinline__ float mlp_inputs<double>(const double (&q)[6], float (&x)[6], float (&xr)[6]) {
   const double r = __dmul_rn(0.5, __dadd_rn(q[2], q[3]));
   float d[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) d[i] = __double2float_rn(__dsub_rn(q[i], r));
+  for (int i = 0; i < 6; ++i) d[i] = to_float_rn(__dsub_rn(q[i], r));
   return mlp_offsets_to_inputs(d, x, xr);
 }
 
