@@ -214,6 +214,13 @@ fv3_status fv3_vertical_remap(fv3_ctx* ctx, const fv3_state* state, const fv3_pa
 fv3_status fv3_fv_tp_2d(fv3_ctx* ctx, void* q, void* crx, void* cry, void* xfx, void* yfx, void* mfx, void* mfy,
                         double damp, void* fx, void* fy, fv3_stream stream);
 
+/* Scan the interior of the state's fields (u, v, w, delp, pt, delz and the
+ * tracers) of every member for NaN or Inf; synchronizes `stream` and returns
+ * FV3_ERR_NONFINITE if one is found (else the pending status, as
+ * fv3_check_status).  Failure detection without any device fault (no
+ * counterpart in the paper). */
+fv3_status fv3_check_finite(fv3_ctx* ctx, const fv3_state* state, fv3_stream stream);
+
 /* Global mass sum(delp * area) per member in FP64 (Neumaier-compensated, fixed
  * order).  out_per_member: host array [n_members]; returns after the sum is
  * on the host. */

@@ -583,9 +583,19 @@ extern "C" fv3_status fv3_check_status(fv3_ctx* x, fv3_stream stream) {
   CK(x, cudaStreamSynchronize(st));
   CK(x, cudaMemcpy(&h, x->c.status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   CK(x, cudaMemset(x->c.status, 0, sizeof(unsigned)));
+  if (h & ST_NONFINITE) return fail(x, FV3_ERR_NONFINITE, "a state field holds a non-finite value");
   if (h & ST_CFL) return fail(x, FV3_ERR_CFL, "a Courant number reached 1");
   if (h & ST_NSPLT) return fail(x, FV3_ERR_UNSUPPORTED, "tracer transport needed more than 4 subcycles");
   return FV3_OK;
+}
+
+extern "C" fv3_status fv3_check_finite(fv3_ctx* x, const fv3_state* s, fv3_stream stream) {
+  if (!x) return FV3_ERR_ARG;
+  fv3_status r = check_state(x, s, false);
+  if (r != FV3_OK) return r;
+  enqueue_check_finite(x->c, view(s), (cudaStream_t)stream);
+  CK(x, cudaGetLastError());
+  return fv3_check_status(x, stream);
 }
 
 extern "C" fv3_status fv3_get_metric(fv3_ctx* x, const char* name, int member, double* dense) {

@@ -1209,6 +1209,32 @@ __global__ void k_copy_planes(const Geo* geo, const int4* planes, const CopyArgs
   for (int f = 0; f < a.nf; ++f) a.dst[f][o] = a.src[f][o];
 }
 
+// flag any non-finite interior value of the listed fields (kind 0 cells,
+// 1 x-faces, 2 y-faces) in the status word
+template <typename R>
+struct CheckArgs {
+  const R* src[MAX_TRACERS + 1];
+  int kind[MAX_TRACERS + 1];
+  int nf;
+};
+
+template <typename R>
+__global__ void k_check_finite(const Geo* geo, const int4* planes, const CheckArgs<R> a, unsigned* status) {
+  const int4 pl = planes[blockIdx.z];
+  const Geo g = geo[pl.x];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = g.n;
+  if (i > n || j > n) return;
+  const long long o = fld0(g, g.off3, g.nz, pl.y, pl.z) + (long long)j * g.pitch + i;
+  bool bad = false;
+  for (int f = 0; f < a.nf; ++f) {
+    const int kind = a.kind[f];
+    const bool in = (i < n || kind == 1) && (j < n || kind == 2) && !(i == n && j == n);
+    if (in) bad |= !isfinite((double)a.src[f][o]);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
 // ------------------------------------------------------------------------
 // global mass (reading R13): sum of delp * area per member, FP64,
 // Neumaier-compensated, fixed order (block partials, then one thread).
@@ -1698,6 +1724,32 @@ void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t s
 #endif
 
 #if FV3_TU_MAIN
+template <typename R>
+static void check_finite_t(Ctx& c, const StateView& s, cudaStream_t st) {
+  CheckArgs<R> a{};
+  const void* f[6] = {s.u, s.v, s.w, s.delp, s.pt, s.delz};
+  const int k6[6] = {2, 1, 0, 0, 0, 0};
+  std::vector<std::pair<const void*, int>> all;
+  for (int q = 0; q < 6; ++q) all.push_back({f[q], k6[q]});
+  for (int q = 0; q < s.nq; ++q) all.push_back({s.q[q], 0});
+  for (size_t b = 0; b < all.size(); b += MAX_TRACERS + 1) {
+    a.nf = 0;
+    for (size_t q = b; q < all.size() && a.nf < MAX_TRACERS + 1; ++q, ++a.nf) {
+      a.src[a.nf] = (const R*)all[q].first;
+      a.kind[a.nf] = all[q].second;
+    }
+    const int nb = c.max_n + 1;
+    k_check_finite<R><<<dim3((nb + 31) / 32, (nb + 7) / 8, c.n_planes), dim3(32, 8), 0, st>>>(c.geo_d, c.planes, a,
+                                                                                               c.status);
+    ++c.launches;
+  }
+}
+
+void enqueue_check_finite(Ctx& c, const StateView& s, cudaStream_t st) {
+  if (c.prec == 0) check_finite_t<double>(c, s, st);
+  else check_finite_t<float>(c, s, st);
+}
+
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st) {
   if (c.prec == 0)
     k_mass_partial<double><<<c.n_planes, 256, 0, st>>>(c.geo_d, c.planes, (const double*)delp, c.Md.area,

@@ -187,6 +187,7 @@ void enqueue_fv_tp_2d(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_fv_tp_2d_f64(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_fv_tp_2d_f32(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st);
+void enqueue_check_finite(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
                   int dir, cudaStream_t st);
 void enqueue_halo_fields(Ctx& c, const std::vector<HaloField>& fields, cudaStream_t st);

@@ -32,7 +32,7 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
            "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap",
-           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32")
+           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite")
 
 
 class GridDesc(C.Structure):
@@ -122,6 +122,8 @@ def load(path=LIB_PATH):
     L.fv3_get_persistent.argtypes = [vp, C.POINTER(i)]
     L.fv3_vertical_remap.restype = st
     L.fv3_vertical_remap.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp]
+    L.fv3_check_finite.restype = st
+    L.fv3_check_finite.argtypes = [vp, C.POINTER(State), vp]
     L.fv3_math_check.restype = st
     L.fv3_math_check.argtypes = [i, vp, vp, vp, i, vp]
     L.fv3_fv_tp_2d.restype = st
@@ -368,6 +370,11 @@ class Grid:
         self.check(self.L.fv3_fv_tp_2d(self.ptr, ptr(q), ptr(crx), ptr(cry), ptr(xfx), ptr(yfx), ptr(mfx), ptr(mfy),
                                        float(damp), ptr(fx), ptr(fy), _stream(stream)))
         return fx, fy
+
+    def check_finite(self, st, stream=None):
+        """0, or FV3_ERR_NONFINITE if a state field holds NaN or Inf"""
+        s = self.cstate(st)
+        return self.L.fv3_check_finite(self.ptr, C.byref(s), _stream(stream))
 
     def check_status(self, stream=None):
         return self.L.fv3_check_status(self.ptr, _stream(stream))
