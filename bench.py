@@ -80,6 +80,12 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default block shape (32 x 8, 8 levels per CTA, one CTA per item)")
+    p.add_argument("--nh-full", action="store_true", help="close each substep (update_dz_d, riem_solver3, "
+                                                           "D-grid pressure gradient)")
+    p.add_argument("--remap", action="store_true", help="vertical remapping at the end of each step")
+    p.add_argument("--d2c-ord", type=int, default=2, help="C-grid winds from the D-grid: 2 or 4")
+    p.add_argument("--d2-bg", type=float, default=0.0, help="divergence damping, background coefficient")
+    p.add_argument("--dddmp", type=float, default=0.0, help="divergence damping, Smagorinsky coefficient")
     p.add_argument("--tiles", default=None,
                    help="BX,BY,KCHUNK,PERSISTENT: set the block shape, level chunk and launch mode instead of "
                         "autotuning")
@@ -144,7 +150,7 @@ def dist():
     return replicas.world()
 
 
-def _oracle_step_rate(npx, nz_sample, nq, n_split, steps, warmup):
+def _oracle_step_rate(npx, nz_sample, nq, n_split, steps, warmup, **options):
     """Oracle (plain C, one thread) remapping steps -- n_split acoustic
     substeps and tracer_2d of nq tracers -- on C{npx} x nz_sample levels;
     returns (cell-substeps/s, seconds per step)."""
@@ -153,7 +159,7 @@ def _oracle_step_rate(npx, nz_sample, nq, n_split, steps, warmup):
     st = I.cubed_state(npx, nz_sample, seed=0, ntracers=nq)
     s = O.State(O.Domain(True, npx, nz_sample), nq)
     s.load(st)
-    prm = O.params(n_split=n_split)
+    prm = O.params(n_split=n_split, **options)
     for _ in range(warmup):
         s.run_dyn(prm, 1)
     t0 = time.perf_counter()
@@ -171,11 +177,12 @@ def reference_arm(a):
     ws, rank, _ = dist()
     if rank != 0:
         return 0
-    _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0)
+    options = dict(nh_full=int(a.nh_full), remap=int(a.remap), d2c_ord=a.d2c_ord, d2_bg=a.d2_bg, dddmp=a.dddmp)
+    _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0, **options)
     per_level = t2 / 2
     budget = 120.0 / max(1, a.steps + a.warmup)
     nzs = int(max(2, min(a.npz, budget / per_level)))
-    value, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, a.steps, a.warmup)
+    value, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, a.steps, a.warmup, **options)
     sample = ("one remapping step (%d acoustic substeps + tracer_2d of %d tracers) of C%d x %d levels (of %d) "
               "per step, FP64 oracle, 1 thread" % (a.n_split, a.nq, a.npx, nzs, a.npz))
     out = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": a.gpus,
@@ -183,7 +190,7 @@ def reference_arm(a):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "cubed-sphere C%d x %d levels, FP64, n_split %d, %d tracers, one remapping "
                                   "step per bench step" % (a.npx, a.npz, a.n_split, a.nq),
-                      "sample_levels": nzs},
+                      "sample_levels": nzs, "options": options},
            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -213,7 +220,8 @@ def ours(a):
     st = I.cubed_state(a.npx, a.npz, seed=rank, ntracers=a.nq)
     gs = g.alloc_state(a.nq)
     g.load(gs, st)
-    prm = fv3.params(n_split=a.n_split)
+    options = dict(nh_full=int(a.nh_full), remap=int(a.remap), d2c_ord=a.d2c_ord, d2_bg=a.d2_bg, dddmp=a.dddmp)
+    prm = fv3.params(n_split=a.n_split, **options)
     cells = 6 * a.npx * a.npx * a.npz
     L = g.L
     L.fv3_kernel_launches.restype = C.c_longlong
@@ -357,9 +365,9 @@ def ours(a):
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         # the same remapping step on a level subset sized to about 15 s
-        _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0)
+        _, t2 = _oracle_step_rate(a.npx, 2, a.nq, a.n_split, 1, 0, **options)
         nzs = int(max(2, min(a.npz, 15.0 / (t2 / 2))))
-        rate, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, 1, 0)
+        rate, dt = _oracle_step_rate(a.npx, nzs, a.nq, a.n_split, 1, 0, **options)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": "one remapping step (%d acoustic substeps + tracer_2d of %d tracers) of C%d x %d levels "
                          "(of %d), FP64 oracle, 1 thread (%.1f s)" % (a.n_split, a.nq, a.npx, nzs, a.npz, dt)}
@@ -372,7 +380,8 @@ def ours(a):
                "config": {"workload": "cubed-sphere C%d x %d levels, %s, n_split %d, %d tracers, one remapping "
                                       "step per bench step" % (a.npx, a.npz, a.precision.upper(), a.n_split, a.nq),
                           "cells": cells, "substeps_per_step": a.n_split, "l2": "inputs larger than L2",
-                          "tiles": tuned, "parallelism": "replicas" if ws > 1 else "single GPU"},
+                          "tiles": tuned, "options": options,
+                          "parallelism": "replicas" if ws > 1 else "single GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "status": status}
         print(json.dumps(out), flush=True)
