@@ -151,9 +151,20 @@ fv3_status fv3_get_layout(const fv3_ctx* ctx, int member, fv3_layout* out);
 /* Copy a dense array of member `member` into (import) or out of (export) a
  * field in the library layout.  Dense layout [tile][level][nj][ni] with
  * (ni, nj) = (n, n) cells, (n+1, n) x-faces, (n, n+1) y-faces, levels nz (nz+1
- * for IFACE).  dense_is_host: the dense array is host memory (copied through
- * a staging buffer; host exports return after the copy completed);
+ * for IFACE).  dense_is_host:
+ *   FV3_DENSE_DEVICE (0): the dense array is device memory (a pack kernel);
+ *   FV3_DENSE_HOST (1): host memory, copied through a staging buffer; host
+ *     exports return after the copy completed;
+ *   FV3_DENSE_HOST_ASYNC (2): page-locked host memory, asynchronous: one
+ *     contiguous copy between the host array and one of four device staging
+ *     slots plus the pack kernel, both enqueued on `stream`; the call returns
+ *     once they are enqueued, and the host array must stay untouched until
+ *     the stream has passed them.  A slot is reused only after its previous
+ *     copy completed (an event, whatever stream that ran on); growing a slot
+ *     waits on the host for that copy.  Lets a caller overlap the I/O of one
+ *     state with the substeps of another on a second stream.
  * dense_is_double: dense elements are double (else float). */
+enum { FV3_DENSE_DEVICE = 0, FV3_DENSE_HOST = 1, FV3_DENSE_HOST_ASYNC = 2 };
 fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, int dense_is_host, int dense_is_double,
                       int member, fv3_stream stream);
 fv3_status fv3_export(fv3_ctx* ctx, int kind, const void* field, void* dense, int dense_is_host, int dense_is_double,
@@ -173,7 +184,8 @@ fv3_status fv3_acoustic_substep(fv3_ctx* ctx, const fv3_state* state, const fv3_
 /* n_steps remapping steps (Section II): each is params->n_split acoustic
  * substeps with accumulated mass fluxes and Courant numbers, then tracer
  * transport (tracer_2d) of the state's nq tracers.  The step is captured once
- * as a CUDA graph (per state pointers and parameters) and replayed. */
+ * as a CUDA graph per state pointers and parameters and replayed; the graphs
+ * of the last four such keys are kept (least recently used evicted). */
 fv3_status fv3_run_dyn(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, int n_steps,
                        fv3_stream stream);
 

@@ -19,11 +19,22 @@
 
 using namespace fv3;
 
+// staging slots of the asynchronous host copies: a slot is reused only after
+// the event recorded behind its last copy, on whatever stream that ran
+struct Slot {
+  void* buf = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+};
+constexpr int kSlots = 4;
+
 struct fv3_ctx {
   Ctx c;
   cudaStream_t cap = nullptr;   // private stream used only to capture graphs
   void* stage = nullptr;        // staging buffer for host <-> device copies
   size_t stage_bytes = 0;
+  Slot ring[kSlots];            // staging of the asynchronous host copies
+  int ring_next = 0;
 };
 
 namespace {
@@ -118,6 +129,14 @@ Params to_params(const fv3_params* p) {
   P.dddmp = p->dddmp;
   P.mlp = (const float*)p->mlp;
   return P;
+}
+
+// captured remapping steps kept at once (a few states or parameter sets)
+constexpr int kMaxGraphs = 4;
+
+void drop_graphs(Ctx& c) {
+  for (Ctx::Graph& e : c.graphs) cudaGraphExecDestroy(e.exec);
+  c.graphs.clear();
 }
 
 fv3_status ensure_stage(fv3_ctx* x, size_t bytes) {
@@ -334,7 +353,12 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
 
 extern "C" void fv3_destroy(fv3_ctx* x) {
   if (!x) return;
-  if (x->c.graph) cudaGraphExecDestroy(x->c.graph);
+  drop_graphs(x->c);
+  for (Slot& sl : x->ring) {
+    if (sl.done) cudaEventSynchronize(sl.done);
+    if (sl.buf) cudaFree(sl.buf);
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
   for (void* p : x->c.owned) cudaFree(p);
   if (x->stage) cudaFree(x->stage);
   if (x->cap) cudaStreamDestroy(x->cap);
@@ -377,6 +401,29 @@ static fv3_status do_pack(fv3_ctx* x, int kind, void* field, void* dense, int ho
   const int nlev = iface ? g.nz + 1 : g.nz;
   const int pk = kind == FV3_KIND_IFACE ? 0 : kind;  // interface fields are cell-shaped
   const size_t bytes = dense_count(g, pk, nlev) * (dbl ? 8 : 4);
+  if (host == FV3_DENSE_HOST_ASYNC) {
+    // one contiguous copy between the host array and a staging slot, and the
+    // pack kernel between the slot and the field, both on `st`
+    Slot& sl = x->ring[x->ring_next];
+    x->ring_next = (x->ring_next + 1) % kSlots;
+    if (!sl.done) CK(x, cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+    if (sl.bytes < bytes) {  // grow: wait for the slot's last copy first
+      CK(x, cudaEventSynchronize(sl.done));
+      if (sl.buf) cudaFree(sl.buf);
+      sl.buf = nullptr;
+      sl.bytes = 0;
+      CK(x, cudaMalloc(&sl.buf, bytes));
+      sl.bytes = bytes;
+    }
+    CK(x, cudaStreamWaitEvent(st, sl.done, 0));
+    if (dir == 0) CK(x, cudaMemcpyAsync(sl.buf, dense, bytes, cudaMemcpyHostToDevice, st));
+    enqueue_pack(x->c, member, pk, nlev, iface, field, sl.buf, dbl, dir, st);
+    CK(x, cudaGetLastError());
+    if (dir == 1) CK(x, cudaMemcpyAsync(dense, sl.buf, bytes, cudaMemcpyDeviceToHost, st));
+    CK(x, cudaEventRecord(sl.done, st));
+    return FV3_OK;
+  }
+  if (host != 0 && host != FV3_DENSE_HOST) return fail(x, FV3_ERR_ARG, "bad dense_is_host");
   void* dd = dense;
   if (host) {
     fv3_status s = ensure_stage(x, bytes);
@@ -521,29 +568,36 @@ extern "C" fv3_status fv3_run_dyn(fv3_ctx* x, const fv3_state* s, const fv3_para
   std::vector<unsigned char> key(sizeof(StateView) + sizeof(Params));
   std::memcpy(key.data(), &in, sizeof(StateView));
   std::memcpy(key.data() + sizeof(StateView), &P, sizeof(Params));
-  if (!c.graph || key != c.graph_key) {
-    if (c.graph) {
-      cudaGraphExecDestroy(c.graph);
-      c.graph = nullptr;
+  Ctx::Graph* G = nullptr;
+  for (Ctx::Graph& e : c.graphs)
+    if (e.key == key) G = &e;
+  if (!G) {
+    if ((int)c.graphs.size() >= kMaxGraphs) {  // evict the least recently used
+      size_t old = 0;
+      for (size_t e = 1; e < c.graphs.size(); ++e)
+        if (c.graphs[e].used < c.graphs[old].used) old = e;
+      cudaGraphExecDestroy(c.graphs[old].exec);
+      c.graphs.erase(c.graphs.begin() + (long)old);
     }
     CK(x, cudaStreamBeginCapture(x->cap, cudaStreamCaptureModeThreadLocal));
     const long long before = c.launches;
     enqueue_remap_step(c, in, P, x->cap);
-    c.graph_launches = c.launches - before;
+    Ctx::Graph e;
+    e.launches = c.launches - before;
     c.launches = before;
     cudaGraph_t g = nullptr;
     cudaError_t e1 = cudaStreamEndCapture(x->cap, &g);
     if (e1 != cudaSuccess) return fail(x, FV3_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
-    cudaError_t e2 = cudaGraphInstantiate(&c.graph, g, 0);
+    cudaError_t e2 = cudaGraphInstantiate(&e.exec, g, 0);
     cudaGraphDestroy(g);
-    if (e2 != cudaSuccess) {
-      c.graph = nullptr;
-      return fail(x, FV3_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
-    }
-    c.graph_key = key;
+    if (e2 != cudaSuccess) return fail(x, FV3_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    e.key = key;
+    c.graphs.push_back(e);
+    G = &c.graphs.back();
   }
-  for (int k = 0; k < n_steps; ++k) CK(x, cudaGraphLaunch(c.graph, st));
-  c.launches += (long long)n_steps * c.graph_launches;
+  G->used = ++c.graph_clock;
+  for (int k = 0; k < n_steps; ++k) CK(x, cudaGraphLaunch(G->exec, st));
+  c.launches += (long long)n_steps * G->launches;
   return FV3_OK;
 }
 
@@ -673,22 +727,14 @@ extern "C" fv3_status fv3_set_tiles(fv3_ctx* x, int bx, int by, int kchunk) {
   c.BX = bx;
   c.BY = by;
   c.kchunk = kchunk;
-  if (c.graph) {
-    cudaGraphExecDestroy(c.graph);
-    c.graph = nullptr;
-    c.graph_key.clear();
-  }
+  drop_graphs(c);
   return FV3_OK;
 }
 
 extern "C" fv3_status fv3_set_persistent(fv3_ctx* x, int on) {
   if (!x) return FV3_ERR_ARG;
   x->c.persistent = on ? 1 : 0;
-  if (x->c.graph) {
-    cudaGraphExecDestroy(x->c.graph);
-    x->c.graph = nullptr;
-    x->c.graph_key.clear();
-  }
+  drop_graphs(x->c);
   return FV3_OK;
 }
 

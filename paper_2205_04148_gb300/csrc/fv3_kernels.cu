@@ -917,39 +917,55 @@ __device__ __forceinline__ R cell_shear(const R* u, const R* v, const TM<R>& m, 
           v[j * P + i] * MT(dy, j, i)) * MT(rarea, j, i);
 }
 
+// a 16 x 16 block of corners (i0 + tx, j0 + ty): the shears of the 18 x 18
+// cells around them and the damping of the 17 x 17 corners the block's faces
+// need are formed once each, in shared memory
 template <typename R>
-__device__ R corner_damping(const R* u, const R* v, const TM<R>& m, const Geo& g, int j, int i, R d2, R sm) {
-  const int n = g.n;
-  if (g.cubed && (i == 0 || i == n) && (j == 0 || j == n)) return R(0);
-  const long long P = g.pitch;
-  const R fe = u[j * P + i] * MT(dyc, j, i) * MT(siny, j, i);
-  const R fw = u[j * P + i - 1] * MT(dyc, j, i - 1) * MT(siny, j, i - 1);
-  const R fn = v[j * P + i] * MT(dxc, j, i) * MT(sinx, j, i);
-  const R fs = v[(j - 1) * P + i] * MT(dxc, j - 1, i) * MT(sinx, j - 1, i);
-  const R div = (fe - fw + fn - fs) * MT(rareac, j, i);
-  const R ten = (fe - fw - (fn - fs)) * MT(rareac, j, i);
-  const R sh = R(0.25) * ((cell_shear(u, v, m, g, j - 1, i - 1) + cell_shear(u, v, m, g, j - 1, i)) +
-                          (cell_shear(u, v, m, g, j, i - 1) + cell_shear(u, v, m, g, j, i)));
-  const R coef = fmax(d2, fmin(R(0.2), sm * sqrt(ten * ten + sh * sh)));
-  return (R)g.da_min * coef * div;
-}
-
-template <typename R>
-__global__ void k_div_damp(StepArgs<R> a, const int4* planes) {
+__global__ void __launch_bounds__(256) k_div_damp(StepArgs<R> a, const int4* planes) {
+  __shared__ R s_sh[18][18];
+  __shared__ R s_cd[17][17];
   const int4 pl = planes[blockIdx.z];
   const Geo g = a.geo[pl.x];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = g.n;
-  if (i > n || j > n) return;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
+  if (i0 > n || j0 > n) return;  // the whole block (uniform)
+  const int tid = threadIdx.y * 16 + threadIdx.x;
   const int t = pl.y, k = pl.z;
   const TM<R> m = tile_metric(a.M, g, t);
   const long long o = fld0(g, g.off3, g.nz, t, k);
   const R *u = a.u + o, *v = a.v + o;
   const R d2 = (R)a.P.d2_bg, sm = (R)(a.P.dddmp * a.P.dt);
-  const R c0 = corner_damping(u, v, m, g, j, i, d2, sm);
+  for (int e = tid; e < 18 * 18; e += 256) {  // cells j0 - 1 .. j0 + 16, i0 - 1 .. i0 + 16
+    const int jj = e / 18, ii = e - jj * 18;
+    const int cj = j0 - 1 + jj, ci = i0 - 1 + ii;
+    s_sh[jj][ii] = (cj <= n && ci <= n) ? cell_shear(u, v, m, g, cj, ci) : R(0);
+  }
+  __syncthreads();
+  for (int e = tid; e < 17 * 17; e += 256) {  // corners j0 .. j0 + 16, i0 .. i0 + 16
+    const int jj = e / 17, ii = e - jj * 17;
+    const int j = j0 + jj, i = i0 + ii;
+    R cd = R(0);
+    if (j <= n && i <= n && !(g.cubed && (i == 0 || i == n) && (j == 0 || j == n))) {
+      const long long P = g.pitch;
+      const R fe = u[j * P + i] * MT(dyc, j, i) * MT(siny, j, i);
+      const R fw = u[j * P + i - 1] * MT(dyc, j, i - 1) * MT(siny, j, i - 1);
+      const R fn = v[j * P + i] * MT(dxc, j, i) * MT(sinx, j, i);
+      const R fs = v[(j - 1) * P + i] * MT(dxc, j - 1, i) * MT(sinx, j - 1, i);
+      const R div = (fe - fw + fn - fs) * MT(rareac, j, i);
+      const R ten = (fe - fw - (fn - fs)) * MT(rareac, j, i);
+      const R sh = R(0.25) * ((s_sh[jj][ii] + s_sh[jj][ii + 1]) + (s_sh[jj + 1][ii] + s_sh[jj + 1][ii + 1]));
+      const R coef = fmax(d2, fmin(R(0.2), sm * sqrt(ten * ten + sh * sh)));
+      cd = (R)g.da_min * coef * div;
+    }
+    s_cd[jj][ii] = cd;
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (i > n || j > n) return;
+  const R c0 = s_cd[threadIdx.y][threadIdx.x];
   const long long q = o + (long long)j * g.pitch + i;
-  if (i < n) a.u_o[q] += (corner_damping(u, v, m, g, j, i + 1, d2, sm) - c0) * MT(rdx, j, i);
-  if (j < n) a.v_o[q] += (corner_damping(u, v, m, g, j + 1, i, d2, sm) - c0) * MT(rdy, j, i);
+  if (i < n) a.u_o[q] += (s_cd[threadIdx.y][threadIdx.x + 1] - c0) * MT(rdx, j, i);
+  if (j < n) a.v_o[q] += (s_cd[threadIdx.y + 1][threadIdx.x] - c0) * MT(rdy, j, i);
 }
 
 // ------------------------------------------------------------------------
@@ -976,31 +992,41 @@ __device__ __forceinline__ R corner_mean(const R* p, const Geo& g, int j, int i)
   return R(0.25) * ((C(j - 1, i - 1) + C(j - 1, i)) + (C(j, i - 1) + C(j, i)));
 }
 
+// a 16 x 16 block of faces: the corner means of pef and gz at the two
+// interfaces for its 17 x 17 corners are formed once each in shared memory
 template <typename R>
-__global__ void k_p_grad_d(StepArgs<R> a, const int4* planes) {
+__global__ void __launch_bounds__(256) k_p_grad_d(StepArgs<R> a, const int4* planes) {
+  __shared__ R s_c[4][17][17];  // pef top, pef bottom, gz top, gz bottom
   const int4 pl = planes[blockIdx.z];
   const Geo g = a.geo[pl.x];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = g.n;
-  if (i > n || j > n) return;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
+  if (i0 > n || j0 > n) return;  // the whole block (uniform)
+  const int tid = threadIdx.y * 16 + threadIdx.x;
   const int t = pl.y, k = pl.z;
   const long long oi0 = fld0(g, g.offi, g.nz + 1, t, k), oi1 = fld0(g, g.offi, g.nz + 1, t, k + 1);
-  const R *p0 = a.pef + oi0, *p1 = a.pef + oi1, *g0 = a.gz + oi0, *g1 = a.gz + oi1;
+  const R* src[4] = {a.pef + oi0, a.pef + oi1, a.gz + oi0, a.gz + oi1};
+  for (int e = tid; e < 17 * 17; e += 256) {
+    const int jj = e / 17, ii = e - jj * 17;
+    const int j = j0 + jj, i = i0 + ii;
+    if (j > n || i > n) continue;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s_c[f][jj][ii] = corner_mean(src[f], g, j, i);
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (i > n || j > n) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const TM<R> m = tile_metric(a.M, g, t);
   const long long o = fld0(g, g.off3, g.nz, t, k) + (long long)j * g.pitch + i;
   const R dt = (R)a.P.dt;
-  const R pA0 = corner_mean(p0, g, j, i), pA1 = corner_mean(p1, g, j, i);
-  const R gA0 = corner_mean(g0, g, j, i), gA1 = corner_mean(g1, g, j, i);
-  if (i < n) {  // u on the y-face (i, j): corners (i, j) and (i + 1, j)
-    const R pB0 = corner_mean(p0, g, j, i + 1), pB1 = corner_mean(p1, g, j, i + 1);
-    const R gB0 = corner_mean(g0, g, j, i + 1), gB1 = corner_mean(g1, g, j, i + 1);
-    a.u_o[o] += dt * MT(rdx, j, i) * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
-  }
-  if (j < n) {  // v on the x-face (i, j): corners (i, j) and (i, j + 1)
-    const R pB0 = corner_mean(p0, g, j + 1, i), pB1 = corner_mean(p1, g, j + 1, i);
-    const R gB0 = corner_mean(g0, g, j + 1, i), gB1 = corner_mean(g1, g, j + 1, i);
-    a.v_o[o] += dt * MT(rdy, j, i) * pgrad(gA0, gA1, gB0, gB1, pA0, pA1, pB0, pB1);
-  }
+  const R pA0 = s_c[0][ty][tx], pA1 = s_c[1][ty][tx], gA0 = s_c[2][ty][tx], gA1 = s_c[3][ty][tx];
+  if (i < n)  // u on the y-face (i, j): corners (i, j) and (i + 1, j)
+    a.u_o[o] += dt * MT(rdx, j, i) *
+                pgrad(gA0, gA1, s_c[2][ty][tx + 1], s_c[3][ty][tx + 1], pA0, pA1, s_c[0][ty][tx + 1], s_c[1][ty][tx + 1]);
+  if (j < n)  // v on the x-face (i, j): corners (i, j) and (i, j + 1)
+    a.v_o[o] += dt * MT(rdy, j, i) *
+                pgrad(gA0, gA1, s_c[2][ty + 1][tx], s_c[3][ty + 1][tx], pA0, pA1, s_c[0][ty + 1][tx], s_c[1][ty + 1][tx]);
 }
 
 // ------------------------------------------------------------------------

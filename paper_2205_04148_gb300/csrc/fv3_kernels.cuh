@@ -124,10 +124,16 @@ struct Ctx {
   // kernels enqueued by the library (host count; graph replays add the
   // number captured in the graph)
   long long launches = 0;
-  long long graph_launches = 0;
-  // graph of one remapping step
-  cudaGraphExec_t graph = nullptr;
-  std::vector<unsigned char> graph_key;
+  // graphs of one remapping step, one per (state, parameters) key, so that a
+  // caller alternating between a few states replays instead of re-capturing
+  struct Graph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;  // kernels captured in it
+    long long used = 0;      // last use, for eviction
+  };
+  std::vector<Graph> graphs;
+  long long graph_clock = 0;
   std::string err;
 };
 

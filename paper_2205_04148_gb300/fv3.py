@@ -22,6 +22,7 @@ STATUS = {0: "FV3_OK", -1: "FV3_ERR_ARG", -2: "FV3_ERR_SHAPE", -3: "FV3_ERR_ALIG
 GRID_PERIODIC, GRID_CUBED = 0, 1
 FP64, FP32 = 0, 1
 KIND_CELL, KIND_XFACE, KIND_YFACE, KIND_IFACE = 0, 1, 2, 3
+DENSE_DEVICE, DENSE_HOST, DENSE_HOST_ASYNC = 0, 1, 2
 HALO_WIND, HALO_W, HALO_DELP, HALO_PT, HALO_DELZ, HALO_TRACERS = 1, 2, 4, 8, 16, 32
 
 # exported symbols declared in include/fv3.h
@@ -268,6 +269,29 @@ class Grid:
         self.check(self.L.fv3_export(self.ptr, kind, C.c_void_p(field.data_ptr()),
                                      a.ctypes.data_as(C.c_void_p), 1, 1, member, _stream(stream)))
         return a
+
+    def host_buffer(self, kind, member=0):
+        """a page-locked host tensor of the dense shape of `kind`, library dtype"""
+        import torch
+        return torch.empty(self._dense_shape(kind, member), dtype=self.torch_dtype, pin_memory=True)
+
+    def _host_ok(self, host, kind, member):
+        if not (host.is_pinned() and host.is_contiguous() and host.dtype == self.torch_dtype
+                and tuple(host.shape) == self._dense_shape(kind, member)):
+            raise ValueError("need a contiguous page-locked %s tensor of shape %s"
+                             % (self.torch_dtype, self._dense_shape(kind, member)))
+
+    def put_async(self, field, kind, host, member=0, stream=None):
+        """enqueue the import of a page-locked dense host tensor"""
+        self._host_ok(host, kind, member)
+        self.check(self.L.fv3_import(self.ptr, kind, C.c_void_p(field.data_ptr()), C.c_void_p(host.data_ptr()),
+                                     DENSE_HOST_ASYNC, int(self.precision == FP64), member, _stream(stream)))
+
+    def get_async(self, field, kind, host, member=0, stream=None):
+        """enqueue the export of a field into a page-locked dense host tensor"""
+        self._host_ok(host, kind, member)
+        self.check(self.L.fv3_export(self.ptr, kind, C.c_void_p(field.data_ptr()), C.c_void_p(host.data_ptr()),
+                                     DENSE_HOST_ASYNC, int(self.precision == FP64), member, _stream(stream)))
 
     def load(self, st, dense, member=0):
         for f, k in self.FIELD_KIND.items():
