@@ -381,6 +381,17 @@ def ours(a):
             ps.synchronize()
 
         pipeline(2)
+        # the copies of one step alone (not overlapped), for the record
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        stage_in(0)
+        cs.synchronize()
+        t_in = time.perf_counter() - t
+        ev_done[0].record(ps)
+        t = time.perf_counter()
+        stage_out(0)
+        cs.synchronize()
+        t_out = time.perf_counter() - t
         ke = max(4, a.steps // 2)
         barrier()
         t0 = time.perf_counter()
@@ -388,7 +399,8 @@ def ours(a):
         te = allmax((time.perf_counter() - t0) / ke)
         e2e = {"value": ws * a.n_split * cells / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3,
-               "io": "two states alternate: one advances while the other's result and next inputs are copied"}
+               "io": "two states alternate: one advances while the other's result and next inputs are copied",
+               "h2d_ms_alone": t_in * 1e3, "d2h_ms_alone": t_out * 1e3}
 
     # --- CPU oracle baseline (rank 0, N = 1) -----------------------------
     cpu = None

@@ -160,9 +160,10 @@ fv3_status fv3_get_layout(const fv3_ctx* ctx, int member, fv3_layout* out);
  *     slots plus the pack kernel, both enqueued on `stream`; the call returns
  *     once they are enqueued, and the host array must stay untouched until
  *     the stream has passed them.  A slot is reused only after its previous
- *     copy completed (an event, whatever stream that ran on); growing a slot
- *     waits on the host for that copy.  Lets a caller overlap the I/O of one
- *     state with the substeps of another on a second stream.
+ *     copy completed (an event, whatever stream that ran on).  Each slot is
+ *     allocated on first use with room for any field of the context (FP64
+ *     elements), so the host never waits on a slot.  Lets a caller overlap
+ *     the I/O of one state with the substeps of another on a second stream.
  * dense_is_double: dense elements are double (else float). */
 enum { FV3_DENSE_DEVICE = 0, FV3_DENSE_HOST = 1, FV3_DENSE_HOST_ASYNC = 2 };
 fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, int dense_is_host, int dense_is_double,

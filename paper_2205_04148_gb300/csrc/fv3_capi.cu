@@ -407,6 +407,13 @@ static fv3_status do_pack(fv3_ctx* x, int kind, void* field, void* dense, int ho
     Slot& sl = x->ring[x->ring_next];
     x->ring_next = (x->ring_next + 1) % kSlots;
     if (!sl.done) CK(x, cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+    if (!sl.buf) {  // first use: large enough for any field of the context
+      size_t most = bytes;
+      for (const Geo& gm : x->c.geo)
+        most = std::max(most, (size_t)gm.nt * (gm.nz + 1) * (gm.n + 1) * (gm.n + 1) * sizeof(double));
+      CK(x, cudaMalloc(&sl.buf, most));
+      sl.bytes = most;
+    }
     if (sl.bytes < bytes) {  // grow: wait for the slot's last copy first
       CK(x, cudaEventSynchronize(sl.done));
       if (sl.buf) cudaFree(sl.buf);

@@ -729,35 +729,55 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
   const long long q = (long long)j * P + i;
   R gzr = R(0), gzn_below = R(0);
   const int l = ty * TXW + tx;
+  // the four faces of the cell: x-faces i, i + 1 and y-faces j, j + 1
+  const long long fq[4] = {q, q + 1, q, q + P};
+  const int lo[4] = {l - 1, l, l - TXW, l};
+  const int hi[4] = {l, l + 1, l, l + TXW};
+  auto face = [&](int K, int f) -> R {
+    const long long o = fld0(g, g.off3, nz, it.t, K) + fq[f];
+    return f < 2 ? a.fx1[o] : a.fy1[o];
+  };
+  // the level loop is sequential: the loads run ahead of it (delz one level,
+  // the fluxes two levels), so their latency overlaps the level before
+  const R ar = inner ? MT(area, j, i) : R(1);
+  R fb[4], fa[4], fn[4];  // fluxes at levels K, K - 1, K - 2
+  R dzk = valid ? a.delz[fld0(g, g.off3, nz, it.t, nz - 1) + q] : R(0);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    fb[f] = inner ? face(nz - 1, f) : R(0);
+    fa[f] = inner ? face(nz - 2, f) : R(0);  // nz >= 2
+    fn[f] = R(0);
+  }
   for (int K = nz - 1; K >= 0; --K) {
     const long long o = fld0(g, g.off3, nz, it.t, K);
+    R dzn = R(0);
+    if (valid && K > 0) dzn = a.delz[o - g.plane + q];
+    if (inner && K >= 2) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) fn[f] = face(K - 2, f);
+    }
     if (valid) {
-      gzr = gzr - grav * a.delz[o + q];
+      gzr = gzr - grav * dzk;
       GZ[l] = gzr;
     }
     __syncthreads();
     if (inner) {
-      const long long oa = fld0(g, g.off3, nz, it.t, K > 0 ? K - 1 : 0);
-      const R* fxa = a.fx1 + oa;
-      const R* fxb = a.fx1 + o;
-      const R* fya = a.fy1 + oa;
-      const R* fyb = a.fy1 + o;
-      const long long fq[4] = {q, q + 1, q, q + P};
-      const int lo[4] = {l - 1, l, l - TXW, l};
-      const int hi[4] = {l, l + 1, l, l + TXW};
       R F[4], Gf[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const R A = f < 2 ? fxa[fq[f]] : fya[fq[f]];
-        const R Bv = f < 2 ? fxb[fq[f]] : fyb[fq[f]];
-        F[f] = K == 0 ? Bv : R(0.5) * (A + Bv);
+        F[f] = K == 0 ? fb[f] : R(0.5) * (fa[f] + fb[f]);
         Gf[f] = F[f] * (F[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
       }
-      const R ar = MT(area, j, i);
       const R gzn = (GZ[l] * ar + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar + F[0] - F[1] + F[2] - F[3]);
       a.delzc[o + q] = fmin((gzn_below - gzn) * rgrav, -dzmin);
       gzn_below = gzn;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        fb[f] = fa[f];
+        fa[f] = fn[f];
+      }
     }
+    dzk = dzn;
     __syncthreads();
   }
 }

@@ -12,11 +12,11 @@
 // delz is remapped as delz / delp; u and v on their face columns, whose
 // interfaces are the means of the two neighbouring cell columns' interfaces.
 //
-// One thread per column and field (cell fields, u on y-face columns, v on
-// x-face columns), levels in sequence: the old and new interfaces advance
-// together, so the walk over the overlaps needs only a four-layer window of
-// the field.  Arithmetic in
-// FP64 for both storage precisions.
+// One thread per column and group of up to four cell fields (u on y-face
+// columns and v on x-face columns alone), levels in sequence: the old and new
+// interfaces advance together, so the walk over the overlaps needs only a
+// four-layer window of each field, and the overlap geometry is formed once
+// for the group.  Arithmetic in FP64 for both storage precisions.
 #include <cuda_runtime.h>
 
 #include "fv3_kernels.cuh"
@@ -36,12 +36,6 @@ __device__ __forceinline__ double remap_edge(int e, int nz, double qm2, double q
   const bool o = k0 < k1;
   const double lo = o ? qm1 : q0, hi = o ? q0 : qm1;
   return ka < (o ? k0 : k1) ? lo : (ka > (o ? k1 : k0) ? hi : a);
-}
-
-// mean of the layer's limited parabola over the fraction [x1, x2]
-__device__ __forceinline__ double remap_mean(double qb, double bl, double br, double x1, double x2) {
-  const double aL = qb + bl, aR = qb + br, a6 = -3.0 * (bl + br);
-  return aL + 0.5 * (aR - aL + a6) * (x1 + x2) - a6 * (1.0 / 3.0) * (x1 * x1 + x1 * x2 + x2 * x2);
 }
 
 template <typename R>
@@ -77,20 +71,41 @@ struct ColumnP {
   }
 };
 
-// remap one field of one column; out(k) receives the new layer means
-template <typename R, typename F>
-__device__ void remap_walk(const ColumnP<R>& C, const ColumnSrc<R>& src, F out) {
+// Remap NF fields of one column together: the overlaps of old and new layers
+// (their pressure widths and the weights of the parabola terms) are formed
+// once and applied to every field.  The limited parabola of an old layer
+// (mean qb, edge values qb + bl and qb + br) integrates over the fraction
+// [x1, x2] of the layer, of pressure width w, to
+//   w (qb + bl (1 - 2 s1 + s2) + br (s2 - s1)),  s1 = x1 + x2,
+//   s2 = x1^2 + x1 x2 + x2^2
+// (a whole layer gives w qb).  out(f, k, value, dpn) receives the new layer
+// means.
+template <int NF, typename R, typename F>
+__device__ void remap_walk(const ColumnP<R>& C, const ColumnSrc<R> (&src)[NF], F out) {
   const int nz = C.nz;
-  // window q[m-1 .. m+2] (the right edge of layer m needs no more)
-  double w1 = 0.0, w2 = src.at(0), w3 = nz > 1 ? src.at(1) : 0.0, w4 = nz > 2 ? src.at(2) : 0.0;
-  double al = remap_edge(0, nz, 0.0, 0.0, w2, 0.0);  // left edge of layer 0
-  double pa = C.ptop, pb = C.ptop;                   // old interfaces of columns a, b
+  // per field the window q[m-1 .. m+2] (the right edge of layer m needs no more)
+  double w1[NF], w2[NF], w3[NF], w4[NF], al[NF], bl[NF], br[NF], mass[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    w1[f] = 0.0;
+    w2[f] = src[f].at(0);
+    w3[f] = nz > 1 ? src[f].at(1) : 0.0;
+    w4[f] = nz > 2 ? src[f].at(2) : 0.0;
+    al[f] = remap_edge(0, nz, 0.0, 0.0, w2[f], 0.0);  // left edge of layer 0
+    mass[f] = 0.0;
+  }
+  double pa = C.ptop, pb = C.ptop;  // old interfaces of columns a, b
   int k = 0;
-  double pn_lo = C.pn(0), pn_hi = C.pn(1), mass = 0.0;
+  double pn_lo = C.pn(0), pn_hi = C.pn(1);
   for (int m = 0; m < nz && k < nz; ++m) {
-    const double ar = remap_edge(m + 1, nz, w1, w2, w3, w4);  // right edge of layer m
-    double bl = al - w2, br = ar - w2;
-    ppm_limit(bl, br);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const double ar = remap_edge(m + 1, nz, w1[f], w2[f], w3[f], w4[f]);  // right edge of layer m
+      bl[f] = al[f] - w2[f];
+      br[f] = ar - w2[f];
+      ppm_limit(bl[f], br[f]);
+      al[f] = ar;
+    }
     double na, nb;
     C.next_old(m, pa, pb, &na, &nb);
     const double pe_lo = C.dpb ? 0.5 * (pa + pb) : pa;
@@ -101,12 +116,21 @@ __device__ void remap_walk(const ColumnP<R>& C, const ColumnSrc<R>& src, F out) 
       // pressures are positive: their bit patterns order like the values
       const long long khi = __double_as_longlong(pe_hi), knh = __double_as_longlong(pn_hi);
       const double top = knh < khi ? pn_hi : pe_hi;
-      if (__double_as_longlong(top) > __double_as_longlong(x))
-        mass += (top - x) * remap_mean(w2, bl, br, (x - pe_lo) * rdp, (top - pe_lo) * rdp);
+      if (__double_as_longlong(top) > __double_as_longlong(x)) {
+        const double x1 = (x - pe_lo) * rdp, x2 = (top - pe_lo) * rdp;
+        const double s1 = x1 + x2, s2 = fma(x1, s1, x2 * x2);
+        const double w = top - x, wl = w * (1.0 - 2.0 * s1 + s2), wr = w * (s2 - s1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) mass[f] = fma(w, w2[f], fma(wl, bl[f], fma(wr, br[f], mass[f])));
+      }
       if (knh <= khi) {  // new layer k ends inside old layer m
-        out(k, mass * rcp(pn_hi - pn_lo), pn_hi - pn_lo);
+        const double dpn = pn_hi - pn_lo, rdpn = rcp(dpn);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          out(f, k, mass[f] * rdpn, dpn);
+          mass[f] = 0.0;
+        }
         ++k;
-        mass = 0.0;
         x = __double_as_longlong(top) > __double_as_longlong(x) ? top : x;
         if (k == nz) break;
         pn_lo = pn_hi;
@@ -117,21 +141,45 @@ __device__ void remap_walk(const ColumnP<R>& C, const ColumnSrc<R>& src, F out) 
     }
     pa = na;
     pb = nb;
-    al = ar;
-    w1 = w2;
-    w2 = w3;
-    w3 = w4;
-    w4 = m + 3 < nz ? src.at(m + 3) : 0.0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      w1[f] = w2[f];
+      w2[f] = w3[f];
+      w3[f] = w4[f];
+      w4[f] = m + 3 < nz ? src[f].at(m + 3) : 0.0;
+    }
   }
+}
+
+// cell fields in groups of up to RG per thread
+constexpr int RG = 4;
+
+template <int NF, typename R>
+__device__ __forceinline__ void remap_cells(const RemapArgs<R>& a, const ColumnP<R>& C, long long bq, int f0) {
+  ColumnSrc<R> src[NF];
+  R* o[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    src[f] = ColumnSrc<R>{a.in[f0 + f] + bq, f0 + f == 2 ? a.delp + bq : nullptr, C.stride};
+    o[f] = a.out[f0 + f] + bq;
+  }
+  R* dpo = a.delp_o + bq;
+  const long long stride = C.stride;
+  remap_walk<NF>(C, src, [&](int f, int k, double v, double dpn) {
+    o[f][k * stride] = (R)(f0 + f == 2 ? v * dpn : v);  // delz from delz / delp
+    if (f0 + f == 0) dpo[k * stride] = (R)dpn;
+  });
 }
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_remap(RemapArgs<R> a, const RowItem* rows) {
   const RowItem r = rows[blockIdx.y];
   const Geo g = a.geo[r.m];
-  // z < nf: cell field z (z == 0 also writes delp); nf: u (y-faces); nf + 1: v (x-faces)
+  // z < ng: cell fields RG z .. RG z + RG - 1 (field 0 also writes delp);
+  // ng: u (y-faces); ng + 1: v (x-faces)
+  const int ng = (a.nf + RG - 1) / RG;
   const int z = blockIdx.z;
-  const int kind = z < a.nf ? 0 : z == a.nf ? 1 : 2;
+  const int kind = z < ng ? 0 : z == ng ? 1 : 2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = r.j, n = g.n, nz = g.nz;
   if (kind == 0 && (i >= n || j >= n)) return;
   if (kind == 1 && (i >= n || j > n)) return;
@@ -157,26 +205,22 @@ __global__ void __launch_bounds__(128) k_remap(RemapArgs<R> a, const RowItem* ro
   C.psa = psa;
   C.psb = psb;
   if (kind == 0) {
-    R* dpo = a.delp_o + base + q;
-    const int f = z;
-    ColumnSrc<R> src{a.in[f] + base + q, f == 2 ? a.delp + base + q : nullptr, stride};
-    R* o = a.out[f] + base + q;
-    const bool ratio = f == 2;
-    remap_walk(C, src, [&](int k, double v, double dpn) {
-      o[k * stride] = (R)(ratio ? v * dpn : v);
-      if (f == 0) dpo[k * stride] = (R)dpn;
-    });
+    const int f0 = z * RG, nfz = min(RG, a.nf - f0);
+    if (nfz == 4) remap_cells<4>(a, C, base + q, f0);
+    else if (nfz == 3) remap_cells<3>(a, C, base + q, f0);
+    else if (nfz == 2) remap_cells<2>(a, C, base + q, f0);
+    else remap_cells<1>(a, C, base + q, f0);
   } else {
-    ColumnSrc<R> src{(kind == 1 ? a.u : a.v) + base + q, nullptr, stride};
+    ColumnSrc<R> src[1] = {ColumnSrc<R>{(kind == 1 ? a.u : a.v) + base + q, nullptr, stride}};
     R* o = (kind == 1 ? a.u_o : a.v_o) + base + q;
-    remap_walk(C, src, [&](int k, double v, double) { o[k * stride] = (R)v; });
+    remap_walk<1>(C, src, [&](int, int k, double v, double) { o[k * stride] = (R)v; });
   }
 }
 
 template <typename R>
 static void remap_t(Ctx& c, const RemapArgs<R>& a, cudaStream_t st) {
   const int nb = (c.max_n + 1 + 127) / 128;
-  k_remap<R><<<dim3(nb, c.n_rows_f, a.nf + 2), 128, 0, st>>>(a, c.rows_f);
+  k_remap<R><<<dim3(nb, c.n_rows_f, (a.nf + RG - 1) / RG + 2), 128, 0, st>>>(a, c.rows_f);
   ++c.launches;
 }
 
