@@ -155,15 +155,18 @@ fv3_status fv3_get_layout(const fv3_ctx* ctx, int member, fv3_layout* out);
  *   FV3_DENSE_DEVICE (0): the dense array is device memory (a pack kernel);
  *   FV3_DENSE_HOST (1): host memory, copied through a staging buffer; host
  *     exports return after the copy completed;
- *   FV3_DENSE_HOST_ASYNC (2): page-locked host memory, asynchronous: one
- *     contiguous copy between the host array and one of four device staging
- *     slots plus the pack kernel, both enqueued on `stream`; the call returns
- *     once they are enqueued, and the host array must stay untouched until
- *     the stream has passed them.  A slot is reused only after its previous
- *     copy completed (an event, whatever stream that ran on).  Each slot is
- *     allocated on first use with room for any field of the context (FP64
- *     elements), so the host never waits on a slot.  Lets a caller overlap
- *     the I/O of one state with the substeps of another on a second stream.
+ *   FV3_DENSE_HOST_ASYNC (2): page-locked host memory, asynchronous: the
+ *     call returns once the copy is enqueued on `stream`, and the host array
+ *     must stay untouched until the stream has passed it.  With dense
+ *     elements of the library's precision (dense_is_double = 1 for FP64, 0
+ *     for FP32) one 3-D copy-engine transfer between the dense array and the
+ *     field's interior, no kernel (so it never waits for multiprocessors held
+ *     by a substep on another stream).  Otherwise a contiguous copy into one
+ *     of four device staging slots plus the converting pack kernel, both on
+ *     `stream`; a slot is reused only after its previous copy completed (an
+ *     event, whatever stream that ran on), and is allocated on first use with
+ *     room for any field of the context.  Lets a caller overlap the I/O of
+ *     one state with the substeps of another on a second stream.
  * dense_is_double: dense elements are double (else float). */
 enum { FV3_DENSE_DEVICE = 0, FV3_DENSE_HOST = 1, FV3_DENSE_HOST_ASYNC = 2 };
 fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, int dense_is_host, int dense_is_double,

@@ -401,9 +401,28 @@ static fv3_status do_pack(fv3_ctx* x, int kind, void* field, void* dense, int ho
   const int nlev = iface ? g.nz + 1 : g.nz;
   const int pk = kind == FV3_KIND_IFACE ? 0 : kind;  // interface fields are cell-shaped
   const size_t bytes = dense_count(g, pk, nlev) * (dbl ? 8 : 4);
+  if (host == FV3_DENSE_HOST_ASYNC && dbl == (x->c.prec == FV3_FP64 ? 1 : 0)) {
+    // same element type: one 3-D copy by the copy engine between the dense
+    // host array and the field's interior (plane z = t * nlev + k, nj rows of
+    // ni elements), no kernel, so it never waits for SMs held by the substep
+    const size_t es = x->c.esize;
+    const int n = g.n, ni = n + (pk == 1 || pk == 3), nj = n + (pk == 2 || pk == 3);
+    const long long base = iface ? g.offi : g.off3;
+    char* fo = (char*)field + (size_t)(base + (long long)HALO * g.pitch + g.ox) * es;
+    cudaMemcpy3DParms cp{};
+    cudaPitchedPtr fp = make_cudaPitchedPtr(fo, (size_t)g.pitch * es, (size_t)ni, (size_t)g.rows);
+    cudaPitchedPtr hp = make_cudaPitchedPtr(dense, (size_t)ni * es, (size_t)ni, (size_t)nj);
+    cp.extent = make_cudaExtent((size_t)ni * es, (size_t)nj, (size_t)g.nt * nlev);
+    cp.srcPtr = dir == 0 ? hp : fp;
+    cp.dstPtr = dir == 0 ? fp : hp;
+    cp.kind = dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    CK(x, cudaMemcpy3DAsync(&cp, st));
+    return FV3_OK;
+  }
   if (host == FV3_DENSE_HOST_ASYNC) {
-    // one contiguous copy between the host array and a staging slot, and the
-    // pack kernel between the slot and the field, both on `st`
+    // element type converted: one contiguous copy between the host array and
+    // a staging slot, and the pack kernel between the slot and the field,
+    // both on `st`
     Slot& sl = x->ring[x->ring_next];
     x->ring_next = (x->ring_next + 1) % kSlots;
     if (!sl.done) CK(x, cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));

@@ -170,6 +170,40 @@ __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
   }
 }
 
+// The block's tile with its halo of 3 ([x0 - 3, x1 + 3) x [y0 - 3, y1 + 3)),
+// fetched into NP registers per thread (the points of the flat loop of for2,
+// 256 threads) and later put into shared memory: the loads are in flight
+// while the block computes.  q: origin of the level.
+template <int NP, typename R>
+__device__ __forceinline__ void tile_fetch(const R* q, R (&reg)[NP], const Blk& B, int P) {
+  const int w = B.x1 - B.x0 + 6, total = w * (B.y1 - B.y0 + 6);
+  const float rw = 1.0f / (float)w;
+  const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int e = tid + p * 256;
+    if (e < total) {
+      const int j = (int)(((float)e + 0.5f) * rw);
+      reg[p] = q[(long long)(B.y0 - 3 + j) * P + (B.x0 - 3 + e - j * w)];
+    }
+  }
+}
+
+template <int NP, typename R>
+__device__ __forceinline__ void tile_put(R* Q, const R (&reg)[NP], const Blk& B) {
+  const int w = B.x1 - B.x0 + 6, total = w * (B.y1 - B.y0 + 6);
+  const float rw = 1.0f / (float)w;
+  const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int e = tid + p * 256;
+    if (e < total) {
+      const int j = (int)(((float)e + 0.5f) * rw);
+      Q[j * B.SX + (e - j * w)] = reg[p];
+    }
+  }
+}
+
 // Cube corners (reading R3): rewrite the 3x3 missing-quadrant cells of a
 // shared-memory scalar from the block's own strips, turned about the corner:
 // role 0 for sweeps along x (from the W/E strip), 1 along y (S/N strip).
@@ -1134,10 +1168,21 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
       D1[l] = rcp(d1);  // reciprocal, shared by every tracer
       a.dp1[o + G(j, i)] = d1;
     });
+    // each tracer's tile (block + halo 3) is fetched into registers while the
+    // previous tracer is transported (the plain kernel; the learned one has
+    // no registers to spare)
+    constexpr int NPRE = LEARN ? 1 : ((BX + 6) * (BY + 6) + 255) / 256;
+    R pre[NPRE];
+    if (!LEARN) tile_fetch<NPRE>(a.q[0] + o, pre, B, P);
     for (int tq = 0; tq < a.nq; ++tq) {
-      const R* q = a.q[tq] + o;
       __syncthreads();
-      for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
+      if (LEARN) {
+        const R* q = a.q[tq] + o;
+        for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
+      } else {
+        tile_put<NPRE>(Q, pre, B);
+        if (tq + 1 < a.nq) tile_fetch<NPRE>(a.q[tq + 1] + o, pre, B, P);
+      }
       transport<R, LEARN>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
       R* qo = a.q_o[tq] + o;
       for2(x0, x1, y0, y1, [&](int i, int j) {

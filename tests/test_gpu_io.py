@@ -1,7 +1,8 @@
-"""Asynchronous host import/export (a contiguous copy between a page-locked
-dense host array and a staging slot, and the pack kernel, on the caller's
-stream) and the per-state graph cache of run_dyn: bitwise the same as the
-synchronous copies and as one state advanced alone."""
+"""Asynchronous host import/export (a 3-D copy-engine transfer between a
+page-locked dense host array and the field's interior; with a converted
+element type a staging slot and the pack kernel) on the caller's stream, and
+the per-state graph cache of run_dyn: bitwise the same as the synchronous
+copies and as one state advanced alone."""
 import ctypes as C
 
 import numpy as np
@@ -89,3 +90,32 @@ def test_two_states_alternating_equal_one_state_alone():
         torch.cuda.synchronize()
         for nm in NAMES + ("q0", "q1"):
             assert np.array_equal(g.read(X, nm), h.read(Y, nm)), (seed, nm)
+
+
+def test_async_converting_copies_match_staged():
+    """double host data into an FP32 context (staging slots + pack kernel),
+    more copies in flight than slots"""
+    import torch
+    from paper_2205_04148_gb300 import fv3
+    n, nz = 20, 5
+    st = seeded(True, n, nz, 5, 0)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=fv3.FP32)
+    gs, ga = g.alloc_state(0), g.alloc_state(0)
+    g.load(gs, st)
+    s = torch.cuda.Stream()
+    hin, hout = {}, {}
+    for nm in NAMES:
+        k = g.FIELD_KIND[nm]
+        hin[nm] = torch.from_numpy(np.ascontiguousarray(st[nm], dtype=np.float64)).pin_memory()
+        g.check(g.L.fv3_import(g.ptr, k, C.c_void_p(ga[nm].data_ptr()), C.c_void_p(hin[nm].data_ptr()),
+                               fv3.DENSE_HOST_ASYNC, 1, 0, C.c_void_p(s.cuda_stream)))
+    for nm in NAMES:
+        k = g.FIELD_KIND[nm]
+        hout[nm] = torch.empty(hin[nm].shape, dtype=torch.float64, pin_memory=True)
+        g.check(g.L.fv3_export(g.ptr, k, C.c_void_p(gs[nm].data_ptr()), C.c_void_p(hout[nm].data_ptr()),
+                               fv3.DENSE_HOST_ASYNC, 1, 0, C.c_void_p(s.cuda_stream)))
+    s.synchronize()
+    for nm in NAMES:
+        k = g.FIELD_KIND[nm]
+        assert np.array_equal(g.get(ga[nm], k), g.get(gs[nm], k)), nm
+        assert np.array_equal(hout[nm].numpy(), g.get(gs[nm], k)), nm
