@@ -53,11 +53,13 @@ DSW_FLOPS_PER_CELL = 655
 # uc, vc and writes u, v, w, delp, pt (12 words).
 DSW_WORDS_PER_CELL = 12
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
-# DRAM bytes (read + write) per cell of one d_sw launch, from an ncu capture of
-# the kernel in this launch configuration (profiles/k_d_sw_fp64_c96x24.md:
-# C96 x 24, FP64, 16 x 16 blocks, one level per work item, persistent grid);
-# scaled by the cells of the timed launch.  Other configurations report null.
-DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 199.0}
+# DRAM bytes (read + write) per cell of one d_sw launch, from ncu captures of
+# the kernel in these launch configurations (profiles/k_d_sw_fp64_c96x24.md:
+# C96 x 24, FP64, 16 x 16 blocks, one level per work item, persistent grid;
+# profiles/k_d_sw_fp32_c192x16.md: C192 x 16, FP32, 32 x 8 blocks, four levels
+# per work item); scaled by the cells of the timed launch (the traffic grows in
+# proportion to the work items).  Other configurations report null.
+DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 197.8, ("f32", 32, 8, 4, False): 103.5}
 
 
 def parse():
@@ -392,15 +394,23 @@ def ours(a):
         stage_out(0)
         cs.synchronize()
         t_out = time.perf_counter() - t
+        # three timed repetitions of ke pipelined steps; the median is reported
         ke = max(4, a.steps // 2)
-        barrier()
-        t0 = time.perf_counter()
-        pipeline(ke)
-        te = allmax((time.perf_counter() - t0) / ke)
+        clocks_e2e = Clocks(smi_index, enabled=not a.no_clocks)
+        clocks_e2e.start()
+        reps = []
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            pipeline(ke)
+            reps.append(allmax((time.perf_counter() - t0) / ke))
+        te = statistics.median(reps)
+        clk_e2e = clocks_e2e.stop()
         e2e = {"value": ws * a.n_split * cells / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3,
                "io": "two states alternate: one advances while the other's result and next inputs are copied",
-               "h2d_ms_alone": t_in * 1e3, "d2h_ms_alone": t_out * 1e3}
+               "h2d_ms_alone": t_in * 1e3, "d2h_ms_alone": t_out * 1e3, "clocks": clk_e2e,
+               "repeats_ms_per_step": [r * 1e3 for r in reps], "steps_per_repeat": ke}
 
     # --- CPU oracle baseline (rank 0, N = 1) -----------------------------
     cpu = None
@@ -544,6 +554,7 @@ def batched(a):
             g1 = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=prec)
             s1 = g1.alloc_state()
             g1.load(s1, members[sizes.index(n)])
+            g1.autotune(s1, prm)  # each member alone at its own best launch shape
             for _ in range(2):
                 g1.run_dyn(s1, prm, 1)
             torch.cuda.synchronize()

@@ -291,7 +291,9 @@ fv3_status fv3_math_check(int what, const double* x, const double* y, double* ou
 
 /* Block shape (bx x by cells) and level chunk of the horizontal kernels
  * (c_sw, d_sw, tracer_2d).  Compiled shapes: 32x8, 32x16, 64x8, 16x16;
- * 1 <= kchunk <= npz.  Drops the cached remapping-step graph. */
+ * 1 <= kchunk <= npz.  Drops the cached remapping-step graphs.  Defaults at
+ * fv3_init_grid: FP64 16x16, kchunk 1, persistent launches; FP32 32x8,
+ * kchunk min(4, npz), one CTA per work item. */
 fv3_status fv3_set_tiles(fv3_ctx* ctx, int bx, int by, int kchunk);
 fv3_status fv3_get_tiles(const fv3_ctx* ctx, int* bx, int* by, int* kchunk);
 

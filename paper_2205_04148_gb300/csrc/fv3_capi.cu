@@ -193,6 +193,14 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
   c.nmem = d->n_members;
   c.prec = d->precision;
   c.esize = c.prec == FV3_FP64 ? 8 : 4;
+  // default launch shapes, the autotuner's picks on one C96 x 80 state: FP64
+  // 16 x 16 blocks, one level per work item, persistent grid; FP32 32 x 8
+  // blocks, four levels per work item
+  if (c.prec == FV3_FP64) {
+    c.BX = 16; c.BY = 16; c.kchunk = 1; c.persistent = 1;
+  } else {
+    c.BX = 32; c.BY = 8; c.kchunk = std::min(4, d->npz); c.persistent = 0;
+  }
   const int nt = c.spec.cubed ? 6 : 1;
   const int align = 128 / c.esize;  // elements per 128 bytes
   long long o3 = 0, oi = 0, o2 = 0, oc = 0;

@@ -231,8 +231,32 @@ __device__ __forceinline__ void corner_roles(R* Q, const Blk& B, int n, int role
 // shared-memory arrays of the transport
 template <typename R>
 struct TS {
-  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL, *GX, *GY;
+  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL;
+  // metric terms of the block's tile staged in shared memory once per work
+  // item (area, 1/area; the damping weights wx, wy where kStageW)
+  R *AREA, *RAREA, *WX, *WY;
 };
+
+// FP64 kernels also stage the damping weights (shared memory allows it at
+// the FP64 block shapes; the FP32 blocks, four per SM, have no room)
+template <typename R>
+constexpr bool kStageW = sizeof(R) == 8;
+
+// the metric terms of the block's tile into shared memory: area and 1/area
+// over the tile, wx and wy over the faces the damping reads
+template <typename R>
+__device__ __forceinline__ void stage_metric(const TS<R>& S, const Blk& B, const TM<R>& m, bool weights) {
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.AREA[l] = MT(area, j, i);
+    S.RAREA[l] = MT(rarea, j, i);
+  });
+  if (kStageW<R> && weights) {
+    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
+  }
+}
 
 template <typename R>
 __device__ __forceinline__ bool positive(R c) { return c > R(0); }
@@ -316,6 +340,16 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   const bool dmp = damp != R(0);
+  // the damping gradients live in the output arrays until the Laplacian is
+  // formed; the fluxes are written only after it
+  R* const GX = FXO;
+  R* const GY = FYO;
+  auto wxv = [&](int l, int j, int i) -> R {
+    if constexpr (kStageW<R>) return S.WX[l]; else return MT(wx, j, i);
+  };
+  auto wyv = [&](int l, int j, int i) -> R {
+    if constexpr (kStageW<R>) return S.WY[l]; else return MT(wy, j, i);
+  };
   MlpFrag F;
   if (LEARN) mlp_load(mlp, F);
   __syncthreads();  // Q (and the strips the corner turn reads) complete
@@ -329,7 +363,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.GY[l] = (Q[l] - Q[l - SX]) * MT(wy, j, i);
+      GY[l] = (Q[l] - Q[l - SX]) * wyv(l, j, i);
     });
   __syncthreads();
   if (LEARN)
@@ -343,7 +377,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // inner y-update in every column of the block and its halo
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * S.RDYd[l];
+    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * S.RDYd[l];
   });
   if (cc) corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
   __syncthreads();
@@ -355,7 +389,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.GX[l] = (Q[l] - Q[l - 1]) * MT(wx, j, i);
+      GX[l] = (Q[l] - Q[l - 1]) * wxv(l, j, i);
     });
   __syncthreads();
   if (LEARN)
@@ -368,7 +402,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.LAP[l] = (S.GX[l + 1] - S.GX[l] + S.GY[l + SX] - S.GY[l]) * MT(rarea, j, i);
+      S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
   __syncthreads();
   // outer x-sweep of the y-updated field
@@ -395,7 +429,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // inner x-update in every row of the block and its halo
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.QIJ[l] = (Q[l] * MT(area, j, i) + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * S.RDXd[l];
+    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * S.RDXd[l];
   });
   __syncthreads();
   // outer y-sweep of the x-updated field
@@ -421,7 +455,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * MT(wx, j, i);
+      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * wxv(l, j, i);
       if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
       FXO[l] = FXO[l] + f;
     });
@@ -429,7 +463,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp) {
     for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * MT(wy, j, i);
+      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * wyv(l, j, i);
       if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
       FYO[l] = FYO[l] + f;
     });
@@ -460,11 +494,11 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
   __syncthreads();
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+    S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
   });
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+    S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
   });
   (void)scaled;
   (void)fr;
@@ -484,7 +518,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
   TS<R> S;
   S.CRX = sb + 10 * SA; S.XFX = sb + 11 * SA; S.CRY = sb + 12 * SA; S.YFX = sb + 13 * SA;
   S.RDXd = sb + 14 * SA; S.RDYd = sb + 15 * SA; S.FY2 = sb + 16 * SA; S.FX2 = sb + 17 * SA;
-  S.QIJ = sb + 18 * SA; S.LAP = sb + 19 * SA; S.AL = sb + 20 * SA; S.GX = sb + 21 * SA; S.GY = sb + 22 * SA;
+  S.QIJ = sb + 18 * SA; S.LAP = sb + 19 * SA; S.AL = sb + 20 * SA;
+  S.AREA = sb + 21 * SA; S.RAREA = sb + 22 * SA;
+  S.WX = kStageW<R> ? sb + 23 * SA : nullptr;
+  S.WY = kStageW<R> ? sb + 24 * SA : nullptr;
   (void)SY;
 
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
@@ -502,6 +539,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
   const R damp = (R)(dd * dd);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  stage_metric(S, B, m, true);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
@@ -532,7 +570,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
     R* dpo = a.delp_o + o;
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
+      const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
       DPN[l] = rcp(d);  // reciprocal, used by pt and w
       dpo[G(j, i)] = d;
     });
@@ -547,7 +585,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
-            (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) * DPN[l];
+            (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * DPN[l];
       });
     }
     __syncthreads();
@@ -555,7 +593,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
     for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
-               V[l] * MT(dy, j, i)) * MT(rarea, j, i) + MT(fA, j, i);
+               V[l] * MT(dy, j, i)) * S.RAREA[l] + MT(fA, j, i);
     });
     transport(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, FXO, FYO);
     // kinetic energy at corners from upwind-PPM corner winds
@@ -1122,7 +1160,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
   TS<R> S;
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
   S.RDXd = sb + 11 * SA; S.RDYd = sb + 12 * SA; S.FY2 = sb + 13 * SA; S.FX2 = sb + 14 * SA;
-  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA; S.AL = sb + 17 * SA; S.GX = S.LAP; S.GY = S.LAP;
+  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA; S.AL = sb + 17 * SA;
+  S.AREA = sb + 18 * SA; S.RAREA = sb + 19 * SA; S.WX = nullptr; S.WY = nullptr;  // no damping
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
   for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
   const Item it = a.items[wi / kz];
@@ -1135,6 +1174,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
   const R fr = R(1) / R(*a.nsplt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
+  stage_metric(S, B, m, false);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
@@ -1154,16 +1194,16 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
     __syncthreads();
     for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+      S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
     });
     for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+      S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
     });
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
-      const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * MT(rarea, j, i);
+      const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
       D0[l] = d0;
       D1[l] = rcp(d1);  // reciprocal, shared by every tracer
       a.dp1[o + G(j, i)] = d1;
@@ -1187,7 +1227,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
       R* qo = a.q_o[tq] + o;
       for2(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
-        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * MT(rarea, j, i)) * D1[l];
+        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * D1[l];
       });
     }
     __syncthreads();
@@ -1210,7 +1250,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
   TS<R> S;
   S.CRX = sb + 5 * SA; S.XFX = sb + 6 * SA; S.CRY = sb + 7 * SA; S.YFX = sb + 8 * SA;
   S.RDXd = sb + 9 * SA; S.RDYd = sb + 10 * SA; S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA;
-  S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA; S.GX = sb + 16 * SA; S.GY = sb + 17 * SA;
+  S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA;
+  S.AREA = sb + 16 * SA; S.RAREA = sb + 17 * SA;
+  S.WX = kStageW<R> ? sb + 18 * SA : nullptr;
+  S.WY = kStageW<R> ? sb + 19 * SA : nullptr;
   const bool mass = a.mfx != nullptr;
   const R damp = (R)a.damp;
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
@@ -1224,6 +1267,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
   const TM<R> m = tile_metric(a.M, g, it.t);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
+  stage_metric(S, B, m, damp != R(0));  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
@@ -1244,11 +1288,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
     __syncthreads();
     for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDYd[l] = rcp(MT(area, j, i) + S.YFX[l] - S.YFX[l + SX]);
+      S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
     });
     for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
-      S.RDXd[l] = rcp(MT(area, j, i) + S.XFX[l] - S.XFX[l + 1]);
+      S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
     });
     transport<R, false>(Q, S, B, m, n, cc, mass ? MFX : (const R*)nullptr, mass ? MFY : (const R*)nullptr, damp,
                         (const R*)nullptr, FXO, FYO);
@@ -1589,7 +1633,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     enqueue_halo_fields(c, F, st);
   }
   if (run(6)) {  // d_sw
-    const size_t sm = blk_smem(c, 23);
+    const size_t sm = blk_smem(c, kStageW<R> ? 25 : 23);
     const bool learn = P.hord == 1 && P.mlp;
 #define FV3_DSW(X, Y)                                                                  \
   (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
@@ -1739,7 +1783,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   a.learn = P.hord == 1 && P.mlp != nullptr;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, 18);
+  const size_t sm = blk_smem(c, 20);
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
@@ -1780,7 +1824,7 @@ static void fv_tp_2d_t(Ctx& c, const TpPtrs& p, cudaStream_t st) {
   a.damp = p.damp;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, 18);
+  const size_t sm = blk_smem(c, kStageW<R> ? 20 : 18);
 #define FV3_TP(X, Y)                                                                   \
   set_smem(k_fv_tp_2d<R, X, Y>, sm);                                                   \
   k_fv_tp_2d<R, X, Y><<<work_grid(c, k_fv_tp_2d<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
