@@ -364,9 +364,15 @@ def ours(a):
             for nm in outs:
                 g.get_async(field(states[x], nm), kind(nm), hout[x][nm], stream=cs.cuda_stream)
 
+        spans = []  # per step: events around its substeps on the compute stream
+
         def advance(x):
             ps.wait_event(ev_in[x])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ps)
             g.run_dyn(states[x], prm, 1, stream=ps.cuda_stream)
+            e1.record(ps)
+            spans.append((e0, e1))
             ev_done[x].record(ps)
 
         def pipeline(k):
@@ -399,18 +405,21 @@ def ours(a):
         clocks_e2e = Clocks(smi_index, enabled=not a.no_clocks)
         clocks_e2e.start()
         reps = []
+        busy = []
         for _ in range(3):
             barrier()
             t0 = time.perf_counter()
             pipeline(ke)
             reps.append(allmax((time.perf_counter() - t0) / ke))
+            busy.append(sum(e0.elapsed_time(e1) for e0, e1 in spans[-ke:]) / ke)
         te = statistics.median(reps)
         clk_e2e = clocks_e2e.stop()
         e2e = {"value": ws * a.n_split * cells / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3,
                "io": "two states alternate: one advances while the other's result and next inputs are copied",
                "h2d_ms_alone": t_in * 1e3, "d2h_ms_alone": t_out * 1e3, "clocks": clk_e2e,
-               "repeats_ms_per_step": [r * 1e3 for r in reps], "steps_per_repeat": ke}
+               "repeats_ms_per_step": [r * 1e3 for r in reps], "steps_per_repeat": ke,
+               "substeps_ms_per_step": busy}
 
     # --- CPU oracle baseline (rank 0, N = 1) -----------------------------
     cpu = None

@@ -233,14 +233,59 @@ template <typename R>
 struct TS {
   R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL;
   // metric terms of the block's tile staged in shared memory once per work
-  // item (area, 1/area; the damping weights wx, wy where kStageW)
+  // item (area, 1/area; the damping weights wx, wy in the damped transports)
   R *AREA, *RAREA, *WX, *WY;
 };
 
-// FP64 kernels also stage the damping weights (shared memory allows it at
-// the FP64 block shapes; the FP32 blocks, four per SM, have no room)
+// FP64 kernels keep the reciprocal denominators of the two inner updates in
+// shared memory (a quotient costs several FP64 pipe slots); the FP32 kernels
+// recompute them (cheap on the FP32 pipe) and spend those two arrays on the
+// damping weights, so that four FP32 blocks still fit an SM
 template <typename R>
-constexpr bool kStageW = sizeof(R) == 8;
+constexpr bool kStoreRD = sizeof(R) == 8;
+
+// 1 / (area + the two area fluxes) of the y- and x-inner updates at l
+template <typename R>
+__device__ __forceinline__ R inner_rdy(const TS<R>& S, int l, int SX) {
+  if constexpr (kStoreRD<R>) return S.RDYd[l];
+  else return rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
+}
+template <typename R>
+__device__ __forceinline__ R inner_rdx(const TS<R>& S, int l) {
+  if constexpr (kStoreRD<R>) return S.RDXd[l];
+  else return rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
+}
+
+// the stored denominators (kStoreRD): y over [x0-3, x1+3) x [y0, y1), x over
+// [x0, x1) x [y0-3, y1+3); read after the next barrier
+template <typename R>
+__device__ __forceinline__ void inner_denominators(const TS<R>& S, const Blk& B) {
+  if constexpr (kStoreRD<R>) {
+    const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
+    });
+    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
+    });
+  }
+}
+
+// shared-memory arrays after the base ones of a kernel: area, 1/area, the
+// stored denominators (kStoreRD) and the damping weights (if `weights`)
+template <typename R>
+constexpr int extra_arrays(bool weights) {
+  return 2 + (kStoreRD<R> ? 2 : 0) + (weights ? 2 : 0);
+}
+template <typename R>
+__device__ __forceinline__ void assign_extra(TS<R>& S, R* p, int SA, bool weights) {
+  S.AREA = p; p += SA;
+  S.RAREA = p; p += SA;
+  if (kStoreRD<R>) { S.RDXd = p; p += SA; S.RDYd = p; p += SA; } else { S.RDXd = nullptr; S.RDYd = nullptr; }
+  if (weights) { S.WX = p; p += SA; S.WY = p; } else { S.WX = nullptr; S.WY = nullptr; }
+}
 
 // the metric terms of the block's tile into shared memory: area and 1/area
 // over the tile, wx and wy over the faces the damping reads
@@ -252,7 +297,7 @@ __device__ __forceinline__ void stage_metric(const TS<R>& S, const Blk& B, const
     S.AREA[l] = MT(area, j, i);
     S.RAREA[l] = MT(rarea, j, i);
   });
-  if (kStageW<R> && weights) {
+  if (weights) {
     for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
   }
@@ -344,12 +389,9 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // formed; the fluxes are written only after it
   R* const GX = FXO;
   R* const GY = FYO;
-  auto wxv = [&](int l, int j, int i) -> R {
-    if constexpr (kStageW<R>) return S.WX[l]; else return MT(wx, j, i);
-  };
-  auto wyv = [&](int l, int j, int i) -> R {
-    if constexpr (kStageW<R>) return S.WY[l]; else return MT(wy, j, i);
-  };
+  // the damped transports (d_sw, fv_tp_2d) have the weights staged
+  auto wxv = [&](int l, int, int) -> R { return S.WX[l]; };
+  auto wyv = [&](int l, int, int) -> R { return S.WY[l]; };
   MlpFrag F;
   if (LEARN) mlp_load(mlp, F);
   __syncthreads();  // Q (and the strips the corner turn reads) complete
@@ -377,7 +419,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // inner y-update in every column of the block and its halo
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * S.RDYd[l];
+    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
   if (cc) corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
   __syncthreads();
@@ -429,7 +471,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // inner x-update in every row of the block and its halo
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * S.RDXd[l];
+    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
   __syncthreads();
   // outer y-sweep of the x-updated field
@@ -492,14 +534,7 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
     S.CRY[l] = dt * vt * MT(siny, j, i) * MT(rdyc, j, i);
   });
   __syncthreads();
-  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
-    const int l = B.L(i, j);
-    S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
-  });
-  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
-    const int l = B.L(i, j);
-    S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
-  });
+  inner_denominators(S, B);
   (void)scaled;
   (void)fr;
 }
@@ -517,11 +552,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
   R* KE = DPN;  // 1/delp_new is dead once pt and w are written
   TS<R> S;
   S.CRX = sb + 10 * SA; S.XFX = sb + 11 * SA; S.CRY = sb + 12 * SA; S.YFX = sb + 13 * SA;
-  S.RDXd = sb + 14 * SA; S.RDYd = sb + 15 * SA; S.FY2 = sb + 16 * SA; S.FX2 = sb + 17 * SA;
-  S.QIJ = sb + 18 * SA; S.LAP = sb + 19 * SA; S.AL = sb + 20 * SA;
-  S.AREA = sb + 21 * SA; S.RAREA = sb + 22 * SA;
-  S.WX = kStageW<R> ? sb + 23 * SA : nullptr;
-  S.WY = kStageW<R> ? sb + 24 * SA : nullptr;
+  S.FY2 = sb + 14 * SA; S.FX2 = sb + 15 * SA; S.QIJ = sb + 16 * SA; S.LAP = sb + 17 * SA; S.AL = sb + 18 * SA;
+  assign_extra(S, sb + 19 * SA, SA, true);
   (void)SY;
 
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
@@ -1159,9 +1191,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
     *D1 = sb + 6 * SA;
   TS<R> S;
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
-  S.RDXd = sb + 11 * SA; S.RDYd = sb + 12 * SA; S.FY2 = sb + 13 * SA; S.FX2 = sb + 14 * SA;
-  S.QIJ = sb + 15 * SA; S.LAP = sb + 16 * SA; S.AL = sb + 17 * SA;
-  S.AREA = sb + 18 * SA; S.RAREA = sb + 19 * SA; S.WX = nullptr; S.WY = nullptr;  // no damping
+  S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA; S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA;
+  assign_extra(S, sb + 16 * SA, SA, false);  // no damping of tracers
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
   for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
   const Item it = a.items[wi / kz];
@@ -1192,14 +1223,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
       MFY[l] = a.amfy[q] * fr;
     });
     __syncthreads();
-    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
-      const int l = B.L(i, j);
-      S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
-    });
-    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
-      const int l = B.L(i, j);
-      S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
-    });
+    inner_denominators(S, B);
     for2(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
@@ -1249,11 +1273,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
   R *Q = sb, *MFX = sb + SA, *MFY = sb + 2 * SA, *FXO = sb + 3 * SA, *FYO = sb + 4 * SA;
   TS<R> S;
   S.CRX = sb + 5 * SA; S.XFX = sb + 6 * SA; S.CRY = sb + 7 * SA; S.YFX = sb + 8 * SA;
-  S.RDXd = sb + 9 * SA; S.RDYd = sb + 10 * SA; S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA;
-  S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA;
-  S.AREA = sb + 16 * SA; S.RAREA = sb + 17 * SA;
-  S.WX = kStageW<R> ? sb + 18 * SA : nullptr;
-  S.WY = kStageW<R> ? sb + 19 * SA : nullptr;
+  S.FY2 = sb + 9 * SA; S.FX2 = sb + 10 * SA; S.QIJ = sb + 11 * SA; S.LAP = sb + 12 * SA; S.AL = sb + 13 * SA;
+  assign_extra(S, sb + 14 * SA, SA, true);
   const bool mass = a.mfx != nullptr;
   const R damp = (R)a.damp;
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
@@ -1286,14 +1307,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
     });
     for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = a.q[o + G(j, i)]; });
     __syncthreads();
-    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
-      const int l = B.L(i, j);
-      S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
-    });
-    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
-      const int l = B.L(i, j);
-      S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
-    });
+    inner_denominators(S, B);
     transport<R, false>(Q, S, B, m, n, cc, mass ? MFX : (const R*)nullptr, mass ? MFY : (const R*)nullptr, damp,
                         (const R*)nullptr, FXO, FYO);
     for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.fx[o + G(j, i)] = FXO[B.L(i, j)]; });
@@ -1633,7 +1647,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     enqueue_halo_fields(c, F, st);
   }
   if (run(6)) {  // d_sw
-    const size_t sm = blk_smem(c, kStageW<R> ? 25 : 23);
+    const size_t sm = blk_smem(c, 19 + extra_arrays<R>(true));
     const bool learn = P.hord == 1 && P.mlp;
 #define FV3_DSW(X, Y)                                                                  \
   (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
@@ -1783,7 +1797,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   a.learn = P.hord == 1 && P.mlp != nullptr;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, 20);
+  const size_t sm = blk_smem(c, 16 + extra_arrays<R>(false));
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
@@ -1824,7 +1838,7 @@ static void fv_tp_2d_t(Ctx& c, const TpPtrs& p, cudaStream_t st) {
   a.damp = p.damp;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, kStageW<R> ? 20 : 18);
+  const size_t sm = blk_smem(c, 14 + extra_arrays<R>(true));
 #define FV3_TP(X, Y)                                                                   \
   set_smem(k_fv_tp_2d<R, X, Y>, sm);                                                   \
   k_fv_tp_2d<R, X, Y><<<work_grid(c, k_fv_tp_2d<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
