@@ -119,3 +119,30 @@ def test_async_converting_copies_match_staged():
         k = g.FIELD_KIND[nm]
         assert np.array_equal(g.get(ga[nm], k), g.get(gs[nm], k)), nm
         assert np.array_equal(hout[nm].numpy(), g.get(gs[nm], k)), nm
+
+
+def test_graph_cache_eviction_keeps_results():
+    """five states in turn (more than the four cached graphs): every step is
+    re-captured or replayed and each state ends where a lone run ends"""
+    import torch
+    from paper_2205_04148_gb300 import fv3
+    n, nz = 16, 3
+    prm = fv3.params(n_split=1)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz)
+    states = []
+    for k in range(5):
+        X = g.alloc_state(1)
+        g.load(X, seeded(True, n, nz, 40 + k, 1))
+        states.append(X)
+    for _ in range(2):
+        for X in states:
+            g.run_dyn(X, prm, 1)
+    torch.cuda.synchronize()
+    h = fv3.Grid(fv3.GRID_CUBED, n, nz)
+    for k, X in enumerate(states):
+        Y = h.alloc_state(1)
+        h.load(Y, seeded(True, n, nz, 40 + k, 1))
+        h.run_dyn(Y, prm, 2)
+        torch.cuda.synchronize()
+        for nm in NAMES + ("q0",):
+            assert np.array_equal(g.read(X, nm), h.read(Y, nm)), (k, nm)
