@@ -82,3 +82,54 @@ def test_zero_steps_and_limits():
         fv3.Grid(fv3.GRID_CUBED, 8, 1025)                       # levels beyond the limit
     with pytest.raises(fv3.Fv3Error, match="SHAPE"):
         fv3.Grid(fv3.GRID_CUBED, 64, 2, n_members=200)          # rows beyond one launch's grid
+
+
+def test_c192x80_fp32_substep(orc):
+    """The FP32-bulk bench configuration (C192 x 80, 32 x 8 blocks, four levels
+    per work item) against the FP64 oracle after one substep.  Bound: every
+    stored FP32 field is a few tens of roundings (2^-24 ~ 6e-8 each) away from
+    the FP64 values it is formed from, so within 1e-6 of the field's maximum
+    (measured: <= 2.2e-7); FP64 mass sums of the FP32 delp conserve to FP32
+    rounding of the sum of the fluxes."""
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+    n, nz = 192, 80
+    st = I.cubed_state(n, nz, seed=0, ntracers=0)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=fv3.FP32)
+    gs = g.alloc_state()
+    g.load(gs, st)
+    g.set_tiles(32, 8, 4)
+    g.set_persistent(False)
+    m0 = g.mass(gs)[0]
+    g.substep(gs)
+    s = orc.State(orc.Domain(True, n, nz))
+    s.load(st)
+    s.substep()
+    for f in FIELDS + ("delz",):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 1e-6, (f, e)
+    assert abs(g.mass(gs)[0] - m0) <= 1e-6 * m0
+
+
+def test_c96x80_fp64_all_options_step(orc):
+    """One remapping step of the C96 x 80 FP64 state with every physics option
+    the bench can switch on (closed substep, vertical remapping, divergence
+    damping, fourth-order C-grid winds), in the bench's launch configuration,
+    against the oracle on every element of every field."""
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+    n, nz, nq = 96, 80, 2
+    opts = dict(nh_full=1, remap=1, d2c_ord=4, d2_bg=0.02, dddmp=0.1)
+    st = I.cubed_state(n, nz, seed=0, ntracers=nq)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz)
+    gs = g.alloc_state(nq)
+    g.load(gs, st)
+    g.set_tiles(16, 16, 1)
+    g.set_persistent(True)
+    g.run_dyn(gs, fv3.params(n_split=6, **opts), 1)
+    s = orc.State(orc.Domain(True, n, nz), nq)
+    s.load(st)
+    s.run_dyn(orc.params(n_split=6, **opts), 1)
+    for f in FIELDS + ("delz", "q0", "q1"):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 10 * TOL64, (f, e)
