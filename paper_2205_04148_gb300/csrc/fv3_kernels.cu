@@ -518,7 +518,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
 // the level.
 template <typename R>
 __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R>& S, const Blk& B,
-                        const TM<R>& m, const Geo& g, R dt, bool scaled, R fr) {
+                        const TM<R>& m, const Geo& g, R dt) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   const int P = g.pitch;
   for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
@@ -535,8 +535,6 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
   });
   __syncthreads();
   inner_denominators(S, B);
-  (void)scaled;
-  (void)fr;
 }
 
 // ------------------------------------------------------------------------
@@ -587,7 +585,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
     for2(x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
     for2(x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     __syncthreads();
-    courant(uc, vc, V, U, S, B, m, g, dt, false, R(1));
+    courant(uc, vc, V, U, S, B, m, g, dt);
     if (a.status) {  // Courant-number guard on the block's own faces
       bool bad = false;
       for2(x0, x1, y0, y1, [&](int i, int j) {
