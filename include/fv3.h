@@ -284,9 +284,11 @@ fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work
 /* Accuracy check of the kernels' FP64 helpers (no counterpart in the paper;
  * for tests).  Device arrays of n doubles.  what = 0: out = 1/x by the
  * Newton-refined hardware reciprocal the transport and the column solve use;
- * what = 1: out = ln((x + y) / x), the log pressure ratio of the column solve
- * (atanh series for small y / (2x + y)).  FV3_ERR_ARG for an unknown `what`,
- * n < 0 or a NULL array; FV3_ERR_CUDA if the launch fails. */
+ * what = 1: out = ln((x + y) / x), the log pressure ratio (atanh series for
+ * small y / (2x + y)); what = 2: out = y / ln((x + y) / x), the layer pressure
+ * of the column solve's gas-law split (series of u / atanh(u) for small
+ * u = y / (2x + y)).  FV3_ERR_ARG for an unknown `what`, n < 0 or a NULL
+ * array; FV3_ERR_CUDA if the launch fails. */
 fv3_status fv3_math_check(int what, const double* x, const double* y, double* out, int n, fv3_stream stream);
 
 /* Block shape (bx x by cells) and level chunk of the horizontal kernels

@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     const double pen = pe + dpk;
     const double rdz = rcp(dzk);
     const double p = -dpk * rd_g * ptk * rdz;
-    const double ph = dpk * rcp(log_ratio(pen, pe, dpk));
+    const double ph = layer_mean_pressure(pen, pe, dpk);
     const double pp = p - ph;
     const double C = -cC * p * rdz;
     const double mm = k == 0 ? 0.5 * dpk * rgrav : 0.5 * (dpp + dpk) * rgrav;

@@ -88,4 +88,33 @@ __device__ __forceinline__ double log_ratio(double pen, double pe, double dp) {
   return 2.0 * u * s;
 }
 
+// dp / ln(pen / pe) for pen = pe + dp, pe > 0, pen > 0: the pressure that
+// splits the gas-law pressure of a layer from its hydrostatic part in the
+// column solve.  With u = dp / (pe + pen), ln(pen / pe) = 2 atanh(u), so
+// dp / ln(pen / pe) = (pe + pen) / 2 * u / atanh(u), and u / atanh(u) is the
+// reciprocal of the series sum_k v^k / (2k + 1) in v = u^2:
+//   1 - v/3 - 4v^2/45 - 44v^3/945 - 428v^4/14175 - 10196v^5/467775
+//     - 10719068v^6/638512875 - 25865068v^7/1915538625
+//     - 5472607916v^8/488462349375 - ...
+// (the coefficients of the series division, exact rationals).  For |u| <= 1/8
+// the terms through v^8 leave a truncation below 1e-18 relative: one
+// reciprocal and a polynomial instead of the logarithm's series and a second
+// reciprocal.  The thin upper layers (larger u) divide by the library log.
+__device__ __forceinline__ double layer_mean_pressure(double pen, double pe, double dp) {
+  const double sum = pe + pen;
+  const double u = dp * rcp(sum);
+  if (fabs(u) > 0.125) return dp / log(pen / pe);
+  const double v = u * u;
+  double r = -5472607916.0 / 488462349375.0;
+  r = fma(r, v, -25865068.0 / 1915538625.0);
+  r = fma(r, v, -10719068.0 / 638512875.0);
+  r = fma(r, v, -10196.0 / 467775.0);
+  r = fma(r, v, -428.0 / 14175.0);
+  r = fma(r, v, -44.0 / 945.0);
+  r = fma(r, v, -4.0 / 45.0);
+  r = fma(r, v, -1.0 / 3.0);
+  r = fma(r, v, 1.0);
+  return 0.5 * sum * r;
+}
+
 }  // namespace fv3

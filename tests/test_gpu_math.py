@@ -45,3 +45,29 @@ def test_log_ratio_matches_log1p():
     # log1p of a correctly rounded quotient: its own error is 1 ulp of dp/pe
     tol = 4 * np.finfo(float).eps * np.abs(want) + np.spacing(dp / pe)
     assert (np.abs(got - want) <= tol).all(), np.max(np.abs(got - want) / tol)
+
+
+def test_layer_mean_pressure_matches_quotient():
+    """dp / ln(pen / pe) of the column solve: the series branch (|u| <= 1/8)
+    and the logarithm branch against the quotient formed from log1p in numpy
+    (each side a few roundings from the exact value)"""
+    rng = np.random.default_rng(3)
+    pe = 10.0 ** rng.uniform(2, 5, 200000)
+    dp = pe * 10.0 ** rng.uniform(-4, 1, 200000)
+    got = run(2, pe, dp)
+    want = dp / np.log1p(dp / pe)
+    u = dp / (2 * pe + dp)
+    series = u <= 0.125
+    assert series.any() and (~series).any()
+    eps = np.finfo(float).eps
+    # series branch: the rounding of u, the polynomial and the final products;
+    # log branch: also the rounding of pen / pe, amplified by 1 / ln(pen / pe)
+    tol = np.where(series, 8 * eps, 16 * eps) * np.abs(want)
+    assert (np.abs(got - want) <= tol).all(), np.max(np.abs(got - want) / tol)
+    # a vanishing layer: pe + dp/2 - dp^2 / (12 pe) + ..., the quadratic term
+    # far below an ulp for these sizes
+    pe = np.full(1000, 5.0e4)
+    dp = 10.0 ** np.linspace(-8, -4, 1000)
+    got = run(2, pe, dp)
+    assert np.allclose(got, pe + 0.5 * dp, rtol=4e-16, atol=0)
+
