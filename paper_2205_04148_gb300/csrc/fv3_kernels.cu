@@ -817,6 +817,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
 template <typename R>
 __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int BYc) {
   __shared__ R GZ[256];
+  __shared__ R SXF[256], SYF[256];  // twice the level-mean flux of each thread's west and south face
   const Item it = a.items[blockIdx.x];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch, nz = g.nz;
@@ -826,59 +827,53 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
   const bool ring = (i == x0 - 1 || i == x1) , ringy = (j == y0 - 1 || j == y1);
   const bool valid = i >= x0 - 1 && i <= x1 && j >= y0 - 1 && j <= y1 && !(ring && ringy);
   const bool inner = i >= x0 && i < x1 && j >= y0 && j < y1;
+  // the thread forms the flux of its west x-face (faces x0 .. x1 of the
+  // block's rows) and of its south y-face (faces y0 .. y1 of its columns);
+  // a cell reads its east and north faces from the neighbours
+  const bool fxo = i >= x0 && i <= x1 && j >= y0 && j < y1;
+  const bool fyo = j >= y0 && j <= y1 && i >= x0 && i < x1;
   const TM<R> m = tile_metric(a.M, g, it.t);
   const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min, rgrav = (R)(1.0 / a.P.grav);
   const long long q = (long long)j * P + i;
   R gzr = R(0), gzn_below = R(0);
   const int l = ty * TXW + tx;
-  // the four faces of the cell: x-faces i, i + 1 and y-faces j, j + 1
-  const long long fq[4] = {q, q + 1, q, q + P};
   const int lo[4] = {l - 1, l, l - TXW, l};
   const int hi[4] = {l, l + 1, l, l + TXW};
-  auto face = [&](int K, int f) -> R {
-    const long long o = fld0(g, g.off3, nz, it.t, K) + fq[f];
-    return f < 2 ? a.fx1[o] : a.fy1[o];
-  };
-  // the level loop is sequential: the loads run ahead of it (delz one level,
-  // the fluxes two levels), so their latency overlaps the level before
-  const R ar = inner ? MT(area, j, i) : R(1);
-  R fb[4], fa[4], fn[4];  // fluxes at levels K, K - 1, K - 2
+  auto fx = [&](int K) { return a.fx1[fld0(g, g.off3, nz, it.t, K) + q]; };
+  auto fy = [&](int K) { return a.fy1[fld0(g, g.off3, nz, it.t, K) + q]; };
+  // The level loop is sequential: the loads run ahead of it (delz one level,
+  // the fluxes two levels), so their latency overlaps the level before.  The
+  // update is written with twice the level-mean fluxes S = fx(K-1) + fx(K)
+  // (2 fx(0) at the top) and twice the area: numerator and denominator both
+  // scale by exactly 2, so the quotient is the one of the mean fluxes.
+  const R ar2 = inner ? R(2) * MT(area, j, i) : R(1);
+  R xb = R(0), xa = R(0), xn = R(0), yb = R(0), ya = R(0), yn = R(0);  // levels K, K - 1, K - 2
   R dzk = valid ? a.delz[fld0(g, g.off3, nz, it.t, nz - 1) + q] : R(0);
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    fb[f] = inner ? face(nz - 1, f) : R(0);
-    fa[f] = inner ? face(nz - 2, f) : R(0);  // nz >= 2
-    fn[f] = R(0);
-  }
+  if (fxo) { xb = fx(nz - 1); xa = fx(nz - 2); }  // nz >= 2
+  if (fyo) { yb = fy(nz - 1); ya = fy(nz - 2); }
   for (int K = nz - 1; K >= 0; --K) {
     const long long o = fld0(g, g.off3, nz, it.t, K);
     R dzn = R(0);
     if (valid && K > 0) dzn = a.delz[o - g.plane + q];
-    if (inner && K >= 2) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) fn[f] = face(K - 2, f);
-    }
+    if (fxo && K >= 2) xn = fx(K - 2);
+    if (fyo && K >= 2) yn = fy(K - 2);
     if (valid) {
       gzr = gzr - grav * dzk;
       GZ[l] = gzr;
     }
+    if (fxo) SXF[l] = K == 0 ? R(2) * xb : xa + xb;
+    if (fyo) SYF[l] = K == 0 ? R(2) * yb : ya + yb;
     __syncthreads();
     if (inner) {
-      R F[4], Gf[4];
+      const R S[4] = {SXF[l], SXF[l + 1], SYF[l], SYF[l + TXW]};
+      R Gf[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        F[f] = K == 0 ? fb[f] : R(0.5) * (fa[f] + fb[f]);
-        Gf[f] = F[f] * (F[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
-      }
-      const R gzn = (GZ[l] * ar + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar + F[0] - F[1] + F[2] - F[3]);
+      for (int f = 0; f < 4; ++f) Gf[f] = S[f] * (S[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
+      const R gzn = (GZ[l] * ar2 + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar2 + S[0] - S[1] + S[2] - S[3]);
       a.delzc[o + q] = fmin((gzn_below - gzn) * rgrav, -dzmin);
       gzn_below = gzn;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        fb[f] = fa[f];
-        fa[f] = fn[f];
-      }
     }
+    xb = xa; xa = xn; yb = ya; ya = yn;
     dzk = dzn;
     __syncthreads();
   }
