@@ -360,10 +360,11 @@ def ours(a):
 
     # --- end to end through the C-ABI with host buffers ------------------
     # Every step imports its inputs from page-locked host memory and exports
-    # its result (every prognostic field but delz) to host memory.  Two states
-    # alternate: while one advances on the compute stream, the previous
-    # step's result leaves the other and the next step's inputs enter it on a
-    # copy stream (fv3_import / fv3_export, asynchronous host mode).
+    # its result (every prognostic field but delz) to host memory.  Three
+    # device states take turns: while one advances on the compute stream, the
+    # previous step's result leaves its state and the inputs of the step after
+    # next enter it on a copy stream (fv3_import / fv3_export, asynchronous
+    # host mode), so a copy has two steps' time to arrive.
     e2e = None
     if not a.no_e2e:
         kinds = dict(g.FIELD_KIND)
@@ -376,26 +377,24 @@ def ours(a):
         def field(state, nm):
             return state[nm] if not nm.startswith("q") else state["q"][int(nm[1:])]
 
-        states = [gs, g.alloc_state(nq=a.nq)]
-        hin, hout = [], []
-        for _ in range(2):
-            d = {}
-            for nm in names:
-                t = g.host_buffer(kind(nm))
-                t.numpy()[...] = st[nm] if not nm.startswith("q") else st["q"][int(nm[1:])]
-                d[nm] = t
-            hin.append(d)
-            hout.append({nm: g.host_buffer(kind(nm)) for nm in outs})
-        h2d = sum(hin[0][nm].numel() * hin[0][nm].element_size() for nm in names)
+        NS = 3  # device states in flight: a step's inputs arrive two steps ahead
+        states = [gs] + [g.alloc_state(nq=a.nq) for _ in range(NS - 1)]
+        hin = {}  # every step's inputs: the same page-locked host arrays
+        for nm in names:
+            t = g.host_buffer(kind(nm))
+            t.numpy()[...] = st[nm] if not nm.startswith("q") else st["q"][int(nm[1:])]
+            hin[nm] = t
+        hout = [{nm: g.host_buffer(kind(nm)) for nm in outs} for _ in range(NS)]
+        h2d = sum(hin[nm].numel() * hin[nm].element_size() for nm in names)
         d2h = sum(hout[0][nm].numel() * hout[0][nm].element_size() for nm in outs)
         cs = torch.cuda.Stream()
         ps = torch.cuda.current_stream()
-        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-        ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_in = [torch.cuda.Event() for _ in range(NS)]
+        ev_done = [torch.cuda.Event() for _ in range(NS)]
 
         def stage_in(x):
             for nm in names:
-                g.put_async(field(states[x], nm), kind(nm), hin[x][nm], stream=cs.cuda_stream)
+                g.put_async(field(states[x], nm), kind(nm), hin[nm], stream=cs.cuda_stream)
             ev_in[x].record(cs)
 
         def stage_out(x):
@@ -415,19 +414,19 @@ def ours(a):
             ev_done[x].record(ps)
 
         def pipeline(k):
-            stage_in(0)
+            for i in range(min(NS - 1, k)):
+                stage_in(i % NS)
             for i in range(k):
-                x = i % 2
-                advance(x)
+                advance(i % NS)
                 if i >= 1:
-                    stage_out(1 - x)  # result of step i - 1
-                if i + 1 < k:
-                    stage_in(1 - x)   # inputs of step i + 1
-            stage_out((k - 1) % 2)
+                    stage_out((i - 1) % NS)        # result of step i - 1
+                if i + NS - 1 < k:
+                    stage_in((i + NS - 1) % NS)    # inputs of step i + NS - 1, same state
+            stage_out((k - 1) % NS)
             cs.synchronize()
             ps.synchronize()
 
-        pipeline(2)
+        pipeline(NS + 1)  # every state's graph captured outside the timed region
         # the copies of one step alone (not overlapped), for the record
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -455,7 +454,8 @@ def ours(a):
         clk_e2e = clocks_e2e.stop()
         e2e = {"value": ws * a.n_split * cells / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3,
-               "io": "two states alternate: one advances while the other's result and next inputs are copied",
+               "io": "three device states in turn: while one advances, the result of the previous step "
+                     "leaves and the inputs of the step after next arrive on a copy stream",
                "h2d_ms_alone": t_in * 1e3, "d2h_ms_alone": t_out * 1e3, "clocks": clk_e2e,
                "repeats_ms_per_step": [r * 1e3 for r in reps], "steps_per_repeat": ke,
                "substeps_ms_per_step": busy}
