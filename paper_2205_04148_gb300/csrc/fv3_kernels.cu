@@ -244,6 +244,12 @@ struct TS {
 template <typename R>
 constexpr bool kStoreRD = sizeof(R) == 8;
 
+// the plain FP64 tracer kernel transports its tracers in pairs (six more
+// shared-memory arrays: two FP64 blocks still fit an SM; four FP32 ones
+// would not)
+template <typename R, bool LEARN>
+constexpr bool kTracerPair = sizeof(R) == 8 && !LEARN;
+
 // 1 / (area + the two area fluxes) of the y- and x-inner updates at l
 template <typename R>
 __device__ __forceinline__ R inner_rdy(const TS<R>& S, int l, int SX) {
@@ -276,7 +282,7 @@ __device__ __forceinline__ void inner_denominators(const TS<R>& S, const Blk& B)
 // shared-memory arrays after the base ones of a kernel: area, 1/area, the
 // stored denominators (kStoreRD) and the damping weights (if `weights`)
 template <typename R>
-constexpr int extra_arrays(bool weights) {
+__host__ __device__ constexpr int extra_arrays(bool weights) {
   return 2 + (kStoreRD<R> ? 2 : 0) + (weights ? 2 : 0);
 }
 template <typename R>
@@ -511,6 +517,115 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     });
     __syncthreads();
   }
+}
+
+// Two scalars transported together (tracer_2d, no damping, plain PPM): the
+// steps of transport() above, each phase doing both fields, so that every
+// barrier is shared by twice the FP64 work.  Per field: the tile Q, the edge,
+// face and inner-update arrays and the output fluxes.
+template <typename R>
+struct TF {
+  R *Q, *AL, *FY2, *FX2, *QIJ, *FXO, *FYO;
+};
+
+template <typename R>
+__device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int n, bool cc, const R* mfx,
+                               const R* mfy) {
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  __syncthreads();  // both tiles complete
+  if (cc) {
+    corner_roles(F[0].Q, B, n, 1);
+    corner_roles(F[1].Q, B, n, 1);
+  }
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R* Q = F[f].Q;
+      F[f].AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
+    }
+  });
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) F[f].FY2[l] = ppm_face_al(F[f].Q, F[f].AL, l, SX, S.CRY[l]);
+  });
+  __syncthreads();
+  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R rd = inner_rdy(S, l, SX);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FY2[l] * S.YFX[l] - F[f].FY2[l + SX] * S.YFX[l + SX]) * rd;
+  });
+  if (cc) {  // touches only missing-quadrant cells
+    corner_roles(F[0].Q, B, n, 0);
+    corner_roles(F[1].Q, B, n, 0);
+  }
+  __syncthreads();
+  for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R* Q = F[f].Q;
+      F[f].AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
+    }
+  });
+  __syncthreads();
+  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) F[f].FX2[l] = ppm_face_al(F[f].Q, F[f].AL, l, 1, S.CRX[l]);
+  });
+  __syncthreads();
+  for2(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R* Q = F[f].QIJ;
+      F[f].AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
+    }
+  });
+  __syncthreads();
+  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R w = mfx[l];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R v = ppm_face_al(F[f].QIJ, F[f].AL, l, 1, S.CRX[l]);
+      F[f].FXO[l] = R(0.5) * (v + F[f].FX2[l]) * w;
+    }
+  });
+  __syncthreads();
+  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R rd = inner_rdx(S, l);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FX2[l] * S.XFX[l] - F[f].FX2[l + 1] * S.XFX[l + 1]) * rd;
+  });
+  __syncthreads();
+  for2(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+    const int l = B.L(i, j);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R* Q = F[f].QIJ;
+      F[f].AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
+    }
+  });
+  __syncthreads();
+  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R w = mfy[l];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const R v = ppm_face_al(F[f].QIJ, F[f].AL, l, SX, S.CRY[l]);
+      F[f].FYO[l] = R(0.5) * (v + F[f].FY2[l]) * w;
+    }
+  });
+  __syncthreads();
 }
 
 // Courant numbers and area fluxes (reading R11) into shared memory, plus the
@@ -1186,6 +1301,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
   S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA; S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA;
   assign_extra(S, sb + 16 * SA, SA, false);  // no damping of tracers
+  // the plain FP64 kernel transports tracers in pairs (kTracerPair): the
+  // second field's arrays follow, its tile in the unused Laplacian array
+  constexpr bool PAIR = kTracerPair<R, LEARN>;
+  R* const sb2 = sb + (16 + extra_arrays<R>(false)) * SA;
+  const TF<R> TFP[2] = {{Q, S.AL, S.FY2, S.FX2, S.QIJ, FXO, FYO},
+                        {S.LAP, sb2, sb2 + SA, sb2 + 2 * SA, sb2 + 3 * SA, sb2 + 4 * SA, sb2 + 5 * SA}};
   const int kz = (a.geo[0].nz + kchunk - 1) / kchunk;
   for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
   const Item it = a.items[wi / kz];
@@ -1230,6 +1351,32 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
     // no registers to spare)
     constexpr int NPRE = LEARN ? 1 : ((BX + 6) * (BY + 6) + 255) / 256;
     R pre[NPRE];
+    if constexpr (PAIR) {
+      R pre2[NPRE];
+      tile_fetch<NPRE>(a.q[0] + o, pre, B, P);
+      if (a.nq > 1) tile_fetch<NPRE>(a.q[1] + o, pre2, B, P);
+      for (int tq = 0; tq < a.nq; tq += 2) {
+        const bool two = tq + 1 < a.nq;
+        __syncthreads();
+        tile_put<NPRE>(TFP[0].Q, pre, B);
+        if (two) tile_put<NPRE>(TFP[1].Q, pre2, B);
+        if (tq + 2 < a.nq) tile_fetch<NPRE>(a.q[tq + 2] + o, pre, B, P);
+        if (tq + 3 < a.nq) tile_fetch<NPRE>(a.q[tq + 3] + o, pre2, B, P);
+        if (two)
+          transport_pair(TFP, S, B, n, cc, MFX, MFY);
+        else
+          transport<R, false>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+        for (int f = 0; f < (two ? 2 : 1); ++f) {
+          R* qo = a.q_o[tq + f] + o;
+          const TF<R>& T = TFP[f];
+          for2(x0, x1, y0, y1, [&](int i, int j) {
+            const int l = B.L(i, j);
+            qo[G(j, i)] =
+                (T.Q[l] * D0[l] + (T.FXO[l] - T.FXO[l + 1] + T.FYO[l] - T.FYO[l + SX]) * S.RAREA[l]) * D1[l];
+          });
+        }
+      }
+    } else {
     if (!LEARN) tile_fetch<NPRE>(a.q[0] + o, pre, B, P);
     for (int tq = 0; tq < a.nq; ++tq) {
       __syncthreads();
@@ -1246,6 +1393,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
         const int l = B.L(i, j);
         qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * D1[l];
       });
+    }
     }
     __syncthreads();
   }
@@ -1790,7 +1938,8 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   a.learn = P.hord == 1 && P.mlp != nullptr;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, 16 + extra_arrays<R>(false));
+  const bool pair = a.learn ? kTracerPair<R, true> : kTracerPair<R, false>;
+  const size_t sm = blk_smem(c, 16 + extra_arrays<R>(false) + (pair ? 6 : 0));
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
