@@ -395,14 +395,26 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   // formed; the fluxes are written only after it
   R* const GX = FXO;
   R* const GY = FYO;
-  // the damped transports (d_sw, fv_tp_2d) have the weights staged
-  auto wxv = [&](int l, int, int) -> R { return S.WX[l]; };
-  auto wyv = [&](int l, int, int) -> R { return S.WY[l]; };
+  // the damped transports (d_sw, fv_tp_2d) have the weights wx, wy staged
   MlpFrag F;
   if (LEARN) mlp_load(mlp, F);
+  // del-4 damping fluxes at x-face / y-face l, added where the fluxes are
+  // formed (the Laplacian is complete by then)
+  auto damp_x = [&](int l) -> R {
+    R f = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
+    if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
+    return f;
+  };
+  auto damp_y = [&](int l) -> R {
+    R f = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
+    if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
+    return f;
+  };
   __syncthreads();  // Q (and the strips the corner turn reads) complete
-  if (cc) corner_roles(Q, B, n, 1);
-  __syncthreads();
+  if (cc) {  // blocks at a cube corner: the missing quadrant for the y-sweep
+    corner_roles(Q, B, n, 1);
+    __syncthreads();
+  }
   // y-sweep of the plain field (y-role corners): edges, then faces
   for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
@@ -411,7 +423,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
-      GY[l] = (Q[l] - Q[l - SX]) * wyv(l, j, i);
+      GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
   __syncthreads();
   if (LEARN)
@@ -427,8 +439,12 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
-  if (cc) corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
-  __syncthreads();
+  // the x-edges below read Q and write AL and GX, which the inner y-update
+  // does not touch: a barrier only where the x-role corners rewrite Q
+  if (cc) {
+    corner_roles(Q, B, n, 0);  // touches only missing-quadrant cells
+    __syncthreads();
+  }
   // x-sweep of the plain field (x-role corners)
   for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
@@ -437,7 +453,7 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
   if (dmp)
     for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      GX[l] = (Q[l] - Q[l - 1]) * wxv(l, j, i);
+      GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
   __syncthreads();
   if (LEARN)
@@ -464,13 +480,15 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     __syncthreads();
     for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      FXO[l] = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+      const R fl = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+      FXO[l] = dmp ? fl + damp_x(l) : fl;
     });
   } else {
     for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
-      FXO[l] = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+      const R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+      FXO[l] = dmp ? fl + damp_x(l) : fl;
     });
   }
   __syncthreads();
@@ -491,32 +509,18 @@ __device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, in
     __syncthreads();
     for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      FYO[l] = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+      const R fl = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+      FYO[l] = dmp ? fl + damp_y(l) : fl;
     });
   } else {
     for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
-      FYO[l] = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+      const R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+      FYO[l] = dmp ? fl + damp_y(l) : fl;
     });
   }
-  if (dmp)
-    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
-      const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - 1]) * wxv(l, j, i);
-      if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
-      FXO[l] = FXO[l] + f;
-    });
   __syncthreads();
-  if (dmp) {
-    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
-      const int l = B.L(i, j);
-      R f = damp * (S.LAP[l] - S.LAP[l - SX]) * wyv(l, j, i);
-      if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
-      FYO[l] = FYO[l] + f;
-    });
-    __syncthreads();
-  }
 }
 
 // Two scalars transported together (tracer_2d, no damping, plain PPM): the
@@ -536,8 +540,8 @@ __device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int
   if (cc) {
     corner_roles(F[0].Q, B, n, 1);
     corner_roles(F[1].Q, B, n, 1);
+    __syncthreads();
   }
-  __syncthreads();
   for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
@@ -560,11 +564,11 @@ __device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int
     for (int f = 0; f < 2; ++f)
       F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FY2[l] * S.YFX[l] - F[f].FY2[l + SX] * S.YFX[l + SX]) * rd;
   });
-  if (cc) {  // touches only missing-quadrant cells
+  if (cc) {  // touches only missing-quadrant cells; else the x-edges need no barrier
     corner_roles(F[0].Q, B, n, 0);
     corner_roles(F[1].Q, B, n, 0);
+    __syncthreads();
   }
-  __syncthreads();
   for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
