@@ -59,7 +59,7 @@ FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
 # profiles/k_d_sw_fp32_c192x16.md: C192 x 16, FP32, 32 x 8 blocks, four levels
 # per work item); scaled by the cells of the timed launch (the traffic grows in
 # proportion to the work items).  Other configurations report null.
-DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 197.8, ("f32", 32, 8, 4, False): 103.5}
+DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 197.9, ("f32", 32, 8, 4, False): 103.7}
 
 
 def parse():
