@@ -167,7 +167,10 @@ fv3_status fv3_get_layout(const fv3_ctx* ctx, int member, fv3_layout* out);
  *     event, whatever stream that ran on), and is allocated on first use with
  *     room for any field of the context.  Lets a caller overlap the I/O of
  *     one state with the substeps of another on a second stream.
- * dense_is_double: dense elements are double (else float). */
+ *   Any other value: FV3_ERR_ARG.
+ * dense_is_double: dense elements are double (else float).
+ * Errors: FV3_ERR_ARG (NULL buffer, bad kind or member), FV3_ERR_ALIGN (field
+ * not 128-byte aligned), FV3_ERR_CUDA (a copy or launch failed). */
 enum { FV3_DENSE_DEVICE = 0, FV3_DENSE_HOST = 1, FV3_DENSE_HOST_ASYNC = 2 };
 fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, int dense_is_host, int dense_is_double,
                       int member, fv3_stream stream);
