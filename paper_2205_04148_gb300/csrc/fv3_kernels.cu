@@ -1025,8 +1025,9 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
   const double dt = FULL ? a.P.dt : 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
   const double kappa = a.P.rdgas / a.P.cp_air, gama = 1.0 / (1.0 - kappa);
   // the loop-invariant quotients once; per level the reciprocals of the
-  // thickness, the interface pressure, the log ratio and the pivot (FP64 here
-  // is 2 lanes per SM per clock, and a quotient costs several of them)
+  // thickness, of the interface pressure sum (inside layer_mean_pressure) and
+  // of the pivot (FP64 here is 2 lanes per SM per clock, and a quotient costs
+  // several of them)
   const double rgrav = 1.0 / grav, rdt = 1.0 / dt, cC = aimp * dt * gama, rd_g = rd / grav;
   const long long q = (long long)r.j * g.pitch + i;
   double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;

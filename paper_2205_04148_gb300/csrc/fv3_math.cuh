@@ -68,7 +68,9 @@ __device__ __forceinline__ double rcp<double>(double x) {
   return fma(r, e, r);
 }
 
-// ln(pen / pe) for pen = pe + dp, pe > 0, pen > 0.  With u = dp / (pe + pen),
+// ln(pen / pe) for pen = pe + dp, pe > 0, pen > 0 (kept for the accuracy
+// check of fv3_math_check; the column solve uses layer_mean_pressure below).
+// With u = dp / (pe + pen),
 // pen / pe = (1 + u) / (1 - u) and ln(pen / pe) = 2 atanh(u) =
 // 2 (u + u^3/3 + u^5/5 + ...), the Taylor series of atanh.  For |u| <= 1/8
 // the terms through u^15 leave a truncation error below 2^-52 relative; the
