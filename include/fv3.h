@@ -177,6 +177,33 @@ fv3_status fv3_import(fv3_ctx* ctx, int kind, void* field, const void* dense, in
 fv3_status fv3_export(fv3_ctx* ctx, int kind, const void* field, void* dense, int dense_is_host, int dense_is_double,
                       int member, fv3_stream stream);
 
+/* One entry of a halo plan: the slot at element offset `dst` of a level
+ * plane of tile `dst_tile` takes the value at offset `src` of tile `src_tile`
+ * (same level) times `sign`; sign 0: no value exists (a cube-corner slot, set
+ * to NaN).  Offsets index one padded plane (`pitch` elements per row, see
+ * fv3_layout).  Vector plans: flags bit 0 set when the slot is in the y-face
+ * array (u of the D-grid pair, vc of the C-grid pair), bit 1 when the source
+ * is. */
+typedef struct {
+  int32_t dst, src, dst_tile, src_tile, sign, flags;
+} fv3_halo_entry;
+enum { FV3_PLAN_CELL = 0, FV3_PLAN_DGRID = 2, FV3_PLAN_CGRID = 3 };
+
+/* The halo plan of kind FV3_PLAN_CELL (scalars, halo 3), FV3_PLAN_DGRID (the
+ * D-grid winds: v on x-faces, u on y-faces) or FV3_PLAN_CGRID (the C-grid
+ * winds: uc on x-faces, vc on y-faces) of member `member` of the grid `desc`:
+ * the plan fv3_halo_fill applies (Section V-C), built on the host without a
+ * device.  For a caller that places the tiles of a member on different
+ * devices, every entry whose src_tile lives elsewhere is a value to receive
+ * (the paper's halo exchange between ranks).  Writes min(total, cap) entries
+ * to `out` (which may be NULL when cap is 0), *total = the number of entries,
+ * and, if `layout` is not NULL, the member's plane geometry for the
+ * descriptor's precision (its offsets are those of fv3_get_layout).  Errors:
+ * as fv3_init_grid for the descriptor (FV3_ERR_ARG, FV3_ERR_SHAPE);
+ * FV3_ERR_ARG for a bad member, kind or NULL total. */
+fv3_status fv3_halo_plan(const fv3_grid_desc* desc, int member, int kind, fv3_halo_entry* out, size_t cap,
+                         size_t* total, fv3_layout* layout);
+
 /* Fill the halos (strips of 3, owner copies of shared tile-edge faces, cube
  * corner slots) of the fields selected by `field_mask` (FV3_HALO_*), all
  * members: Section V-C, on the device. */

@@ -169,20 +169,45 @@ size_t dense_count(const Geo& g, int kind, int nlev) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_stream stream) {
-  (void)stream;
-  if (!out || !d) return FV3_ERR_ARG;
-  *out = nullptr;
+namespace {
+
+// descriptor checks shared by fv3_init_grid and fv3_halo_plan; npx per member
+fv3_status check_desc(const fv3_grid_desc* d, std::vector<int>& npx) {
   if (d->grid_type != FV3_GRID_PERIODIC && d->grid_type != FV3_GRID_CUBED) return FV3_ERR_ARG;
   if (d->precision != FV3_FP64 && d->precision != FV3_FP32) return FV3_ERR_ARG;
   if (d->n_members < 1 || d->n_members > 4096 || d->npz < 2 || d->npz > 1024) return FV3_ERR_SHAPE;
   if (d->grid_type == FV3_GRID_PERIODIC && !(d->dx > 0)) return FV3_ERR_ARG;
   if (d->grid_type == FV3_GRID_CUBED && (!(d->radius > 0) || !std::isfinite(d->omega))) return FV3_ERR_ARG;
-  std::vector<int> npx(d->n_members);
+  npx.assign(d->n_members, 0);
   for (int m = 0; m < d->n_members; ++m) {
     npx[m] = d->member_npx ? d->member_npx[m] : d->npx;
     if (npx[m] < 8 || npx[m] > 4096) return FV3_ERR_SHAPE;
   }
+  return FV3_OK;
+}
+
+// plane geometry of one member (offsets left to the caller)
+void plane_geo(int n, int nz, int nt, bool cubed, int esize, Geo& g) {
+  const int align = 128 / esize;  // elements per 128 bytes
+  g.n = n;
+  g.nz = nz;
+  g.nt = nt;
+  g.cubed = cubed ? 1 : 0;
+  g.ox = align;  // first interior element of a row on a 128-byte boundary
+  g.pitch = ((g.ox + g.n + 1 + HALO) + align - 1) / align * align;
+  g.rows = g.n + 1 + 2 * HALO;
+  g.plane = (long long)g.rows * g.pitch;
+}
+
+}  // namespace
+
+extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_stream stream) {
+  (void)stream;
+  if (!out || !d) return FV3_ERR_ARG;
+  *out = nullptr;
+  std::vector<int> npx;
+  const fv3_status dr = check_desc(d, npx);
+  if (dr != FV3_OK) return dr;
   fv3_ctx* x = new fv3_ctx();
   Ctx& c = x->c;
   c.spec.cubed = d->grid_type == FV3_GRID_CUBED;
@@ -202,21 +227,13 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
     c.BX = 32; c.BY = 8; c.kchunk = std::min(4, d->npz); c.persistent = 0;
   }
   const int nt = c.spec.cubed ? 6 : 1;
-  const int align = 128 / c.esize;  // elements per 128 bytes
   long long o3 = 0, oi = 0, o2 = 0, oc = 0;
   c.geo.resize(c.nmem);
   std::vector<HostMetric> HM(c.nmem);
   std::vector<Plans> PL(c.nmem);
   for (int m = 0; m < c.nmem; ++m) {
     Geo& g = c.geo[m];
-    g.n = npx[m];
-    g.nz = c.nz;
-    g.nt = nt;
-    g.cubed = c.spec.cubed ? 1 : 0;
-    g.ox = align;  // first interior element of a row on a 128-byte boundary
-    g.pitch = ((g.ox + g.n + 1 + HALO) + align - 1) / align * align;
-    g.rows = g.n + 1 + 2 * HALO;
-    g.plane = (long long)g.rows * g.pitch;
+    plane_geo(npx[m], c.nz, nt, c.spec.cubed, c.esize, g);
     g.off3 = o3;
     g.offi = oi;
     g.off2 = o2;
@@ -470,6 +487,54 @@ static fv3_status do_pack(fv3_ctx* x, int kind, void* field, void* dense, int ho
   if (host && dir == 1) {
     CK(x, cudaMemcpyAsync(dense, dd, bytes, cudaMemcpyDeviceToHost, st));
     CK(x, cudaStreamSynchronize(st));
+  }
+  return FV3_OK;
+}
+
+extern "C" fv3_status fv3_halo_plan(const fv3_grid_desc* d, int member, int kind, fv3_halo_entry* out, size_t cap,
+                                    size_t* total, fv3_layout* layout) {
+  if (!d || !total) return FV3_ERR_ARG;
+  std::vector<int> npx;
+  const fv3_status dr = check_desc(d, npx);
+  if (dr != FV3_OK) return dr;
+  if (member < 0 || member >= d->n_members) return FV3_ERR_ARG;
+  if (kind != FV3_PLAN_CELL && kind != FV3_PLAN_DGRID && kind != FV3_PLAN_CGRID) return FV3_ERR_ARG;
+  if (cap > 0 && !out) return FV3_ERR_ARG;
+  GridSpec spec{};
+  spec.cubed = d->grid_type == FV3_GRID_CUBED;
+  spec.dx = d->dx;
+  spec.radius = d->radius;
+  spec.omega = d->omega;
+  const int nt = spec.cubed ? 6 : 1, esize = d->precision == FV3_FP64 ? 8 : 4;
+  long long o3 = 0, oi = 0;  // member offsets, as fv3_init_grid lays them out
+  Geo g{};
+  for (int m = 0; m <= member; ++m) {
+    plane_geo(npx[m], d->npz, nt, spec.cubed, esize, g);
+    if (m < member) {
+      o3 += (long long)nt * d->npz * g.plane;
+      oi += (long long)nt * (d->npz + 1) * g.plane;
+    }
+  }
+  g.off3 = o3;
+  g.offi = oi;
+  HostMetric M;
+  Plans P;
+  build_metric(spec, member, g, M, P);
+  const PlanKind pk = kind == FV3_PLAN_CELL ? K_CELL3 : kind == FV3_PLAN_DGRID ? K_DGRID : K_CGRID;
+  const std::vector<HaloEntry>& E = P.p[pk];
+  *total = E.size();
+  for (size_t e = 0; e < E.size() && e < cap; ++e) {
+    out[e].dst = E[e].dst;
+    out[e].src = E[e].src;
+    out[e].dst_tile = E[e].dt;
+    out[e].src_tile = E[e].st;
+    out[e].sign = E[e].sign;
+    out[e].flags = E[e].flags;
+  }
+  if (layout) {
+    layout->n = g.n; layout->nz = g.nz; layout->ntiles = g.nt;
+    layout->pitch = g.pitch; layout->rows = g.rows; layout->ox = g.ox;
+    layout->plane = g.plane; layout->offset3 = g.off3; layout->offseti = g.offi;
   }
   return FV3_OK;
 }

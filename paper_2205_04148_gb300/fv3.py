@@ -33,7 +33,13 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
            "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap",
-           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite")
+           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite", "fv3_halo_plan")
+PLAN_CELL, PLAN_DGRID, PLAN_CGRID = 0, 2, 3
+
+
+class HaloEntry(C.Structure):
+    _fields_ = [("dst", C.c_int32), ("src", C.c_int32), ("dst_tile", C.c_int32), ("src_tile", C.c_int32),
+                ("sign", C.c_int32), ("flags", C.c_int32)]
 
 
 class GridDesc(C.Structure):
@@ -89,6 +95,9 @@ def load(path=LIB_PATH):
     L.fv3_elem_size.argtypes = [vp]
     L.fv3_get_layout.restype = st
     L.fv3_get_layout.argtypes = [vp, i, C.POINTER(Layout)]
+    L.fv3_halo_plan.restype = st
+    L.fv3_halo_plan.argtypes = [C.POINTER(GridDesc), i, i, C.POINTER(HaloEntry), C.c_size_t,
+                                C.POINTER(C.c_size_t), C.POINTER(Layout)]
     for nm in ("fv3_import", "fv3_export"):
         f = getattr(L, nm)
         f.restype = st
@@ -165,6 +174,29 @@ def params(mlp=None, **kw):
         prm.mlp = C.c_void_p(mlp.data_ptr())
         prm._keep = mlp
     return prm
+
+
+def halo_plan(grid_type, npx, npz, kind=PLAN_CELL, member=0, precision=FP64, n_members=1, member_npx=None,
+              dx=1.0e5, radius=6.3712e6, omega=7.292e-5):
+    """The halo plan of one member (fv3_halo_plan; host only, no device):
+    returns (entries, layout) with entries a dict of int64 numpy arrays dst,
+    src, dst_tile, src_tile, sign, flags."""
+    L = load()
+    mn = (C.c_int * len(member_npx))(*member_npx) if member_npx is not None else None
+    desc = GridDesc(grid_type, npx, npz, n_members, C.cast(mn, C.POINTER(C.c_int)) if mn else None, precision,
+                    dx, radius, omega)
+    total = C.c_size_t()
+    lay = Layout()
+    rc = L.fv3_halo_plan(C.byref(desc), member, kind, None, 0, C.byref(total), C.byref(lay))
+    if rc != FV3_OK:
+        raise Fv3Error("%s: fv3_halo_plan" % STATUS.get(rc, rc))
+    buf = (HaloEntry * max(1, total.value))()
+    rc = L.fv3_halo_plan(C.byref(desc), member, kind, buf, total.value, C.byref(total), None)
+    if rc != FV3_OK:
+        raise Fv3Error("%s: fv3_halo_plan" % STATUS.get(rc, rc))
+    a = np.frombuffer(buf, dtype=np.int32).reshape(-1, 6)[: total.value].astype(np.int64)
+    names = ("dst", "src", "dst_tile", "src_tile", "sign", "flags")
+    return {nm: a[:, k].copy() for k, nm in enumerate(names)}, lay
 
 
 def _stream(stream):
