@@ -36,7 +36,7 @@ def test_c96x80_fp64_substep_and_step(orc):
     s2.run_dyn(orc.params(n_split=6), 1)
     for f in FIELDS + tuple("q%d" % k for k in range(nq)):
         e = relerr(g.read(gs, f), s2.get(f))
-        assert e <= 10 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
 
 
 def test_batched_ensemble_members(orc):
@@ -132,4 +132,4 @@ def test_c96x80_fp64_all_options_step(orc):
     s.run_dyn(orc.params(n_split=6, **opts), 1)
     for f in FIELDS + ("delz", "q0", "q1"):
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 10 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)

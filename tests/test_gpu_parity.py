@@ -57,7 +57,7 @@ def test_full_substep(orc, cubed, n, nz):
         s.substep()
         for f in FIELDS:
             e = relerr(g.read(gs, f), s.get(f))
-            assert e <= TOL64 * (it + 1), (it, f, e)
+            assert e <= TOL64, (it, f, e)
 
 
 def test_halo_fill_slots(orc):
@@ -129,10 +129,71 @@ def test_run_dyn_with_tracers(orc, cubed, n, nz, nq):
     s.run_dyn(prm_o, n_steps=2)
     for f in FIELDS:
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 6 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
     for m in range(nq):
         e = relerr(g.read(gs, "q%d" % m), s.get("q%d" % m))
-        assert e <= 6 * TOL64, ("q%d" % m, e)
+        assert e <= TOL64, ("q%d" % m, e)
+    assert g.check_status() == 0
+
+
+SUBCYCLE_RADIUS = I.RADIUS / 20    # a small sphere: C12 cells of about 40 km
+
+
+@pytest.mark.parametrize("n_split,nsplt", [(30, 2), (45, 3), (60, 4)])
+def test_tracer_subcycling_cube(orc, n_split, nsplt):
+    """tracer_2d with nsplt > 1 (reading R12): a 100 m/s rotation on a sphere of
+    radius R/20 accumulates Courant numbers 1.9 / 2.8 / 3.8 over n_split
+    substeps whose own Courant numbers stay below 0.07; the GPU's cmax /
+    nsplt kernels and the subcycles in the captured graph against the oracle"""
+    from paper_2205_04148_gb300 import fv3
+    n, nz, nq = 12, 3, 2
+    st = I.cubed_state(n, nz, seed=3, ntracers=nq, wind=100.0)
+    st["q"][1] = np.full_like(st["q"][1], 0.625)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz, radius=SUBCYCLE_RADIUS)
+    gs = g.alloc_state(nq)
+    g.load(gs, st)
+    g.run_dyn(gs, fv3.params(n_split=n_split), 1)
+    d = orc.Domain(True, n, nz, radius=SUBCYCLE_RADIUS)
+    s = orc.State(d, nq)
+    s.load(st)
+    s.run_dyn(orc.params(n_split=n_split), 1)
+    cmax = max(np.abs(s.get("crx")).max(), np.abs(s.get("cry")).max())
+    assert int(np.ceil(cmax)) == nsplt
+    for f in FIELDS + ("q0", "q1"):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= TOL64, (f, e)
+    assert np.abs(g.read(gs, "q1") - 0.625).max() <= 1e-14
+    assert g.check_status() == 0
+
+
+@pytest.mark.parametrize("U,V,nsplt", [(25.0, -20.0, 2), (45.0, 30.0, 3)])
+def test_tracer_subcycling_translation(orc, U, V, nsplt):
+    """uniform translation on a periodic 2 km grid: per-substep Courant numbers
+    0.25 / 0.45, accumulated over 6 substeps 1.5 / 2.7"""
+    from paper_2205_04148_gb300 import fv3
+    n, nz, nq, dx = 16, 2, 2, 2.0e3
+    xc = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(xc, xc)
+    rng = np.random.default_rng(5)
+    q0 = 0.5 + 0.4 * np.sin(2 * np.pi * X + 0.3) * np.cos(2 * np.pi * Y) + 0.05 * rng.standard_normal((n, n))
+    delp = np.full((1, nz, n, n), 1000.0)
+    pt = np.full((1, nz, n, n), 280.0)
+    st = dict(u=np.full((1, nz, n + 1, n), U), v=np.full((1, nz, n, n + 1), V), w=np.zeros((1, nz, n, n)),
+              delp=delp, pt=pt, delz=I.hydrostatic_delz(delp, pt),
+              q=[np.broadcast_to(q0, (1, nz, n, n)).copy(), np.full((1, nz, n, n), 0.3)])
+    g = fv3.Grid(fv3.GRID_PERIODIC, n, nz, dx=dx)
+    gs = g.alloc_state(nq)
+    g.load(gs, st)
+    g.run_dyn(gs, fv3.params(n_split=6), 1)
+    d = orc.Domain(False, n, nz, dx=dx)
+    s = orc.State(d, nq)
+    s.load(st)
+    s.run_dyn(orc.params(n_split=6), 1)
+    cmax = max(np.abs(s.get("crx")).max(), np.abs(s.get("cry")).max())
+    assert int(np.ceil(cmax)) == nsplt
+    for f in FIELDS + ("q0", "q1"):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= TOL64, (f, e)
     assert g.check_status() == 0
 
 
@@ -235,7 +296,7 @@ def test_autotune_keeps_parity(orc):
     s.run_dyn(prm_o, 1)
     for f in FIELDS + ("q0",):
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 3 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -268,7 +329,7 @@ def test_persistent_launch_matches(orc, precision):
             s.run_dyn(orc.params(n_split=3), 1)
             for f in FIELDS + ("q1",):
                 e = relerr(out[1][(f, m)], s.get(f))
-                assert e <= 3 * TOL64, (m, f, e)
+                assert e <= TOL64, (m, f, e)
 
 
 def test_fp32_error_after_100_substeps():
@@ -303,7 +364,7 @@ def test_fourth_order_c_grid_winds(orc, cubed):
     s.run_dyn(orc.params(n_split=2, d2c_ord=4), 1)
     for f in FIELDS + ("q0",):
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 3 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
     g32, gs32, _, _, _ = pair(orc, cubed, 20, 4, seed=97, nq=1, precision=fv3.FP32)
     g32.run_dyn(gs32, fv3.params(n_split=2, d2c_ord=4), 1)
     for f in ("u", "v", "delp", "pt"):
@@ -323,6 +384,6 @@ def test_divergence_damping(orc, cubed):
         s.substep(orc.params(d2_bg=0.04, dddmp=0.3))
     for f in FIELDS:
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 3 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
     with pytest.raises(fv3.Fv3Error, match="ARG"):
         g.substep(gs, fv3.params(d2_bg=-1.0))

@@ -56,7 +56,7 @@ def test_run_dyn_with_remap(orc):
     s.run_dyn(orc.params(n_split=2, remap=1), 1)
     for f in ALL + ("q0",):
         e = relerr(g.read(gs, f), s.get(f))
-        assert e <= 3 * TOL64, (f, e)
+        assert e <= TOL64, (f, e)
 
 
 def test_remap_batched_members(orc):
