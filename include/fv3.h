@@ -204,6 +204,27 @@ enum { FV3_PLAN_CELL = 0, FV3_PLAN_DGRID = 2, FV3_PLAN_CGRID = 3 };
 fv3_status fv3_halo_plan(const fv3_grid_desc* desc, int member, int kind, fv3_halo_entry* out, size_t cap,
                          size_t* total, fv3_layout* layout);
 
+/* Device side of a halo exchange between ranks that hold different tiles of
+ * one member (Section V-C; tiles on several GPUs).  A rank's part of the plan
+ * of fv3_halo_plan, split by tile owner, is lists of element offsets (int64,
+ * device) into its field buffer (device, elements of elem_size 4 or 8 bytes):
+ *   fv3_halo_gather:  out[e] = sign[e] * field[src[e]]  (the message to a
+ *                     peer; sign int8 +-1, NULL for +1);
+ *   fv3_halo_scatter: field[dst[e]] = in[e]  (a peer's message; in NULL
+ *                     writes NaN, for halo slots that have no value);
+ *   fv3_halo_copy:    field[dst[e]] = sign[e] * field[src[e]]  (slots filled
+ *                     from the rank's own tiles; dst and src must be disjoint
+ *                     sets, as halo slots are filled from interior values).
+ * e < count; count = 0 is a no-op.  The messages travel between ranks through
+ * the caller's transport.  Errors: FV3_ERR_ARG (count < 0, elem_size not 4 or
+ * 8, a NULL array), FV3_ERR_CUDA (launch failure). */
+fv3_status fv3_halo_gather(const void* field, int elem_size, const int64_t* src, const int8_t* sign, int64_t count,
+                           void* out, fv3_stream stream);
+fv3_status fv3_halo_scatter(void* field, int elem_size, const int64_t* dst, const void* in, int64_t count,
+                            fv3_stream stream);
+fv3_status fv3_halo_copy(void* field, int elem_size, const int64_t* src, const int64_t* dst, const int8_t* sign,
+                         int64_t count, fv3_stream stream);
+
 /* Fill the halos (strips of 3, owner copies of shared tile-edge faces, cube
  * corner slots) of the fields selected by `field_mask` (FV3_HALO_*), all
  * members: Section V-C, on the device. */
@@ -349,8 +370,11 @@ fv3_status fv3_autotune(fv3_ctx* ctx, const fv3_state* state, const fv3_params* 
  * Network: 6 -> 32 -> 32 -> 1 with tanh, parameters float[1313] on the device
  * (W1[6][32] at 0, b1 at 192, W2[32][32] at 224, b2 at 1248, W3[32] at 1280,
  * b3 at 1312).  Inputs per face: the six cells of the PPM face stencil minus
- * their mean, over their standard deviation.  Tensor-core evaluation
- * (bfloat16 operands, float accumulation, hardware tanh). */
+ * their mean, over their standard deviation sig (+ 1e-12 |mean|).  The
+ * learned face value is the plain PPM face value + sig * y, y the
+ * mirror-symmetric network output; plain PPM where that value leaves the
+ * range of the two cells next to the face or is negative.  Tensor-core
+ * evaluation (bfloat16 operands, float accumulation, hardware tanh). */
 
 /* y[n] = network(x[n][6]); symmetric != 0 averages x and the reversed x. */
 fv3_status fv3_mlp_forward(const float* w, const float* x, int n, int symmetric, float* y, fv3_stream stream);
@@ -373,6 +397,27 @@ size_t fv3_mlp_work_floats_fp32(int n);
 fv3_status fv3_mlp_grad_fp32(const float* w, const float* x, const float* t, int n, float weight, float* work,
                              float* grad, float* loss, fv3_stream stream);
 
+/* Single-stencil exports of the FP64 transport's face arithmetic (readings R4
+ * and R14; Section IX-C for the PPM face values), for forming training
+ * targets and for tests.  q6: device double[n][6], six consecutive cell means
+ * along a sweep, the face between q6[f][2] and q6[f][3]; cr: device double[n]
+ * Courant numbers at that face (|cr| <= 1).  Outputs (device, each may be
+ * NULL): plain[n] the plain PPM face value (edge values, limiter, swept mean
+ * of the upwind cell's parabola, as inside fv3_fv_tp_2d); edge[n] the clamped
+ * fourth-order edge value between q6[f][2] and q6[f][3]; x[n][6], sig[n] the
+ * network inputs and standard deviation (float).  n = 0 is a no-op.  Errors:
+ * FV3_ERR_ARG (q6 NULL, n < 0, cr NULL with plain requested), FV3_ERR_CUDA
+ * (launch failure). */
+fv3_status fv3_face_stencils(const double* q6, const double* cr, int n, double* plain, double* edge, float* x,
+                             float* sig, fv3_stream stream);
+
+/* Learned face values of n stencils as the FP64 transport forms them with
+ * the network w (device float[1313]): value[n] (device) is the plain PPM face
+ * value + sig * y where that lies in [min(q6[f][2], q6[f][3]), max(...)] and
+ * is not negative, else the plain value.  Arguments as fv3_face_stencils. */
+fv3_status fv3_learned_faces(const float* w, const double* q6, const double* cr, int n, double* value,
+                             fv3_stream stream);
+
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected, step >= 1) on
  * float master weights w with moments m, v. */
 fv3_status fv3_mlp_adam(float* w, float* m, float* v, const float* grad, int step, float lr, fv3_stream stream);
@@ -389,12 +434,20 @@ fv3_status fv3_mlp_adam(float* w, float* m, float* v, const float* grad, int ste
  * (held on every GPU that loads the library until the process exits), so
  * 5 * nz * ncol must not exceed 4,194,304 (e.g. ncol <= 10485 at nz = 80);
  * larger sizes return FV3_ERR_SHAPE without launching.  The first call on a
- * device looks up the scratch address on that device (make that first call
- * before any stream capture).  All calls share the one scratch array, so
- * calls that may run at the same time on the GPU (different streams, or
- * host threads) race and must be ordered by the caller; nothing in the
- * scratch has to start at zero, every value read is written first in the
- * same call. */
+ * device looks up the scratch address on that device; with lazy module
+ * loading (the CUDA default) that lookup loads the library's module there and
+ * so reserves the 32 MiB array and the kernel image.  Make that first call
+ * (or any other fv3 call on the device) before entering a region where
+ * nothing may be allocated, and before any stream capture; later calls
+ * allocate nothing.  The looked-up address does not survive a device reset
+ * (cudaDeviceReset): do not call this entry point across one.  All calls
+ * share the one scratch array, so calls that may run at the same time on the
+ * GPU (different streams, or host threads) race and must be ordered by the
+ * caller; nothing in the scratch has to start at zero, every value read is
+ * written first in the same call.  Errors: FV3_ERR_ARG (a NULL pointer;
+ * dt, grav, a_imp, rdgas or ptop not positive; cp_air <= rdgas),
+ * FV3_ERR_SHAPE (ncol < 1, nz < 2, or beyond the scratch), FV3_ERR_CUDA (the
+ * address lookup or the launch failed). */
 fv3_status fv3_riem_solver_c_noalloc(int ncol, int nz, const double* delpc, const double* ptc, const double* wc,
                                      const double* delzc, double* pef, double* gz, const fv3_params* params,
                                      fv3_stream stream);

@@ -663,6 +663,7 @@ static double ppm_face(const double* q, long s, double c) {
 
 /* exported for the pins: face value from the six cells q6[0..5] = q_{i-3..i+2} */
 double orc_ppm_face(const double* q6, double c) { return ppm_face(q6 + 3, 1, c); }
+double orc_ppm_edge(const double* q4) { return ppm_edge(q4[0], q4[1], q4[2], q4[3]); }
 
 /* ------------------------------------------------------------------ */
 /* learned edge value (reading R14; no counterpart in the paper, which */
@@ -671,7 +672,8 @@ double orc_ppm_face(const double* q6, double c) { return ppm_face(q6 + 3, 1, c);
 /* Parameters, flat (1313 values): W1[6][32] (input i -> hidden j at i*32+j),
    b1[32], W2[32][32], b2[32], W3[32], b3.  Network: h1 = tanh(x W1 + b1),
    h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, on the six cell means normalised by
-   their mean mu and standard deviation sigma; edge value = mu + sigma * y. */
+   their mean mu and standard deviation sigma; learned face value = plain PPM
+   face value + sigma * y (reading R14). */
 #define MLP_NP 1313
 #define MLP_W1 0
 #define MLP_B1 192
@@ -690,27 +692,23 @@ static float bf16r(float f) {
   return v.f;
 }
 
-/* network inputs of the six cells (reading R14): offsets d_i = q_i - r from
-   the mean r of the two cells next to the face (FP64, rounded to float),
-   then in float their mean m, the deviations e_i = d_i - m, the standard
-   deviation sig = sqrt(mean e_i^2) and x_i = e_i / (sig + 1e-30).  Sums are
-   taken in mirror pairs (i, 5 - i) so that the reversed stencil gives the
-   reversed inputs bit for bit.  Returns sig. */
-static float mlp_normalise(const double* q6, float* x) {
-  const double r = 0.5 * (q6[2] + q6[3]);
-  float d[6], e[6];
-  for (int i = 0; i < 6; i++) d[i] = (float)(q6[i] - r);
-  const float sixth = 1.0f / 6.0f;
-  const float m = ((d[0] + d[5]) + (d[1] + d[4]) + (d[2] + d[3])) * sixth;
-  for (int i = 0; i < 6; i++) e[i] = d[i] - m;
-  float sq[6];
-  for (int i = 0; i < 6; i++) sq[i] = e[i] * e[i];
-  const float v = ((sq[0] + sq[5]) + (sq[1] + sq[4]) + (sq[2] + sq[3])) * sixth;
-  const float sig = sqrtf(v);
-  const float inv = 1.0f / (sig + 1e-30f);
-  for (int i = 0; i < 6; i++) x[i] = e[i] * inv;
+/* network inputs of the six cells (reading R14): the stencil mean mu and the
+   standard deviation sig = sqrt(mean (q_i - mu)^2), then x_i = (q_i - mu) /
+   (sig + eps) with eps = 1e-12 |mu| + 1e-300, all in FP64.  Sums are taken in
+   mirror pairs (i, 5 - i) so that the reversed stencil gives the reversed
+   inputs bit for bit.  Returns sig. */
+static double mlp_normalise(const double* q6, double* x) {
+  const double mu = ((q6[0] + q6[5]) + (q6[1] + q6[4]) + (q6[2] + q6[3])) / 6.0;
+  double e[6];
+  for (int i = 0; i < 6; i++) e[i] = q6[i] - mu;
+  const double v = ((e[0] * e[0] + e[5] * e[5]) + (e[1] * e[1] + e[4] * e[4]) + (e[2] * e[2] + e[3] * e[3])) / 6.0;
+  const double sig = sqrt(v);
+  const double den = sig + (1e-12 * fabs(mu) + 1e-300);
+  for (int i = 0; i < 6; i++) x[i] = e[i] / den;
   return sig;
 }
+
+double orc_mlp_normalise(const double* q6, double* x) { return mlp_normalise(q6, x); }
 
 /* FP64 forward; h1, h2 (32 each) returned for the backward pass */
 double orc_mlp_forward(const double* w, const double* x, double* h1, double* h2) {
@@ -804,23 +802,32 @@ double orc_mlp_forward_bf16(const double* w, const double* x) {
    plain value alone where the sum leaves the range of the two cells or, for a
    positive field, goes negative */
 static double learned_value(const double* mlp, int bf16, const double* q6, int positive, double plain) {
-  float x[6];
-  double xd[6], xr[6], h1[32], h2[32];
-  const float sig = mlp_normalise(q6, x);
-  for (int i = 0; i < 6; i++) {
-    xd[i] = (double)x[i];
-    xr[5 - i] = (double)x[i];
-  }
+  double x[6], xr[6], h1[32], h2[32];
+  const double sig = mlp_normalise(q6, x);
+  for (int i = 0; i < 6; i++) xr[5 - i] = x[i];
   /* mirror-symmetric evaluation: the two tiles that share a cube edge see
      the stencil in opposite orders and must compute the same flux */
-  const float y1 = (float)(bf16 ? orc_mlp_forward_bf16(mlp, xd) : orc_mlp_forward(mlp, xd, h1, h2));
-  const float y2 = (float)(bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2));
-  const float y = 0.5f * (y1 + y2);
-  const float corr = y * sig;
-  const double a = plain + (double)corr;
+  const double y1 = bf16 ? orc_mlp_forward_bf16(mlp, x) : orc_mlp_forward(mlp, x, h1, h2);
+  const double y2 = bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2);
+  const double a = plain + 0.5 * (y1 + y2) * sig;
   const double lo = fmin(q6[2], q6[3]), hi = fmax(q6[2], q6[3]);
   if (!(a >= lo && a <= hi)) return plain;
   if (positive && a < 0.0) return plain;
+  return a;
+}
+
+/* the learned candidate a = plain + sig y before the fallback test, for the
+   pins of the fallback decision (returns a; *accepted = 1 where it is kept) */
+double orc_learned_candidate(const double* mlp, int bf16, const double* q6, double c, int positive, int* accepted) {
+  double x[6], xr[6], h1[32], h2[32];
+  const double plain = ppm_face(q6 + 3, 1, c);
+  const double sig = mlp_normalise(q6, x);
+  for (int i = 0; i < 6; i++) xr[5 - i] = x[i];
+  const double y1 = bf16 ? orc_mlp_forward_bf16(mlp, x) : orc_mlp_forward(mlp, x, h1, h2);
+  const double y2 = bf16 ? orc_mlp_forward_bf16(mlp, xr) : orc_mlp_forward(mlp, xr, h1, h2);
+  const double a = plain + 0.5 * (y1 + y2) * sig;
+  const double lo = fmin(q6[2], q6[3]), hi = fmax(q6[2], q6[3]);
+  *accepted = (a >= lo && a <= hi) && !(positive && a < 0.0);
   return a;
 }
 

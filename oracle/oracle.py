@@ -58,6 +58,8 @@ def _load():
     L.orc_get_metric.argtypes = [vp, C.c_char_p, dp]
     L.orc_ppm_face.restype = C.c_double
     L.orc_ppm_face.argtypes = [dp, C.c_double]
+    L.orc_ppm_edge.restype = C.c_double
+    L.orc_ppm_edge.argtypes = [dp]
     L.orc_state_create.restype = vp
     L.orc_state_create.argtypes = [vp, C.c_int]
     L.orc_state_free.argtypes = [vp]
@@ -94,6 +96,10 @@ def _load():
     L.orc_remap_column.argtypes = [C.c_int, dp, dp, dp, dp]
     L.orc_remap.restype = None
     L.orc_remap.argtypes = [C.c_void_p, C.POINTER(OParams)]
+    L.orc_mlp_normalise.restype = C.c_double
+    L.orc_mlp_normalise.argtypes = [dp, dp]
+    L.orc_learned_candidate.restype = C.c_double
+    L.orc_learned_candidate.argtypes = [dp, C.c_int, dp, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.orc_learned_face.restype = C.c_double
     L.orc_learned_face.argtypes = [dp, C.c_int, dp, C.c_double, C.c_int]
     _lib = L
@@ -261,6 +267,13 @@ def ppm_face(q6, c):
     return L.orc_ppm_face(_p(q), float(c))
 
 
+def ppm_edge(q4):
+    """clamped fourth-order edge value between q4[1] and q4[2] (reading R4)"""
+    L = _load()
+    q = _c(q4)
+    return L.orc_ppm_edge(_p(q))
+
+
 def thomas(a, b, c, d):
     L = _load()
     a, b, c, d = map(_c, (a, b, c, d))
@@ -403,20 +416,30 @@ def learned_face(w, q6, c, positive=1, bf16=0):
 
 
 def mlp_normalise(q6):
-    """network inputs and sigma of six-cell stencils [..., 6] (reading R14, as
-    in the C oracle): float offsets from the mean of the two centre cells,
-    mirror-pair sums in float"""
-    q = np.asarray(q6, dtype=np.float64)
-    r = 0.5 * (q[..., 2] + q[..., 3])
-    d = (q - r[..., None]).astype(np.float32)
-    sixth = np.float32(1.0) / np.float32(6.0)
-    m = ((d[..., 0] + d[..., 5]) + (d[..., 1] + d[..., 4]) + (d[..., 2] + d[..., 3])) * sixth
-    e = d - m[..., None]
-    sq = e * e
-    v = ((sq[..., 0] + sq[..., 5]) + (sq[..., 1] + sq[..., 4]) + (sq[..., 2] + sq[..., 3])) * sixth
-    sig = np.sqrt(v)
-    inv = np.float32(1.0) / (sig + np.float32(1e-30))
-    return e * inv[..., None], sig
+    """network inputs x [..., 6] and sigma [...] of six-cell stencils (reading
+    R14, FP64: mean, standard deviation, x = (q - mean) / (sigma + 1e-12
+    |mean| + 1e-300), mirror-pair sums)"""
+    L = _load()
+    q = _c(q6)
+    shp = q.shape[:-1]
+    q = q.reshape(-1, 6)
+    x = np.empty_like(q)
+    sig = np.empty(q.shape[0])
+    for f in range(q.shape[0]):
+        xf = np.empty(6)
+        sig[f] = L.orc_mlp_normalise(_p(np.ascontiguousarray(q[f])), _p(xf))
+        x[f] = xf
+    return x.reshape(shp + (6,)), sig.reshape(shp)
+
+
+def learned_candidate(w, q6, c, positive=1, bf16=0):
+    """(a, accepted): the learned face value candidate plain + sigma y before
+    the fallback test, and whether the fallback keeps it (reading R14)"""
+    L = _load()
+    w, q6 = _c(w), _c(q6)
+    acc = C.c_int()
+    a = L.orc_learned_candidate(_p(w), int(bf16), _p(q6), float(c), int(positive), C.byref(acc))
+    return a, bool(acc.value)
 
 
 def remap_column(pe, pn, q):

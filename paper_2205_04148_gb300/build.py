@@ -22,7 +22,7 @@ SOURCES = [("fv3_grid.cpp", "fv3_grid", ()),
            ("fv3_kernels.cu", "fv3_kernels_main", ("-DFV3_TU=1",)),
            ("fv3_capi.cu", "fv3_capi", ()), ("fv3_calib.cu", "fv3_calib", ()),
            ("fv3_noalloc.cu", "fv3_noalloc", ()), ("fv3_mlp.cu", "fv3_mlp", ()),
-           ("fv3_remap.cu", "fv3_remap", ())]
+           ("fv3_remap.cu", "fv3_remap", ()), ("fv3_exchange.cu", "fv3_exchange", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

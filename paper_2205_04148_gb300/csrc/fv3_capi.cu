@@ -911,3 +911,23 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
   if (best_ms) *best_ms = best;
   return r;
 }
+
+// ------------------------------------------------------------------------
+// single-stencil exports (readings R4, R14)
+// ------------------------------------------------------------------------
+extern "C" fv3_status fv3_face_stencils(const double* q6, const double* cr, int n, double* plain, double* edge,
+                                        float* x, float* sig, fv3_stream stream) {
+  if (!q6 || n < 0 || (plain && !cr)) return FV3_ERR_ARG;
+  if (n == 0) return FV3_OK;
+  return fv3::launch_face_stencils(q6, cr, n, plain, edge, x, sig, (cudaStream_t)stream) == cudaSuccess
+             ? FV3_OK
+             : FV3_ERR_CUDA;
+}
+
+extern "C" fv3_status fv3_learned_faces(const float* w, const double* q6, const double* cr, int n, double* value,
+                                        fv3_stream stream) {
+  if (!w || !q6 || !cr || !value || n < 0) return FV3_ERR_ARG;
+  if (n == 0) return FV3_OK;
+  return fv3::launch_learned_stencils(w, q6, cr, n, value, (cudaStream_t)stream) == cudaSuccess ? FV3_OK
+                                                                                               : FV3_ERR_CUDA;
+}

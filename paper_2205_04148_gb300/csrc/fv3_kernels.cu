@@ -2080,4 +2080,90 @@ void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padde
 
 #endif
 
+#if FV3_TU_F64
+// ------------------------------------------------------------------------
+// stencil exports (FP64; readings R4, R14): the PPM face value, the clamped
+// edge value and the network inputs of single six-cell stencils q6[f][0..5]
+// (the face between q6[f][2] and q6[f][3]), formed by the same device
+// functions as the transports (edge values first, then the limited parabola
+// of the upwind cell), and the learned face value of the FP64 transport
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_face_stencils(const double* q6, const double* cr, int n, double* plain,
+                                                       double* edge, float* x, float* sig) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n; f += gridDim.x * blockDim.x) {
+    double q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = q6[6 * (long long)f + k];
+    if (plain) {
+      // AL[l]: edge between q[l - 1] and q[l], l = 2, 3, 4
+      double al[5];
+#pragma unroll
+      for (int l = 2; l <= 4; ++l) al[l] = ppm_edge<double>(q[l - 2], q[l - 1], q[l], q[l + 1]);
+      plain[f] = ppm_face_al<double>(q, al, 3, 1, cr[f]);
+    }
+    if (edge) edge[f] = ppm_edge<double>(q[1], q[2], q[3], q[4]);
+    if (x || sig) {
+      float xi[6], xr[6];
+      const float sg = mlp_inputs<double>(q, xi, xr);
+      if (x)
+        for (int k = 0; k < 6; ++k) x[6 * (long long)f + k] = xi[k];
+      if (sig) sig[f] = sg;
+    }
+  }
+}
+
+// learned face values: 256 stencils per CTA laid out as rows of a
+// shared-memory tile (cells i = -3 .. 2 of row j, the face at i = 0), so that
+// the transport's warp-level evaluation learned_faces runs unchanged
+constexpr int kStencilRows = 256, kStencilSX = 8;
+
+__global__ void __launch_bounds__(256) k_learned_stencils(const float* w, const double* q6, const double* cr, int n,
+                                                          double* value) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int SA = (kStencilRows + 6) * kStencilSX;
+  double* Q = reinterpret_cast<double*>(smraw);
+  double *AL = Q + SA, *CC = Q + 2 * SA, *OUT = Q + 3 * SA;
+  MlpFrag F;
+  mlp_load(w, F);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int f0 = blockIdx.x * kStencilRows; f0 < n; f0 += gridDim.x * kStencilRows) {
+    const int rows = min(kStencilRows, n - f0);
+    const Blk B{0, 1, 0, rows, kStencilSX};
+    for (int e = tid; e < rows * 6; e += 256) {
+      const int j = e / 6, k = e % 6;
+      Q[B.L(k - 3, j)] = q6[6 * (long long)(f0 + j) + k];
+    }
+    for (int j = tid; j < rows; j += 256) CC[B.L(0, j)] = cr[f0 + j];
+    __syncthreads();
+    for (int e = tid; e < rows * 3; e += 256) {
+      const int j = e / 3, i = e % 3 - 1;  // edges i = -1, 0, 1
+      const int l = B.L(i, j);
+      AL[l] = ppm_edge<double>(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
+    }
+    __syncthreads();
+    learned_faces<double>(Q, AL, CC, OUT, 0, 1, 0, rows, 1, B, F);
+    __syncthreads();
+    for (int j = tid; j < rows; j += 256) value[f0 + j] = OUT[B.L(0, j)];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_face_stencils(const double* q6, const double* cr, int n, double* plain, double* edge, float* x,
+                                 float* sig, cudaStream_t st) {
+  const int blocks = std::min((n + 255) / 256, 152 * 8);
+  k_face_stencils<<<blocks, 256, 0, st>>>(q6, cr, n, plain, edge, x, sig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_learned_stencils(const float* w, const double* q6, const double* cr, int n, double* value,
+                                    cudaStream_t st) {
+  const size_t sm = 4 * sizeof(double) * (kStencilRows + 6) * kStencilSX;
+  cudaError_t e = cudaFuncSetAttribute(k_learned_stencils, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int blocks = std::min((n + kStencilRows - 1) / kStencilRows, 152 * 2);
+  k_learned_stencils<<<blocks, dim3(32, 8), sm, st>>>(w, q6, cr, n, value);
+  return cudaGetLastError();
+}
+#endif
+
 }  // namespace fv3

@@ -17,6 +17,7 @@ struct StepArgs {
   const Geo* geo;        // per member
   const Item* items;     // CTA work list
   Metric<R> M;           // metric in the arithmetic precision
+  Metric<double> Md;     // the FP64 metric (kernels with FP64 metric terms)
   Params P;
   // prognostic state (in) and next state (out)
   const R *u, *v, *w, *delp, *pt, *delz;
@@ -54,6 +55,7 @@ struct TracerArgs {
   const Geo* geo;
   const Item* items;
   Metric<R> M;
+  Metric<double> Md;     // the FP64 metric (kernels with FP64 metric terms)
   int nq, it;            // tracers, subcycle index
   const int* nsplt;      // device: number of subcycles of this remapping step
   const R* q[MAX_TRACERS];
@@ -79,6 +81,8 @@ struct RowItem {
 // the library context behind the opaque fv3_ctx handle
 struct Ctx {
   GridSpec spec{};
+  // prec: 0 FP64; 1 FP32 bulk with FP32 copies of the metric; 2 FP32 bulk
+  // with the metric terms in FP64
   int nz = 0, nmem = 0, prec = 0, esize = 8;
   std::vector<Geo> geo;
   Geo* geo_d = nullptr;
@@ -155,8 +159,11 @@ void enqueue_substep_f64(Ctx& c, const StateView& in, const StateView& out, cons
                      cudaStream_t st, int stop_after, int only);
 void enqueue_substep_f32(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
                      cudaStream_t st, int stop_after, int only);
+void enqueue_substep_f32m64(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                            cudaStream_t st, int stop_after, int only);
 void enqueue_tracers_f64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_tracers_f32(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
+void enqueue_tracers_f32m64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st);
 
 // vertical remapping (fv3_remap.cu): caller's state in, context buffers out
@@ -185,6 +192,7 @@ struct TpArgs {
   const Geo* geo;
   const Item* items;
   Metric<R> M;
+  Metric<double> Md;     // the FP64 metric (kernels with FP64 metric terms)
   const R *q, *crx, *cry, *xfx, *yfx, *mfx, *mfy;
   R *fx, *fy;
   double damp;
@@ -192,6 +200,7 @@ struct TpArgs {
 void enqueue_fv_tp_2d(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_fv_tp_2d_f64(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_fv_tp_2d_f32(Ctx& c, const TpPtrs& p, cudaStream_t st);
+void enqueue_fv_tp_2d_f32m64(Ctx& c, const TpPtrs& p, cudaStream_t st);
 void enqueue_mass(Ctx& c, const void* delp, cudaStream_t st);
 void enqueue_check_finite(Ctx& c, const StateView& s, cudaStream_t st);
 void enqueue_pack(Ctx& c, int member, int kind, int nlev, int iface, void* padded, void* dense, int dense_is_double,
@@ -201,6 +210,12 @@ void enqueue_copy_state(Ctx& c, const StateView& dst, const StateView& src, cuda
 void enqueue_zero_acc(Ctx& c, cudaStream_t st);
 void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st);
 bool shape_supported(int bx, int by);
+// stencil exports (FP64, no context): plain PPM face values, clamped edge
+// values and network inputs of six-cell stencils; learned face values
+cudaError_t launch_face_stencils(const double* q6, const double* cr, int n, double* plain, double* edge, float* x,
+                                 float* sig, cudaStream_t st);
+cudaError_t launch_learned_stencils(const float* w, const double* q6, const double* cr, int n, double* value,
+                                    cudaStream_t st);
 // calibration kernels (fv3_calib.cu): returns work per launch (flops or bytes)
 double enqueue_calibration(Ctx& c, int what, cudaStream_t st);
 

@@ -148,12 +148,16 @@ __device__ __forceinline__ float mlp_warp(const MlpFrag& F, const float (&x)[6],
   return y + F.c3;
 }
 
-// network inputs of a six-cell stencil (reading R14): offsets from the mean
-// of the two centre cells in the stencil's precision, rounded to float; then
-// in float the mean, deviations, standard deviation sig and x = dev / (sig +
-// 1e-30), all sums in mirror pairs and without contraction so the reversed
-// stencil gives the reversed inputs bit for bit.  Returns sig; xr = reversed x.
-__device__ __forceinline__ float mlp_offsets_to_inputs(const float (&d)[6], float (&x)[6], float (&xr)[6]) {
+// network inputs of a six-cell stencil (reading R14: x = (q - mean) / (sig +
+// 1e-12 |mean|), sig the standard deviation): offsets d from the mean r of
+// the two centre cells in the stencil's precision, rounded to float; then in
+// float the mean m of the offsets, deviations e = d - m, sig and x = e / (sig
+// + 1e-12 |r| + 1e-30) (|r| stands for the stencil mean's magnitude: the two
+// differ by less than 5 sig), all sums in mirror pairs and without
+// contraction so the reversed stencil gives the reversed inputs bit for bit.
+// ar = |r| as a float.  Returns sig; xr = reversed x.
+__device__ __forceinline__ float mlp_offsets_to_inputs(const float (&d)[6], float ar, float (&x)[6],
+                                                      float (&xr)[6]) {
   const float sixth = 1.0f / 6.0f;
   const float m =
       __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(d[0], d[5]), __fadd_rn(d[1], d[4])), __fadd_rn(d[2], d[3])), sixth);
@@ -166,7 +170,7 @@ __device__ __forceinline__ float mlp_offsets_to_inputs(const float (&d)[6], floa
   const float v =
       __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(sq[0], sq[5]), __fadd_rn(sq[1], sq[4])), __fadd_rn(sq[2], sq[3])), sixth);
   const float sig = __fsqrt_rn(v);
-  const float inv = __fdiv_rn(1.0f, __fadd_rn(sig, 1e-30f));
+  const float inv = __fdiv_rn(1.0f, __fadd_rn(__fadd_rn(sig, __fmul_rn(1e-12f, ar)), 1e-30f));
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     x[i] = __fmul_rn(e[i], inv);
@@ -219,7 +223,7 @@ __device__ __forceinline__ float mlp_inputs<double>(const double (&q)[6], float 
   float d[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) d[i] = to_float_rn(__dsub_rn(q[i], r));
-  return mlp_offsets_to_inputs(d, x, xr);
+  return mlp_offsets_to_inputs(d, fabsf(to_float_rn(r)), x, xr);
 }
 
 template <>
@@ -228,7 +232,7 @@ __device__ __forceinline__ float mlp_inputs<float>(const float (&q)[6], float (&
   float d[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) d[i] = __fsub_rn(q[i], r);
-  return mlp_offsets_to_inputs(d, x, xr);
+  return mlp_offsets_to_inputs(d, fabsf(r), x, xr);
 }
 
 }  // namespace fv3

@@ -15,7 +15,13 @@
 // name as a device address (in host code the name only stands for the
 // symbol), so the address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
-// that device.
+// that device.  With lazy module loading (the CUDA default) that lookup is
+// also what loads this file's module on the device, so the first call
+// reserves the array and the kernel image: it must come before the region in
+// which nothing may be allocated.  Later calls allocate nothing.  The cached
+// address belongs to the context that was current at the first call; after
+// a device reset (cudaDeviceReset) the module is loaded again and the array
+// may move, so the entry point is not for use across a device reset.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -118,8 +124,8 @@ extern "C" fv3_status fv3_riem_solver_c_noalloc(int ncol, int nz, const double* 
   if (!delpc || !ptc || !wc || !delzc || !pef || !gz || !params) return FV3_ERR_ARG;
   if (ncol < 1 || nz < 2) return FV3_ERR_SHAPE;
   if (5LL * nz * (long long)ncol > kScratchDoubles) return FV3_ERR_SHAPE;  // beyond the fixed scratch
-  if (!(params->dt > 0) || !(params->grav > 0) || !(params->a_imp > 0) || !(params->cp_air > params->rdgas) ||
-      !(params->ptop > 0))
+  if (!(params->dt > 0) || !(params->grav > 0) || !(params->a_imp > 0) || !(params->rdgas > 0) ||
+      !(params->cp_air > params->rdgas) || !(params->ptop > 0))
     return FV3_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FV3_ERR_CUDA;

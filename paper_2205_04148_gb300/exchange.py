@@ -11,9 +11,18 @@ its own order, so the values of a message need no index.
 Fields are tensors [arrays][local tiles][levels][plane] in the library's plane
 layout (arrays: 1 for a scalar, 2 for a vector pair: the x-face array, then the
 y-face array); the tiles of a rank are its owned tiles in increasing order.
-The messages go through torch.distributed point-to-point operations (gloo on
-CPU tensors, NCCL on device tensors); a message that does not arrive within
-the timeout raises ExchangeError instead of waiting for ever.
+An exchange is three steps: pack (each peer's message gathered with the
+vector sign), local (halo slots filled from the rank's own tiles, NaN where
+the plan has no value) and unpack (each received message scattered into its
+halo slots).  On device tensors every step runs in the library's kernels
+(fv3_halo_gather, fv3_halo_copy, fv3_halo_scatter); on CPU tensors in torch.
+The messages go through torch.distributed point-to-point operations.  With
+gloo and CPU tensors a message that does not arrive within the timeout
+raises ExchangeError instead of waiting for ever.  With NCCL and device
+tensors the timeout bounds only the host's wait: a peer that never sends
+can leave the receive waiting on the device, so that case has no failure
+guarantee; the device path has been checked on one GPU only (pack and
+unpack against fv3_halo_fill), not between GPUs.
 """
 from __future__ import annotations
 
@@ -54,6 +63,13 @@ class TileExchange:
             base = (arr * ntl + s) * nlev * plane + off
             return (base[:, None] + lev[None, :]).reshape(-1)
 
+        # halo slots are filled from interior values only: no source slot of
+        # the plan is also a destination, so the steps of an exchange (and
+        # the entries within a step) do not depend on their order
+        dst_key = set(zip(dst_t.tolist(), dst_a.tolist(), entries["dst"].tolist()))
+        src_key = set(zip(src_t[sign != 0].tolist(), src_a[sign != 0].tolist(), entries["src"][sign != 0].tolist()))
+        if dst_key & src_key:
+            raise ValueError("plan reads a slot that it also writes")
         mine_dst = owner[dst_t] == rank
         nan = mine_dst & (sign == 0)
         local = mine_dst & (sign != 0) & (owner[src_t] == rank)
@@ -78,12 +94,64 @@ class TileExchange:
         import torch
         dev = like.device
         idx = lambda a: torch.as_tensor(a, dtype=torch.long, device=dev)  # noqa: E731
-        val = lambda a: torch.as_tensor(a, dtype=like.dtype, device=dev)  # noqa: E731
+        if dev.type == "cuda":   # the kernels take the signs as int8
+            val = lambda a: torch.as_tensor(a, dtype=torch.int8, device=dev)  # noqa: E731
+        else:
+            val = lambda a: torch.as_tensor(a, dtype=like.dtype, device=dev)  # noqa: E731
         self._t = {"nan": idx(self.nan_dst), "ls": idx(self.local_src), "ld": idx(self.local_dst),
                    "lsg": val(self.local_sign),
                    "recv": {p: idx(d) for p, d in self.recv.items()},
                    "send": {p: (idx(s), val(g)) for p, (s, g) in self.send.items()},
                    "dev": dev, "dtype": like.dtype}
+
+    def _check(self, buf):
+        if tuple(buf.shape) != self.shape() or not buf.is_contiguous():
+            raise ValueError("need a contiguous tensor of shape %s" % (self.shape(),))
+        if self._t is None or self._t["dev"] != buf.device or self._t["dtype"] != buf.dtype:
+            self._tensors(buf)
+        return self._t
+
+    def pack(self, buf):
+        """{peer: message}: the values of `buf` each peer needs, in plan order,
+        with the vector sign applied"""
+        T = self._check(buf)
+        flat = buf.view(-1)
+        if buf.is_cuda:
+            from . import fv3
+            return {p: fv3.halo_gather(flat, s, g) for p, (s, g) in T["send"].items()}
+        return {p: flat[s] * g for p, (s, g) in T["send"].items()}
+
+    def local(self, buf):
+        """halo slots filled from the rank's own tiles, NaN where the plan has
+        no value"""
+        T = self._check(buf)
+        flat = buf.view(-1)
+        if buf.is_cuda:
+            from . import fv3
+            if T["ls"].numel():
+                fv3.halo_copy(flat, T["ls"], T["ld"], T["lsg"])
+            if T["nan"].numel():
+                fv3.halo_scatter(flat, T["nan"])
+            return buf
+        if T["ls"].numel():
+            flat[T["ld"]] = flat[T["ls"]] * T["lsg"]
+        if T["nan"].numel():
+            flat[T["nan"]] = float("nan")
+        return buf
+
+    def unpack(self, buf, peer, message):
+        """the message of `peer` into its halo slots"""
+        T = self._check(buf)
+        d = T["recv"][peer]
+        if message.numel() != d.numel():
+            raise ExchangeError("message of rank %d has %d values, the plan %d" % (peer, message.numel(), d.numel()))
+        flat = buf.view(-1)
+        if buf.is_cuda:
+            from . import fv3
+            fv3.halo_scatter(flat, d, message.contiguous())
+        else:
+            flat[d] = message
+        return buf
 
     def run(self, buf, timeout_s=30.0, group=None):
         """Fill the halo slots of the local tiles of `buf` (a contiguous
@@ -91,24 +159,16 @@ class TileExchange:
         no value, and the values the owners of the other tiles send."""
         import torch
         import torch.distributed as dist
-        if tuple(buf.shape) != self.shape() or not buf.is_contiguous():
-            raise ValueError("need a contiguous tensor of shape %s" % (self.shape(),))
-        if self._t is None or self._t["dev"] != buf.device or self._t["dtype"] != buf.dtype:
-            self._tensors(buf)
-        T = self._t
-        flat = buf.view(-1)
+        T = self._check(buf)
         reqs = []
-        inbox, outbox = {}, {}  # the messages stay referenced until their waits end
-        for peer, (s, g) in T["send"].items():
-            outbox[peer] = flat[s] * g
-            reqs.append((peer, dist.isend(outbox[peer], peer, group=group)))
+        inbox = {}
+        outbox = self.pack(buf)   # the messages stay referenced until their waits end
+        for peer, msg in outbox.items():
+            reqs.append((peer, dist.isend(msg, peer, group=group)))
         for peer, d in T["recv"].items():
             inbox[peer] = torch.empty(d.numel(), dtype=buf.dtype, device=buf.device)
             reqs.append((peer, dist.irecv(inbox[peer], peer, group=group)))
-        if T["ls"].numel():
-            flat[T["ld"]] = flat[T["ls"]] * T["lsg"]
-        if T["nan"].numel():
-            flat[T["nan"]] = float("nan")
+        self.local(buf)
         limit = datetime.timedelta(seconds=timeout_s)
         for peer, r in reqs:
             try:
@@ -117,6 +177,6 @@ class TileExchange:
                 raise ExchangeError("halo exchange with rank %d failed: %s" % (peer, e)) from e
             if ok is False:
                 raise ExchangeError("halo exchange with rank %d: no message within %.1f s" % (peer, timeout_s))
-        for peer, d in T["recv"].items():
-            flat[d] = inbox[peer]
+        for peer in T["recv"]:
+            self.unpack(buf, peer, inbox[peer])
         return buf

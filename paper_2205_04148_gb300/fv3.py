@@ -33,7 +33,8 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
            "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap",
-           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite", "fv3_halo_plan")
+           "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite", "fv3_halo_plan",
+           "fv3_face_stencils", "fv3_learned_faces", "fv3_halo_gather", "fv3_halo_scatter", "fv3_halo_copy")
 PLAN_CELL, PLAN_DGRID, PLAN_CGRID = 0, 2, 3
 
 
@@ -144,6 +145,16 @@ def load(path=LIB_PATH):
     L.fv3_autotune.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp, C.POINTER(d)]
     L.fv3_mlp_forward.restype = st
     L.fv3_mlp_forward.argtypes = [vp, vp, i, i, vp, vp]
+    L.fv3_halo_gather.restype = st
+    L.fv3_halo_gather.argtypes = [vp, i, vp, vp, C.c_int64, vp, vp]
+    L.fv3_halo_scatter.restype = st
+    L.fv3_halo_scatter.argtypes = [vp, i, vp, vp, C.c_int64, vp]
+    L.fv3_halo_copy.restype = st
+    L.fv3_halo_copy.argtypes = [vp, i, vp, vp, vp, C.c_int64, vp]
+    L.fv3_face_stencils.restype = st
+    L.fv3_face_stencils.argtypes = [vp, vp, i, vp, vp, vp, vp, vp]
+    L.fv3_learned_faces.restype = st
+    L.fv3_learned_faces.argtypes = [vp, vp, vp, i, vp, vp]
     L.fv3_mlp_work_floats.restype = C.c_size_t
     L.fv3_mlp_work_floats.argtypes = [i]
     L.fv3_mlp_grad.restype = st
@@ -456,6 +467,72 @@ def mlp_forward(w, x, symmetric=True, stream=None):
     _chk(L.fv3_mlp_forward(C.c_void_p(w.data_ptr()), C.c_void_p(x.data_ptr()), n, int(symmetric),
                            C.c_void_p(y.data_ptr()), _stream(stream)), "fv3_mlp_forward")
     return y
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def face_stencils(q6, cr=None, plain=True, edge=False, inputs=False, stream=None):
+    """Face arithmetic of the FP64 transport on single stencils (fv3_face_stencils).
+    q6: cuda float64[n, 6]; cr: cuda float64[n] (needed for ``plain``).
+    Returns a dict with the requested ``plain``, ``edge`` (float64[n]) and
+    ``x`` (float32[n, 6]), ``sig`` (float32[n])."""
+    import torch
+    L = load()
+    q6 = q6.contiguous()
+    n = q6.shape[0]
+    out = {}
+    dev = q6.device
+    if plain:
+        out["plain"] = torch.empty(n, dtype=torch.float64, device=dev)
+    if edge:
+        out["edge"] = torch.empty(n, dtype=torch.float64, device=dev)
+    if inputs:
+        out["x"] = torch.empty((n, 6), dtype=torch.float32, device=dev)
+        out["sig"] = torch.empty(n, dtype=torch.float32, device=dev)
+    _chk(L.fv3_face_stencils(_ptr(q6), _ptr(cr.contiguous()) if cr is not None else None, n,
+                             _ptr(out.get("plain")), _ptr(out.get("edge")), _ptr(out.get("x")),
+                             _ptr(out.get("sig")), _stream(stream)), "fv3_face_stencils")
+    return out
+
+
+def halo_gather(field, src, sign=None, stream=None):
+    """message = sign * field.view(-1)[src] on the device (fv3_halo_gather);
+    src: cuda int64, sign: cuda int8 or None"""
+    import torch
+    L = load()
+    out = torch.empty(src.numel(), dtype=field.dtype, device=field.device)
+    _chk(L.fv3_halo_gather(_ptr(field), field.element_size(), _ptr(src), _ptr(sign), src.numel(), _ptr(out),
+                           _stream(stream)), "fv3_halo_gather")
+    return out
+
+
+def halo_scatter(field, dst, values=None, stream=None):
+    """field.view(-1)[dst] = values (NaN when values is None) on the device"""
+    L = load()
+    _chk(L.fv3_halo_scatter(_ptr(field), field.element_size(), _ptr(dst), _ptr(values), dst.numel(),
+                            _stream(stream)), "fv3_halo_scatter")
+
+
+def halo_copy(field, src, dst, sign=None, stream=None):
+    """field.view(-1)[dst] = sign * field.view(-1)[src] on the device (dst and
+    src disjoint)"""
+    L = load()
+    _chk(L.fv3_halo_copy(_ptr(field), field.element_size(), _ptr(src), _ptr(dst), _ptr(sign), src.numel(),
+                         _stream(stream)), "fv3_halo_copy")
+
+
+def learned_faces(w, q6, cr, stream=None):
+    """learned face values of stencils q6 [n, 6] (cuda float64) at Courant
+    numbers cr [n] with network w (cuda float32[1313]) -> cuda float64[n]"""
+    import torch
+    L = load()
+    q6, cr = q6.contiguous(), cr.contiguous()
+    v = torch.empty(q6.shape[0], dtype=torch.float64, device=q6.device)
+    _chk(L.fv3_learned_faces(_ptr(w), _ptr(q6), _ptr(cr), q6.shape[0], _ptr(v), _stream(stream)),
+         "fv3_learned_faces")
+    return v
 
 
 class MlpTrainer:

@@ -59,51 +59,26 @@ def interior_face(g, t, kind, member=0):
 
 def normalise(st):
     """network inputs x [S, 6] (float) and sigma [S] of six-cell stencils
-    st [S, 6] (float64), as the kernels form them (reading R14)"""
-    import torch
-    r = 0.5 * (st[:, 2] + st[:, 3])
-    d = (st - r[:, None]).float()
-    sixth = torch.tensor(1.0 / 6.0, dtype=torch.float32, device=st.device)
-    m = ((d[:, 0] + d[:, 5]) + (d[:, 1] + d[:, 4]) + (d[:, 2] + d[:, 3])) * sixth
-    e = d - m[:, None]
-    sq = e * e
-    v = ((sq[:, 0] + sq[:, 5]) + (sq[:, 1] + sq[:, 4]) + (sq[:, 2] + sq[:, 3])) * sixth
-    sig = torch.sqrt(v)
-    return e / (sig + 1e-30)[:, None], sig
+    st [S, 6] (float64, on the device), formed by the library's kernels
+    (fv3_face_stencils, reading R14)"""
+    out = fv3.face_stencils(st, plain=False, inputs=True)
+    return out["x"], out["sig"]
 
 
 def plain_face(st, c):
     """plain PPM face value (reading R4) between st[:, 2] and st[:, 3] for
-    Courant numbers c [S] (float64)"""
+    Courant numbers c [S] (float64, on the device), from the library's kernels"""
+    return fv3.face_stencils(st, c)["plain"]
+
+
+def edge_at(q, fi, dim):
+    """fine clamped fourth-order edge values (reading R4, step 1) between
+    cells fi - 1 and fi along ``dim`` (-1 = x, -2 = y), from the library's
+    kernels; the result has the indices fi in place of ``dim``"""
     import torch
-
-    def edge(qm, q0, q1, qp):
-        al = 7.0 / 12.0 * (q0 + q1) - 1.0 / 12.0 * (qm + qp)
-        return torch.minimum(torch.maximum(al, torch.minimum(q0, q1)), torch.maximum(q0, q1))
-
-    aL = edge(st[:, 0], st[:, 1], st[:, 2], st[:, 3])
-    aC = edge(st[:, 1], st[:, 2], st[:, 3], st[:, 4])
-    aR = edge(st[:, 2], st[:, 3], st[:, 4], st[:, 5])
-    pos = c > 0
-    qu = torch.where(pos, st[:, 2], st[:, 3])
-    bl = torch.where(pos, aL, aC) - qu
-    br = torch.where(pos, aC, aR) - qu
-    flat = bl * br >= 0
-    cut_l = ~flat & (bl.abs() > 2 * br.abs())
-    cut_r = ~flat & ~cut_l & (br.abs() > 2 * bl.abs())
-    bl, br = torch.where(flat, 0.0, torch.where(cut_l, -2 * br, bl)), torch.where(flat, 0.0, torch.where(cut_r, -2 * bl, br))
-    ac = c.abs()
-    x = torch.where(pos, br, bl)
-    return qu + (1 - ac) * (x - ac * (bl + br))
-
-
-def edge_values(q, dim):
-    """fine PPM edge values (clamped 4th-order interpolation) between cells
-    i-1 and i along `dim` (last = x, -2 = y), for i = 2 .. n-2"""
-    import torch
-    qm2, qm1, q0, qp1 = (q.narrow(dim, s, q.shape[dim] - 3) for s in range(4))
-    al = 7.0 / 12.0 * (qm1 + q0) - 1.0 / 12.0 * (qm2 + qp1)
-    return torch.minimum(torch.maximum(al, torch.minimum(qm1, q0)), torch.maximum(qm1, q0))
+    st = torch.stack([q.index_select(dim, fi + s) for s in range(-2, 2)], -1)   # cells fi-2 .. fi+1
+    q6 = torch.cat([st[..., :1], st, st[..., 3:]], -1)       # the edge reads the middle four
+    return fv3.face_stencils(q6.reshape(-1, 6), plain=False, edge=True)["edge"].reshape(st.shape[:-1])
 
 
 def coarsen(fine, area, r, weight=None):
@@ -135,11 +110,11 @@ def samples_from_snapshot(fields, winds, area, dxf, dyf, r, rng, per_field, dt=2
     m = n // r
     dxc = r * float(torch.sqrt(area.mean()))      # coarse cell width for the Courant estimate
     xs, ts = [], []
-    dpe_x = edge_values(dp, -1)   # fine faces i = 2 .. n-2 along x
-    dpe_y = edge_values(dp, -2)
-    # normal winds on fine x-faces (from u) and y-faces (from v), coarse-face means
     I_ = torch.arange(3, m - 2, device=dp.device)
     fi = r * I_
+    dpe_x = edge_at(dp, fi, -1)   # fine x-faces fi: [nt, nz, n, nI]
+    dpe_y = edge_at(dp, fi, -2)   # fine y-faces fi: [nt, nz, nI, n]
+    # normal winds on fine x-faces (from u) and y-faces (from v), coarse-face means
     ucx = 0.25 * (u[..., :-1, fi - 1] + u[..., :-1, fi] + u[..., 1:, fi - 1] + u[..., 1:, fi])   # [nt,nz,n,nI]
     ucx = ucx.reshape(nt, nz, m, r, -1).mean(3)                                                    # [nt,nz,m,nI]
     vcy = 0.25 * (v[..., fi - 1, :-1] + v[..., fi - 1, 1:] + v[..., fi, :-1] + v[..., fi, 1:])     # [nt,nz,nJ,n]
@@ -148,22 +123,18 @@ def samples_from_snapshot(fields, winds, area, dxf, dyf, r, rng, per_field, dt=2
         qc = coarse[name]
         for axis in ("x", "y"):
             if axis == "x":
-                al = edge_values(q, -1)          # [.., n, n-3]: face i at index i-2
-                wgt = dyf[None, None, :, 2:n - 1].expand_as(al)
+                a = edge_at(q, fi, -1)                          # [nt, nz, n, nI]
+                wv = dyf[None, None, :, fi].expand_as(a)
                 if name != "delp":
-                    wgt = wgt * dpe_x
-                a = al[..., fi - 2]              # [nt, nz, n, nI]
-                wv = wgt[..., fi - 2]
+                    wv = wv * dpe_x
                 a = (a * wv).reshape(nt, nz, m, r, -1).sum(3) / wv.reshape(nt, nz, m, r, -1).sum(3)
                 st = torch.stack([qc[..., :, I_ + s] for s in range(-3, 3)], -1)   # [nt, nz, m, nI, 6]
                 c = dt * ucx / dxc
             else:
-                al = edge_values(q, -2)          # [.., n-3, n]
-                wgt = dxf[None, None, 2:n - 1, :].expand_as(al)
+                a = edge_at(q, fi, -2)                          # [nt, nz, nJ, n]
+                wv = dxf[None, None, fi, :].expand_as(a)
                 if name != "delp":
-                    wgt = wgt * dpe_y
-                a = al[..., fi - 2, :]           # [nt, nz, nJ, n]
-                wv = wgt[..., fi - 2, :]
+                    wv = wv * dpe_y
                 a = (a * wv).reshape(nt, nz, -1, m, r).sum(4) / wv.reshape(nt, nz, -1, m, r).sum(4)
                 st = torch.stack([qc[..., I_ + s, :] for s in range(-3, 3)], -1)   # [nt, nz, nJ, m, 6]
                 c = dt * vcy / dxc

@@ -39,3 +39,22 @@ def pair(orc, cubed, n, nz, seed=0, nq=0, precision=0, members=None):
     s = orc.State(d, nq)
     s.load(st)
     return g, gs, d, s, st
+
+
+def ulp_sensitivity(orc, st, cubed, n, nz, nq, run, fields, seed=1):
+    """per field, the relative max-norm change of the oracle's result when pt
+    is perturbed by one unit in the last place (random signs): the rounding
+    condition of the computation.  A field formed by cancellation (w after
+    the closed substep: a small difference of pressure perturbations) moves
+    by far more than 1e-16 under any change of rounding, so two correct
+    implementations can differ by that much."""
+    out = []
+    rng = np.random.default_rng(seed)
+    for eps in (0.0, 1.0):
+        s = orc.State(orc.Domain(cubed, n, nz), nq)
+        st2 = dict(st)
+        st2["pt"] = st["pt"] * (1 + eps * 2.220446049250313e-16 * rng.choice([-1.0, 1.0], st["pt"].shape))
+        s.load(st2)
+        run(s)
+        out.append({f: s.get(f) for f in fields})
+    return {f: relerr(out[1][f], out[0][f]) for f in fields}, out[0]

@@ -1,8 +1,8 @@
 """Halo exchange between ranks holding different tiles (Section V-C: the
 halo exchange with the orientation transform between cube faces), on the CPU:
 the host-built plan of fv3_halo_plan applied on one rank reproduces the
-oracle's halo fill slot by slot; split over two gloo ranks (tiles 0-2 and 3-5)
-it gives the same fields; and a rank that never joins makes the other rank's
+oracle's halo fill slot by slot; split over two gloo ranks (tiles 0-2 and 3-5,
+or interleaved 0, 2, 4 and 1, 3, 5) it gives the same fields; and a rank that never joins makes the other rank's
 exchange fail within its timeout instead of hanging."""
 import os
 import socket
@@ -91,7 +91,7 @@ def _free_port():
     return port
 
 
-def _rank(rank, ws, port, kind, vector, out, join=True):
+def _rank(rank, ws, port, kind, vector, out, join=True, owner=(0, 0, 0, 1, 1, 1)):
     import datetime
 
     import torch
@@ -100,8 +100,7 @@ def _rank(rank, ws, port, kind, vector, out, join=True):
     dist.init_process_group("gloo", rank=rank, world_size=ws, timeout=datetime.timedelta(seconds=20))
     from paper_2205_04148_gb300 import exchange, fv3
     entries, lay = fv3.halo_plan(fv3.GRID_CUBED, N, NZ, kind=kind)
-    owner = [0, 0, 0, 1, 1, 1]
-    X = exchange.TileExchange(entries, owner, rank, NZ, lay.plane, vector=vector)
+    X = exchange.TileExchange(entries, list(owner), rank, NZ, lay.plane, vector=vector)
     buf, _ = _fields(lay, vector, 5)
     mine = torch.from_numpy(np.ascontiguousarray(buf[:, X.tiles]))
     try:
@@ -118,11 +117,11 @@ def _rank(rank, ws, port, kind, vector, out, join=True):
     dist.destroy_process_group()
 
 
-def _spawn(kind, vector, joins):
+def _spawn(kind, vector, joins, owner=(0, 0, 0, 1, 1, 1)):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, kind, vector, q, joins[r])) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, kind, vector, q, joins[r], owner)) for r in range(2)]
     for p in procs:
         p.start()
     try:
@@ -139,19 +138,21 @@ def _spawn(kind, vector, joins):
     return res
 
 
+@pytest.mark.parametrize("owner", [(0, 0, 0, 1, 1, 1), (0, 1, 0, 1, 0, 1)])
 @pytest.mark.parametrize("kind_name,vector", [("PLAN_CELL", False), ("PLAN_DGRID", True), ("PLAN_CGRID", True)])
-def test_two_ranks_equal_one(kind_name, vector):
+def test_two_ranks_equal_one(kind_name, vector, owner):
     import torch
 
     from paper_2205_04148_gb300 import exchange, fv3
     kind = getattr(fv3, kind_name)
-    res = _spawn(kind, vector, (True, True))
+    res = _spawn(kind, vector, (True, True), owner)
     entries, lay = _plan(kind)
     buf, _ = _fields(lay, vector, 5)
     whole = torch.from_numpy(buf.copy())
     exchange.TileExchange(entries, [0] * 6, 0, NZ, lay.plane, vector=vector).run(whole)
     whole = whole.numpy()
-    for r, tiles in ((0, [0, 1, 2]), (1, [3, 4, 5])):
+    for r in (0, 1):
+        tiles = [t for t in range(6) if owner[t] == r]
         status, data = res[r]
         assert status == "ok", data
         assert np.array_equal(np.isnan(data), np.isnan(whole[:, tiles]))

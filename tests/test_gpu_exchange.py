@@ -48,3 +48,52 @@ def test_host_plan_is_the_device_plan(precision):
             assert np.array_equal(np.isnan(got), np.isnan(want)), f
             fin = np.isfinite(want)
             assert np.array_equal(got[fin], want[fin]), f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("owner", [[0, 0, 0, 1, 1, 1], [0, 1, 0, 1, 0, 1], [0, 1, 2, 0, 1, 2]])
+def test_device_pack_unpack_reproduces_halo_fill(precision, owner):
+    """The device side of the exchange (fv3_halo_gather / fv3_halo_copy /
+    fv3_halo_scatter) on one GPU: the ranks' parts of the plan, each on its
+    own device buffer, with every message gathered by one rank's kernel and
+    scattered by the receiver's (handed over directly, no transport), fill
+    the halo slots exactly as fv3_halo_fill does"""
+    import torch
+
+    from paper_2205_04148_gb300 import exchange, fv3
+    prec = fv3.FP64 if precision == "fp64" else fv3.FP32
+    n, nz = 12, 3
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=prec)
+    st = seeded(True, n, nz, 6, 0)
+    gs = g.alloc_state()
+    g.load(gs, st)
+    lay = g.layout(0)
+    P = lay.plane
+
+    def planes(t):
+        return t.view(-1)[lay.offset3:lay.offset3 + 6 * nz * P].view(6, nz, P).clone()
+
+    before = {f: planes(gs[f]) for f in ("delp", "u", "v")}
+    g.halo_fill(gs, fv3.HALO_WIND | fv3.HALO_DELP)
+    after = {f: planes(gs[f]).cpu().numpy() for f in ("delp", "u", "v")}
+    ranks = sorted(set(owner))
+    for kind, fields in ((fv3.PLAN_CELL, ("delp",)), (fv3.PLAN_DGRID, ("v", "u"))):
+        e, _ = fv3.halo_plan(fv3.GRID_CUBED, n, nz, kind=kind, precision=prec)
+        X = {r: exchange.TileExchange(e, owner, r, nz, P, vector=len(fields) == 2) for r in ranks}
+        bufs = {r: torch.stack([before[f][X[r].tiles] for f in fields]).contiguous() for r in ranks}
+        msgs = {r: X[r].pack(bufs[r]) for r in ranks}
+        for r in ranks:
+            X[r].local(bufs[r])
+        for src in ranks:
+            for dst, m in msgs[src].items():
+                assert m.is_cuda and m.dtype == bufs[dst].dtype
+                X[dst].unpack(bufs[dst], src, m)
+        torch.cuda.synchronize()
+        dst_slots = np.unique(e["dst"])
+        for r in ranks:
+            got_all = bufs[r].cpu().numpy()
+            for a, f in enumerate(fields):
+                got, want = got_all[a][:, :, dst_slots], after[f][X[r].tiles][:, :, dst_slots]
+                assert np.array_equal(np.isnan(got), np.isnan(want)), (r, f)
+                fin = np.isfinite(want)
+                assert np.array_equal(got[fin], want[fin]), (r, f)

@@ -6,7 +6,7 @@ steps, size limits)."""
 import numpy as np
 import pytest
 
-from gpu_common import FIELDS, TOL64, relerr
+from gpu_common import FIELDS, TOL64, relerr, ulp_sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -115,7 +115,10 @@ def test_c96x80_fp64_all_options_step(orc):
     """One remapping step of the C96 x 80 FP64 state with every physics option
     the bench can switch on (closed substep, vertical remapping, divergence
     damping, fourth-order C-grid winds), in the bench's launch configuration,
-    against the oracle on every element of every field."""
+    against the oracle on every element of every field.  Bound per field: 1e-12,
+    or four times the oracle's own change under a one-ulp perturbation of its
+    inputs where that is larger (w after the closed substep, formed by
+    cancellation, moves by about 1e-12 under any change of rounding)."""
     from paper_2205_04148_gb300 import fv3
     from paper_2205_04148_gb300 import inputs as I
     n, nz, nq = 96, 80, 2
@@ -127,9 +130,10 @@ def test_c96x80_fp64_all_options_step(orc):
     g.set_tiles(16, 16, 1)
     g.set_persistent(True)
     g.run_dyn(gs, fv3.params(n_split=6, **opts), 1)
-    s = orc.State(orc.Domain(True, n, nz), nq)
-    s.load(st)
-    s.run_dyn(orc.params(n_split=6, **opts), 1)
-    for f in FIELDS + ("delz", "q0", "q1"):
-        e = relerr(g.read(gs, f), s.get(f))
-        assert e <= TOL64, (f, e)
+    fields = FIELDS + ("delz", "q0", "q1")
+    sens, want = ulp_sensitivity(orc, st, True, n, nz, nq, lambda s: s.run_dyn(orc.params(n_split=6, **opts), 1),
+                                 fields)
+    for f in fields:
+        e = relerr(g.read(gs, f), want[f])
+        assert e <= max(TOL64, 4 * sens[f]), (f, e, sens[f])
+    assert sens["w"] < 1e-10            # the conditioning stays what it is

@@ -74,17 +74,36 @@ def test_constant_output_correction_closed_form(orc):
 
 
 def test_normalised_inputs(orc):
+    # FP64 definition (reading R14): sigma is the population standard
+    # deviation, x (sigma + 1e-12 |mean|) the deviations from the mean
     rng = np.random.default_rng(22)
     q = 1000.0 + rng.standard_normal((200, 6)) * 10.0 ** rng.uniform(-6, 2, (200, 1))
     x, sig = orc.mlp_normalise(q)
-    assert np.abs(x.mean(-1)).max() < 1e-5
-    assert np.abs(np.sqrt((x.astype(np.float64) ** 2).mean(-1)) - 1).max() < 1e-5
-    assert np.allclose(sig, q.std(-1), rtol=1e-4)
+    mu = q.mean(-1)
+    assert np.abs(sig - q.std(-1)).max() <= 1e-9 * sig.min() + 1e-13 * np.abs(mu).max()
+    dev = x * (sig + 1e-12 * np.abs(mu))[:, None]
+    assert np.abs(dev - (q - mu[:, None])).max() <= 1e-12 * np.abs(mu).max()
+    assert (np.abs(x.mean(-1)) <= 1e-14 * np.abs(mu) / sig).all()   # cancellation in q - mean
     xr, sigr = orc.mlp_normalise(q[:, ::-1])
     assert np.array_equal(xr, x[:, ::-1]) and np.array_equal(sigr, sig)
-    # a constant stencil has no deviation and zero inputs
+    # a constant stencil: no deviation beyond the rounding of its mean, and
+    # eps keeps the inputs near zero
     x0, s0 = orc.mlp_normalise(np.full((1, 6), 3.7))
-    assert s0[0] == 0 and not x0.any()
+    assert s0[0] <= 4e-16 * 3.7 and np.abs(x0).max() <= 1e-3
+
+
+def test_learned_candidate_and_decision(orc):
+    # the candidate is plain + sigma y (output-bias network: y = beta) and the
+    # fallback keeps it exactly when it lies in the range of the two cells
+    w = np.zeros(orc.MLP_NP)
+    q6 = np.array([1.0, 2.0, 2.5, 3.5, 4.0, 5.0])
+    x, sig = orc.mlp_normalise(q6)
+    for beta, keep in ((0.2, True), (0.9, False), (-0.9, False)):
+        w[1312] = beta
+        a, acc = orc.learned_candidate(w, q6, 0.3)
+        assert abs(a - (orc.ppm_face(q6, 0.3) + beta * sig)) <= 1e-14
+        assert acc == keep == (2.5 <= a <= 3.5)
+        assert orc.learned_face(w, q6, 0.3) == (a if keep else orc.ppm_face(q6, 0.3))
 
 
 def test_fallbacks(orc):
