@@ -18,8 +18,12 @@ timed region.
 Before timing, the block shape, level chunk and launch mode are autotuned
 (fv3_autotune; --tiles or --no-autotune to fix them).  Beside the timed
 region: the dominant kernel (d_sw) timed alone for the roofline object, an
-end-to-end pass through the C-ABI with host buffers (e2e), and the CPU oracle
-on a level subset of the same remapping step (cpu_baseline).  Other
+end-to-end pass through the C-ABI with host buffers (e2e), the CPU oracle
+on a level subset of the same remapping step (cpu_baseline), and two
+sub-records of the other forms (skipped with --no-extra): ``fp32_c192`` (FP32
+bulk on C192 against the plain FP64 GPU path: both rates, the speed-up and
+the per-field error after 1 and 100 substeps) and ``batched`` (the 24-member
+ensemble in one launch per stage against its members one at a time).  Other
 workloads: --precision fp32 --npx 192 (FP32 bulk), --workload batched (the
 24-member ensemble), --workload modules (riem_solver_c and fv_tp_2d alone).
 
@@ -53,13 +57,28 @@ DSW_FLOPS_PER_CELL = 655
 # uc, vc and writes u, v, w, delp, pt (12 words).
 DSW_WORDS_PER_CELL = 12
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
-# DRAM bytes (read + write) per cell of one d_sw launch, from ncu captures of
-# the kernel in these launch configurations (profiles/k_d_sw_fp64_c96x24.md:
-# C96 x 24, FP64, 16 x 16 blocks, one level per work item, persistent grid;
-# profiles/k_d_sw_fp32_c192x16.md: C192 x 16, FP32, 32 x 8 blocks, four levels
-# per work item); scaled by the cells of the timed launch (the traffic grows in
-# proportion to the work items).  Other configurations report null.
-DSW_TRAFFIC_BYTES_PER_CELL = {("f64", 16, 16, 1, True): 197.9, ("f32", 32, 8, 4, False): 103.7}
+# DRAM bytes (read + write) per cell of one d_sw launch come from ncu
+# captures of the kernel in given launch configurations (precision, block
+# shape, level chunk, launch mode), recorded with the source commit of the
+# capture in profiles/dram_traffic.json; the roofline object scales them by
+# the cells of the timed launch (the traffic grows in proportion to the work
+# items) and says so.  A configuration without a capture reports null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def dram_traffic(kernel, prec, bx, by, kc, persistent, cells):
+    """(bytes per launch scaled from a capture, the capture's record) or (None, None)"""
+    try:
+        caps = json.load(open(TRAFFIC_FILE))["captures"]
+    except (OSError, ValueError, KeyError):
+        return None, None
+    for c in caps:
+        if (c["kernel"], c["precision"], c["bx"], c["by"], c["kchunk"], bool(c["persistent"])) == \
+                (kernel, prec, bx, by, kc, bool(persistent)):
+            rec = {k: c[k] for k in ("bytes_per_cell", "capture_cells", "capture", "commit") if k in c}
+            rec["scaled"] = "bytes per cell of the capture x cells of the timed launch"
+            return c["bytes_per_cell"] * cells, rec
+    return None, None
 
 
 def parse():
@@ -80,6 +99,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the FP32-bulk C192 and batched-ensemble sub-records of the default FP64 C96 line")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default block shape (32 x 8, 8 levels per CTA, one CTA per item)")
     p.add_argument("--nh-full", action="store_true", help="close each substep (update_dz_d, riem_solver3, "
@@ -144,6 +165,14 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline denominator"""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured hbm_gbs"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s of the profiling recipe"
 
 
 # ---------------------------------------------------------------------------
@@ -231,7 +260,11 @@ def reference_arm(a):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "cubed-sphere C%d x %d levels, FP64, n_split %d, %d tracers, one remapping "
                                   "step per bench step" % (a.npx, a.npz, a.n_split, a.nq),
-                      "sample_levels": nzs, "options": options},
+                      "sample_levels": nzs, "levels": a.npz, "options": options,
+                      "same_config": nzs == a.npz,
+                      "sampling": "the oracle runs %d of the %d levels per replica; value is its cell-substeps/s "
+                                  "on that sample (levels are independent in the horizontal stages, the column "
+                                  "solve's cost grows linearly with them)" % (nzs, a.npz)},
            "cpu_baseline": {"value": value, "unit": METRIC, "cores": procs, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -338,25 +371,24 @@ def ours(a):
     fp64_meas = work.value * 3 / (c0.elapsed_time(c1) / 1e3) / 1e9
     esize = 8 if prec == fv3.FP64 else 4
     bx, by, kc = g.tiles()
-    tkey = ("f64" if prec == fv3.FP64 else "f32", bx, by, kc, g.persistent())
-    traffic = DSW_TRAFFIC_BYTES_PER_CELL[tkey] * cells if tkey in DSW_TRAFFIC_BYTES_PER_CELL else None
+    pname = "f64" if prec == fv3.FP64 else "f32"
+    traffic, traffic_rec = dram_traffic("k_d_sw", pname, bx, by, kc, g.persistent(), cells)
+    hbm, hbm_src = hbm_peak()
+    hbm_ach = DSW_WORDS_PER_CELL * esize * cells / t_dsw / 1e9
+    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
+               "bytes_per_cell": DSW_WORDS_PER_CELL * esize, "peak_source": hbm_src}
     if prec == fv3.FP64:
         ach = DSW_FLOPS_PER_CELL * cells / t_dsw / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
-                "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": traffic, "kernel": "k_d_sw<double>",
+                "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": traffic, "traffic_capture": traffic_rec,
+                "kernel": "k_d_sw<double>",
                 "ms_per_launch": t_dsw * 1e3, "flops_per_cell": DSW_FLOPS_PER_CELL,
                 "peak_measured_fma": fp64_meas,
-                "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it"}
+                "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it",
+                "hbm": hbm_obj}
     else:
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except Exception:
-            pass
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        ach = DSW_WORDS_PER_CELL * esize * cells / t_dsw / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
-                "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3}
+        roof = dict(hbm_obj, traffic=traffic, traffic_capture=traffic_rec, kernel="k_d_sw<float>",
+                    ms_per_launch=t_dsw * 1e3)
 
     # --- end to end through the C-ABI with host buffers ------------------
     # Every step imports its inputs from page-locked host memory and exports
@@ -474,7 +506,18 @@ def ours(a):
                "sample": "one remapping step (%d acoustic substeps + tracer_2d of %d tracers) of C%d x %d levels "
                          "(of %d) per replica, FP64 oracle, %d one-thread replicas side by side (%.1f s)"
                          % (a.n_split, a.nq, a.npx, nzs, a.npz, procs, dt),
-               "single_thread": {"value": rate1, "cores": 1, "seconds": dt1}}
+               "single_thread": {"value": rate1, "cores": 1, "seconds": dt1},
+               "same_config": nzs == a.npz, "sample_levels": nzs}
+
+    # --- the other forms at N = 1: FP32 bulk on C192 and the batched ensemble
+    extra = {}
+    if ws == 1 and not a.no_extra and prec == fv3.FP64 and a.npx == 96:
+        t = time.perf_counter()
+        extra["fp32_c192"] = fp32_record(a, max(3, a.steps // 2))
+        extra["fp32_c192"]["record_s"] = time.perf_counter() - t
+        t = time.perf_counter()
+        extra["batched"] = batched_measure(a, ws, rank, max(3, a.steps // 4), local)
+        extra["batched"]["record_s"] = time.perf_counter() - t
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps,
@@ -489,6 +532,7 @@ def ours(a):
                           "parallelism": "replicas" if ws > 1 else "single GPU"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "status": status}
+        out.update(extra)
         print(json.dumps(out), flush=True)
     replicas.finish()
     return 0
@@ -510,24 +554,19 @@ def _time_steps(g, gs, prm, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def batched(a):
+def batched_measure(a, ws, rank, steps, local=0):
     """The batched ensemble: 24 members of mixed resolution in one context,
     every stage one launch over the work list of all members (persistent or
     one CTA per item, as tuned), the n_split loop replayed from a CUDA graph.
     Tile shape, level chunk and launch mode are tuned on a single C96 member
     and transferred.  Beside it: the same members advanced one at a time by
-    the plain FP64 path and by the FP32 path, for the speed-ups."""
+    the plain FP64 path and by the FP32 path, each size autotuned alone, for
+    the speed-ups.  Returns a dict of the measurements."""
     import ctypes as C
 
     import torch
 
-    from paper_2205_04148_gb300 import replicas
-    ws, rank, local = replicas.init("nccl")
-    if ws == 1:
-        torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import fv3, replicas
     from paper_2205_04148_gb300 import inputs as I
 
     nz = a.npz
@@ -565,7 +604,7 @@ def batched(a):
     torch.cuda.synchronize()
     clocks.start()
     l0 = L.fv3_kernel_launches(g.ptr)
-    ms_step = _time_steps(g, gs, prm, a.steps, stream)
+    ms_step = _time_steps(g, gs, prm, steps, stream)
     replicas.barrier()
     clk = clocks.stop()
     launches = L.fv3_kernel_launches(g.ptr) - l0
@@ -590,15 +629,10 @@ def batched(a):
     g.close()
     del gs
     torch.cuda.empty_cache()
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm, hbm_src = hbm_peak()
     ach = DSW_WORDS_PER_CELL * 4 * cells / t_dsw / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3, "peak_source": "measured hbm_gbs"}
+            "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3, "peak_source": hbm_src}
 
     # the same members one at a time: plain FP64 path and FP32 path
     per_member = {}
@@ -612,31 +646,105 @@ def batched(a):
             for _ in range(2):
                 g1.run_dyn(s1, prm, 1)
             torch.cuda.synchronize()
-            tot += sizes.count(n) * _time_steps(g1, s1, prm, max(3, a.steps // 2), stream)
+            tot += sizes.count(n) * _time_steps(g1, s1, prm, max(3, steps // 2), stream)
             g1.close()
             del s1
             torch.cuda.empty_cache()
         per_member[label] = tot
+    return {"value": value, "ms_per_step": ms_step, "cells": cells, "members": len(sizes),
+            "tiles": {"bx": bx, "by": by, "kchunk": kc, "persistent": pers,
+                      "tuned_on": "single C96 member (transferred)", "tuned_ms": tuned_ms},
+            "speedup": {"vs_fp64_one_member_at_a_time": per_member["fp64"] / ms_step,
+                        "vs_fp32_one_member_at_a_time": per_member["fp32"] / ms_step,
+                        "fp64_one_at_a_time_ms_per_step": per_member["fp64"],
+                        "fp32_one_at_a_time_ms_per_step": per_member["fp32"]},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk, "status": status}
+
+
+def batched(a):
+    """--workload batched: the ensemble's own bench line"""
+    import torch
+
+    from paper_2205_04148_gb300 import replicas
+    ws, rank, local = replicas.init("nccl")
+    if ws == 1:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    r = batched_measure(a, ws, rank, a.steps, local)
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps,
-               "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        out = {"metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32 (column solve f64)", "data": "synthetic",
                "config": {"workload": "batched ensemble 8 x C48 + 8 x C96 + 8 x C128, %d levels, FP32 bulk, "
-                                      "n_split %d, perturbations 1%% delp and 1 m/s wind" % (nz, a.n_split),
-                          "members": len(sizes), "cells": cells, "substeps_per_step": a.n_split,
-                          "l2": "inputs larger than L2",
-                          "tiles": {"bx": bx, "by": by, "kchunk": kc, "persistent": pers,
-                                    "tuned_on": "single C96 member (transferred)", "tuned_ms": tuned_ms},
+                                      "n_split %d, perturbations 1%% delp and 1 m/s wind" % (a.npz, a.n_split),
+                          "members": r["members"], "cells": r["cells"], "substeps_per_step": a.n_split,
+                          "l2": "inputs larger than L2", "tiles": r["tiles"],
                           "parallelism": "replicas" if ws > 1 else "single GPU"},
-               "speedup": {"vs_fp64_one_member_at_a_time": per_member["fp64"] / ms_step,
-                           "vs_fp32_one_member_at_a_time": per_member["fp32"] / ms_step,
-                           "fp64_one_at_a_time_ms_per_step": per_member["fp64"],
-                           "fp32_one_at_a_time_ms_per_step": per_member["fp32"]},
-               "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
-               "clocks": clk, "status": status}
+               "speedup": r["speedup"], "roofline": r["roofline"], "cpu_baseline": None, "e2e": None,
+               "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "status": r["status"]}
         print(json.dumps(out), flush=True)
     replicas.finish()
     return 0
+
+
+ERROR_FIELDS = ("u", "v", "w", "delp", "pt", "delz")
+
+
+def fp32_record(a, steps):
+    """FP32 bulk against the plain FP64 GPU path on the C192 x npz state with
+    the bench's tracers (each autotuned alone): device rate of each, the
+    speed-up, and the per-field relative max-norm error of the FP32 fields
+    against the FP64 GPU path (which matches the oracle to 1e-12 per substep)
+    after 1 and 100 substeps from the same initial state."""
+    import numpy as np
+    import torch
+
+    from paper_2205_04148_gb300 import fv3
+    from paper_2205_04148_gb300 import inputs as I
+
+    npx, nz = 192, a.npz
+    st = I.cubed_state(npx, nz, seed=0, ntracers=a.nq)
+    prm = fv3.params(n_split=a.n_split)
+    cells = 6 * npx * npx * nz
+    stream = torch.cuda.current_stream()
+    res = {}
+    for label, prec in (("fp32", fv3.FP32), ("fp64", fv3.FP64)):
+        g = fv3.Grid(fv3.GRID_CUBED, npx, nz, precision=prec)
+        gs = g.alloc_state(a.nq)
+        g.load(gs, st)
+        (bx, by, kc), _ = g.autotune(gs, prm)
+        g.load(gs, st)
+        for _ in range(2):
+            g.run_dyn(gs, prm, 1)
+        torch.cuda.synchronize()
+        ms = _time_steps(g, gs, prm, steps, stream)
+        g.load(gs, st)
+        g.substep(gs, prm)
+        f1 = {f: g.read(gs, f) for f in ERROR_FIELDS}
+        for _ in range(99):
+            g.substep(gs, prm)
+        f100 = {f: g.read(gs, f) for f in ERROR_FIELDS}
+        res[label] = {"ms": ms, "f1": f1, "f100": f100, "tiles": [bx, by, kc, g.persistent()]}
+        g.close()
+        del gs
+        torch.cuda.empty_cache()
+
+    def rel(x, y):
+        den = float(np.abs(y).max())
+        return float(np.abs(x - y).max()) / den if den > 0 else float(np.abs(x - y).max())
+
+    r32, r64 = res["fp32"], res["fp64"]
+    return {"workload": "cubed-sphere C%d x %d levels, %d tracers, n_split %d, one remapping step per bench step"
+                        % (npx, nz, a.nq, a.n_split),
+            "value": a.n_split * cells / (r32["ms"] / 1e3), "unit": METRIC, "ms_per_step": r32["ms"],
+            "fp64_value": a.n_split * cells / (r64["ms"] / 1e3), "fp64_ms_per_step": r64["ms"],
+            "speedup_vs_fp64": r64["ms"] / r32["ms"], "steps": steps,
+            "tiles": {"fp32": r32["tiles"], "fp64": r64["tiles"]},
+            "rel_error_vs_fp64_gpu": {"after_1_substep": {f: rel(r32["f1"][f], r64["f1"][f]) for f in ERROR_FIELDS},
+                                      "after_100_substeps": {f: rel(r32["f100"][f], r64["f100"][f])
+                                                             for f in ERROR_FIELDS}},
+            "error_definition": "max |fp32 - fp64| / max |fp64| per field (w: absolute where fp64 w is 0)"}
 
 
 # the paper's module timings (Table II; P100, GT4Py + DaCe, FP64, 192 x 192 x 80 per GPU)
