@@ -26,9 +26,12 @@
  *    thickness (Pa), delz the (negative) layer height thickness (m), k = 0 the
  *    model top.  Faces on a tile edge are stored by both tiles; the tile with
  *    the lower index owns them (periodic: faces i = 0, j = 0).
- *  - Element type: double (FV3_FP64) or float (FV3_FP32, "FP32-bulk": all
- *    stencils in FP32, the column solve and global sums in FP64), fixed at
- *    fv3_init_grid.
+ *  - Element type: double (FV3_FP64) or float (FV3_FP32 and FV3_FP32_M64,
+ *    "FP32-bulk": all stencils in FP32, the column solve and global sums in
+ *    FP64), fixed at fv3_init_grid.  FV3_FP32 reads FP32 copies of the metric
+ *    terms (areas, lengths, grid-angle sin/cos, Coriolis); FV3_FP32_M64 keeps
+ *    them in FP64 and forms every product with a metric term in FP64, rounding
+ *    to FP32 where the result is stored.
  *  - Ownership: the caller allocates and owns the state buffers (device
  *    memory, base address aligned to 128 bytes) and the streams; the library
  *    owns the metric terms, halo plans, intermediates, solver scratch and
@@ -67,7 +70,7 @@ typedef enum {
 } fv3_status;
 
 enum { FV3_GRID_PERIODIC = 0, FV3_GRID_CUBED = 1 };
-enum { FV3_FP64 = 0, FV3_FP32 = 1 };
+enum { FV3_FP64 = 0, FV3_FP32 = 1, FV3_FP32_M64 = 2 };
 /* field kinds: cell levels, x-face levels, y-face levels, cell interfaces (nz+1) */
 enum { FV3_KIND_CELL = 0, FV3_KIND_XFACE = 1, FV3_KIND_YFACE = 2, FV3_KIND_IFACE = 3 };
 /* fv3_halo_fill field mask bits */
@@ -86,7 +89,7 @@ typedef struct {
   int npz;               /* vertical levels; >= 2 */
   int n_members;         /* independent states advanced together; >= 1 */
   const int* member_npx; /* host array [n_members] of per-member npx, or NULL */
-  int precision;         /* FV3_FP64 or FV3_FP32 */
+  int precision;         /* FV3_FP64, FV3_FP32 or FV3_FP32_M64 */
   double dx;             /* periodic grid spacing (m) */
   double radius;         /* sphere radius (m), cube only */
   double omega;          /* rotation rate (1/s), cube only */

@@ -19,6 +19,7 @@ LIB = os.path.join(OUT, "libfv3.so")
 SOURCES = [("fv3_grid.cpp", "fv3_grid", ()),
            ("fv3_kernels.cu", "fv3_kernels_f64", ("-DFV3_TU=64",)),
            ("fv3_kernels.cu", "fv3_kernels_f32", ("-DFV3_TU=32",)),
+           ("fv3_kernels.cu", "fv3_kernels_f32m64", ("-DFV3_TU=33",)),
            ("fv3_kernels.cu", "fv3_kernels_main", ("-DFV3_TU=1",)),
            ("fv3_capi.cu", "fv3_capi", ()), ("fv3_calib.cu", "fv3_calib", ()),
            ("fv3_noalloc.cu", "fv3_noalloc", ()), ("fv3_mlp.cu", "fv3_mlp", ()),

@@ -174,7 +174,7 @@ namespace {
 // descriptor checks shared by fv3_init_grid and fv3_halo_plan; npx per member
 fv3_status check_desc(const fv3_grid_desc* d, std::vector<int>& npx) {
   if (d->grid_type != FV3_GRID_PERIODIC && d->grid_type != FV3_GRID_CUBED) return FV3_ERR_ARG;
-  if (d->precision != FV3_FP64 && d->precision != FV3_FP32) return FV3_ERR_ARG;
+  if (d->precision != FV3_FP64 && d->precision != FV3_FP32 && d->precision != FV3_FP32_M64) return FV3_ERR_ARG;
   if (d->n_members < 1 || d->n_members > 4096 || d->npz < 2 || d->npz > 1024) return FV3_ERR_SHAPE;
   if (d->grid_type == FV3_GRID_PERIODIC && !(d->dx > 0)) return FV3_ERR_ARG;
   if (d->grid_type == FV3_GRID_CUBED && (!(d->radius > 0) || !std::isfinite(d->omega))) return FV3_ERR_ARG;

@@ -39,6 +39,7 @@
 #define FV3_TU_MAIN (FV3_TU == 0 || FV3_TU == 1)
 #define FV3_TU_F64 (FV3_TU == 0 || FV3_TU == 64)
 #define FV3_TU_F32 (FV3_TU == 0 || FV3_TU == 32)
+#define FV3_TU_F32M64 (FV3_TU == 0 || FV3_TU == 33)
 
 namespace fv3 {
 
@@ -140,6 +141,14 @@ __device__ __forceinline__ TM<R> tile_metric(const Metric<R>& M, const Geo& g, i
   return m;
 }
 
+// the metric a kernel with metric type MR reads: the FP64 master copy, or
+// the copy in the arithmetic precision
+template <typename MR, typename A>
+__device__ __forceinline__ Metric<MR> metric_sel(const A& a) {
+  if constexpr (sizeof(MR) == 8) return a.Md;
+  else return a.M;
+}
+
 // origin (i = j = 0) of level k of tile t in a [tile][nlev][plane] field
 __device__ __forceinline__ long long fld0(const Geo& g, long long off, int nlev, int t, int k) {
   return off + ((long long)t * nlev + k) * g.plane + (long long)HALO * g.pitch + g.ox;
@@ -229,12 +238,16 @@ __device__ __forceinline__ void corner_roles(R* Q, const Blk& B, int n, int role
 }
 
 // shared-memory arrays of the transport
-template <typename R>
+// MR: the type of the metric terms (R, or double in the FP32-bulk mode that
+// keeps the metric in FP64: every product with a metric term is then formed
+// in FP64 and rounded to R where it is stored)
+template <typename R, typename MR = R>
 struct TS {
-  R *CRX, *XFX, *CRY, *YFX, *RDXd, *RDYd, *FY2, *FX2, *QIJ, *LAP, *AL;
+  R *CRX, *XFX, *CRY, *YFX, *FY2, *FX2, *QIJ, *LAP, *AL;
+  MR *RDXd, *RDYd;
   // metric terms of the block's tile staged in shared memory once per work
   // item (area, 1/area; the damping weights wx, wy in the damped transports)
-  R *AREA, *RAREA, *WX, *WY;
+  MR *AREA, *RAREA, *WX, *WY;
 };
 
 // FP64 kernels keep the reciprocal denominators of the two inner updates in
@@ -251,21 +264,21 @@ template <typename R, bool LEARN>
 constexpr bool kTracerPair = sizeof(R) == 8 && !LEARN;
 
 // 1 / (area + the two area fluxes) of the y- and x-inner updates at l
-template <typename R>
-__device__ __forceinline__ R inner_rdy(const TS<R>& S, int l, int SX) {
+template <typename R, typename MR>
+__device__ __forceinline__ MR inner_rdy(const TS<R, MR>& S, int l, int SX) {
   if constexpr (kStoreRD<R>) return S.RDYd[l];
-  else return rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
+  else return rcp<MR>(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
 }
-template <typename R>
-__device__ __forceinline__ R inner_rdx(const TS<R>& S, int l) {
+template <typename R, typename MR>
+__device__ __forceinline__ MR inner_rdx(const TS<R, MR>& S, int l) {
   if constexpr (kStoreRD<R>) return S.RDXd[l];
-  else return rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
+  else return rcp<MR>(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
 }
 
 // the stored denominators (kStoreRD): y over [x0-3, x1+3) x [y0, y1), x over
 // [x0, x1) x [y0-3, y1+3); read after the next barrier
-template <typename R>
-__device__ __forceinline__ void inner_denominators(const TS<R>& S, const Blk& B) {
+template <typename R, typename MR>
+__device__ __forceinline__ void inner_denominators(const TS<R, MR>& S, const Blk& B) {
   if constexpr (kStoreRD<R>) {
     const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
     for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
@@ -279,14 +292,22 @@ __device__ __forceinline__ void inner_denominators(const TS<R>& S, const Blk& B)
   }
 }
 
-// shared-memory arrays after the base ones of a kernel: area, 1/area, the
-// stored denominators (kStoreRD) and the damping weights (if `weights`)
-template <typename R>
+// shared-memory arrays after the base ones of a kernel, counted in elements
+// of R: area, 1/area, the stored denominators (kStoreRD) and the damping
+// weights (if `weights`), each of type MR, plus one element of alignment
+// slack when MR is wider than R
+template <typename R, typename MR = R>
 __host__ __device__ constexpr int extra_arrays(bool weights) {
   return 2 + (kStoreRD<R> ? 2 : 0) + (weights ? 2 : 0);
 }
-template <typename R>
-__device__ __forceinline__ void assign_extra(TS<R>& S, R* p, int SA, bool weights) {
+template <typename R, typename MR = R>
+__host__ __device__ constexpr size_t extra_bytes(int SA, bool weights) {
+  return (size_t)extra_arrays<R, MR>(weights) * SA * sizeof(MR) + (sizeof(MR) > sizeof(R) ? sizeof(MR) : 0);
+}
+template <typename R, typename MR>
+__device__ __forceinline__ void assign_extra(TS<R, MR>& S, R* base, int SA, bool weights) {
+  // MR arrays start on an MR boundary
+  MR* p = reinterpret_cast<MR*>((reinterpret_cast<uintptr_t>(base) + sizeof(MR) - 1) & ~(uintptr_t)(sizeof(MR) - 1));
   S.AREA = p; p += SA;
   S.RAREA = p; p += SA;
   if (kStoreRD<R>) { S.RDXd = p; p += SA; S.RDYd = p; p += SA; } else { S.RDXd = nullptr; S.RDYd = nullptr; }
@@ -295,8 +316,8 @@ __device__ __forceinline__ void assign_extra(TS<R>& S, R* p, int SA, bool weight
 
 // the metric terms of the block's tile into shared memory: area and 1/area
 // over the tile, wx and wy over the faces the damping reads
-template <typename R>
-__device__ __forceinline__ void stage_metric(const TS<R>& S, const Blk& B, const TM<R>& m, bool weights) {
+template <typename R, typename MR>
+__device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
   for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
@@ -386,8 +407,8 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
 // damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
 // Every PPM sweep first computes each edge value once (AL), then the face
 // values; the Laplacian of the damping is the divergence of face gradients.
-template <typename R, bool LEARN = false>
-__device__ void transport(R* Q, const TS<R>& S, const Blk& B, const TM<R>& m, int n, bool cc, const R* mfx,
+template <typename R, bool LEARN = false, typename MR = R>
+__device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   const bool dmp = damp != R(0);
@@ -532,8 +553,8 @@ struct TF {
   R *Q, *AL, *FY2, *FX2, *QIJ, *FXO, *FYO;
 };
 
-template <typename R>
-__device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int n, bool cc, const R* mfx,
+template <typename R, typename MR>
+__device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx,
                                const R* mfy) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   __syncthreads();  // both tiles complete
@@ -559,7 +580,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int
   __syncthreads();
   for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R rd = inner_rdy(S, l, SX);
+    const MR rd = inner_rdy(S, l, SX);
 #pragma unroll
     for (int f = 0; f < 2; ++f)
       F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FY2[l] * S.YFX[l] - F[f].FY2[l + SX] * S.YFX[l + SX]) * rd;
@@ -605,7 +626,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int
   __syncthreads();
   for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R rd = inner_rdx(S, l);
+    const MR rd = inner_rdx(S, l);
 #pragma unroll
     for (int f = 0; f < 2; ++f)
       F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FX2[l] * S.XFX[l] - F[f].FX2[l + 1] * S.XFX[l + 1]) * rd;
@@ -635,20 +656,20 @@ __device__ void transport_pair(const TF<R>* F, const TS<R>& S, const Blk& B, int
 // Courant numbers and area fluxes (reading R11) into shared memory, plus the
 // reciprocal denominators of the two inner updates.  uc/vc: global, origin of
 // the level.
-template <typename R>
-__device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R>& S, const Blk& B,
-                        const TM<R>& m, const Geo& g, R dt) {
+template <typename R, typename MR>
+__device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R, MR>& S, const Blk& B,
+                        const TM<MR>& m, const Geo& g, R dt) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
   const int P = g.pitch;
   for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R ut = (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]) * MT(rsin2x, j, i);
+    const auto ut = (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]) * MT(rsin2x, j, i);
     S.XFX[l] = dt * ut * MT(dy, j, i) * MT(sinx, j, i);
     S.CRX[l] = dt * ut * MT(sinx, j, i) * MT(rdxc, j, i);
   });
   for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R vt = (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]) * MT(rsin2y, j, i);
+    const auto vt = (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]) * MT(rsin2y, j, i);
     S.YFX[l] = dt * vt * MT(dx, j, i) * MT(siny, j, i);
     S.CRY[l] = dt * vt * MT(siny, j, i) * MT(rdyc, j, i);
   });
@@ -659,15 +680,16 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
 // ------------------------------------------------------------------------
 // d_sw (reading R11): one level of a block per loop iteration
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY, bool LEARN>
-__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw(StepArgs<R> a, int kchunk, int nwork) {
+template <typename R, int BX, int BY, bool LEARN, typename MR = R>
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(MR) == 8 ? 3 : 4))
+    k_d_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
   R *DP = sb, *PT = sb + SA, *W = sb + 2 * SA, *U = sb + 3 * SA, *V = sb + 4 * SA;
   R *MFX = sb + 5 * SA, *MFY = sb + 6 * SA, *FXO = sb + 7 * SA, *FYO = sb + 8 * SA, *DPN = sb + 9 * SA;
   R* KE = DPN;  // 1/delp_new is dead once pt and w are written
-  TS<R> S;
+  TS<R, MR> S;
   S.CRX = sb + 10 * SA; S.XFX = sb + 11 * SA; S.CRY = sb + 12 * SA; S.YFX = sb + 13 * SA;
   S.FY2 = sb + 14 * SA; S.FX2 = sb + 15 * SA; S.QIJ = sb + 16 * SA; S.LAP = sb + 17 * SA; S.AL = sb + 18 * SA;
   assign_extra(S, sb + 19 * SA, SA, true);
@@ -682,7 +704,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
   const int n = g.n, P = g.pitch;
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
   const bool cc = g.cubed && (B.x0 == 0 || B.x1 == n) && (B.y0 == 0 || B.y1 == n);
-  const TM<R> m = tile_metric(a.M, g, it.t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R dt = (R)a.P.dt;
   const double dd = a.P.d4_bg * g.da_min;
   const R damp = (R)(dd * dd);
@@ -794,7 +816,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_d_sw
 // ------------------------------------------------------------------------
 // c_sw (reading R7)
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY>
+template <typename R, int BX, int BY, typename MR = R>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
@@ -810,7 +832,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
   const int n = g.n, P = g.pitch;
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
-  const TM<R> m = tile_metric(a.M, g, it.t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R dt2 = R(0.5 * a.P.dt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
@@ -907,7 +929,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
         fp[f] = fm[f] * PT[up[f]];
         fw[f] = fm[f] * W[up[f]];
       }
-      const R ra = MT(rarea, j, i);
+      const MR ra = MT(rarea, j, i);
       const R d = DP[l] + (fm[0] - fm[1] + fm[2] - fm[3]) * ra;
       dpc[G(j, i)] = d;
       const R rdn = rcp(d);
@@ -933,7 +955,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
 // the interface geopotential of the block and its ring exchanged in shared
 // memory level by level.  Block: (BXc + 2) x (BYc + 2) threads.
 // ------------------------------------------------------------------------
-template <typename R>
+template <typename R, typename MR = R>
 __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int BYc) {
   __shared__ R GZ[256];
   __shared__ R SXF[256], SYF[256];  // twice the level-mean flux of each thread's west and south face
@@ -951,7 +973,7 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
   // a cell reads its east and north faces from the neighbours
   const bool fxo = i >= x0 && i <= x1 && j >= y0 && j < y1;
   const bool fyo = j >= y0 && j <= y1 && i >= x0 && i < x1;
-  const TM<R> m = tile_metric(a.M, g, it.t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min, rgrav = (R)(1.0 / a.P.grav);
   const long long q = (long long)j * P + i;
   R gzr = R(0), gzn_below = R(0);
@@ -965,7 +987,7 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
   // update is written with twice the level-mean fluxes S = fx(K-1) + fx(K)
   // (2 fx(0) at the top) and twice the area: numerator and denominator both
   // scale by exactly 2, so the quotient is the one of the mean fluxes.
-  const R ar2 = inner ? R(2) * MT(area, j, i) : R(1);
+  const MR ar2 = inner ? MR(2) * MT(area, j, i) : MR(1);
   R xb = R(0), xa = R(0), xn = R(0), yb = R(0), ya = R(0), yn = R(0);  // levels K, K - 1, K - 2
   R dzk = valid ? a.delz[fld0(g, g.off3, nz, it.t, nz - 1) + q] : R(0);
   if (fxo) { xb = fx(nz - 1); xa = fx(nz - 2); }  // nz >= 2
@@ -1112,7 +1134,7 @@ __device__ __forceinline__ R pgrad(R gA0, R gA1, R gB0, R gB1, R pA0, R pA1, R p
   return ((gA1 - gB0) * (pB1 - pA0) + (gA0 - gB1) * (pA1 - pB0)) * rcp(pA1 - pA0 + pB1 - pB0);
 }
 
-template <typename R>
+template <typename R, typename MR = R>
 __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
   const int4 pl = planes[blockIdx.z];
   const Geo g = a.geo[pl.x];
@@ -1120,7 +1142,7 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
   const int n = g.n;
   if (i > n || j > n) return;
   const int t = pl.y, k = pl.z;
-  const TM<R> m = tile_metric(a.M, g, t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, t);
   const R dt2 = R(0.5 * a.P.dt);
   const long long o = fld0(g, g.off3, g.nz, t, k);
   const R* p0 = a.pef + fld0(g, g.offi, g.nz + 1, t, k);
@@ -1147,8 +1169,8 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
 // u += (cd(i+1, j) - cd(i, j)) rdx and v += (cd(i, j+1) - cd(i, j)) rdy.
 // None at the cube corners.  One thread per (i, j) of a level plane.
 // ------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ R cell_shear(const R* u, const R* v, const TM<R>& m, const Geo& g, int j, int i) {
+template <typename R, typename MR>
+__device__ __forceinline__ R cell_shear(const R* u, const R* v, const TM<MR>& m, const Geo& g, int j, int i) {
   const long long P = g.pitch;
   return (u[(j + 1) * P + i] * MT(dx, j + 1, i) - u[j * P + i] * MT(dx, j, i) + v[j * P + i + 1] * MT(dy, j, i + 1) -
           v[j * P + i] * MT(dy, j, i)) * MT(rarea, j, i);
@@ -1157,7 +1179,7 @@ __device__ __forceinline__ R cell_shear(const R* u, const R* v, const TM<R>& m, 
 // a 16 x 16 block of corners (i0 + tx, j0 + ty): the shears of the 18 x 18
 // cells around them and the damping of the 17 x 17 corners the block's faces
 // need are formed once each, in shared memory
-template <typename R>
+template <typename R, typename MR = R>
 __global__ void __launch_bounds__(256) k_div_damp(StepArgs<R> a, const int4* planes) {
   __shared__ R s_sh[18][18];
   __shared__ R s_cd[17][17];
@@ -1168,7 +1190,7 @@ __global__ void __launch_bounds__(256) k_div_damp(StepArgs<R> a, const int4* pla
   if (i0 > n || j0 > n) return;  // the whole block (uniform)
   const int tid = threadIdx.y * 16 + threadIdx.x;
   const int t = pl.y, k = pl.z;
-  const TM<R> m = tile_metric(a.M, g, t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, t);
   const long long o = fld0(g, g.off3, g.nz, t, k);
   const R *u = a.u + o, *v = a.v + o;
   const R d2 = (R)a.P.d2_bg, sm = (R)(a.P.dddmp * a.P.dt);
@@ -1231,7 +1253,7 @@ __device__ __forceinline__ R corner_mean(const R* p, const Geo& g, int j, int i)
 
 // a 16 x 16 block of faces: the corner means of pef and gz at the two
 // interfaces for its 17 x 17 corners are formed once each in shared memory
-template <typename R>
+template <typename R, typename MR = R>
 __global__ void __launch_bounds__(256) k_p_grad_d(StepArgs<R> a, const int4* planes) {
   __shared__ R s_c[4][17][17];  // pef top, pef bottom, gz top, gz bottom
   const int4 pl = planes[blockIdx.z];
@@ -1254,7 +1276,7 @@ __global__ void __launch_bounds__(256) k_p_grad_d(StepArgs<R> a, const int4* pla
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   if (i > n || j > n) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const TM<R> m = tile_metric(a.M, g, t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, t);
   const long long o = fld0(g, g.off3, g.nz, t, k) + (long long)j * g.pitch + i;
   const R dt = (R)a.P.dt;
   const R pA0 = s_c[0][ty][tx], pA1 = s_c[1][ty][tx], gA0 = s_c[2][ty][tx], gA1 = s_c[3][ty][tx];
@@ -1294,15 +1316,16 @@ __global__ void k_halo(const HaloBatch b, const Geo* geo) {
 // ------------------------------------------------------------------------
 // tracer_2d subcycle (reading R12)
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY, bool LEARN>
-__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_tracer(TracerArgs<R> a, int kchunk, int nwork) {
+template <typename R, int BX, int BY, bool LEARN, typename MR = R>
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
+    k_tracer(TracerArgs<R> a, int kchunk, int nwork) {
   if (a.it >= *a.nsplt) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SA = SX * (BY + 7);
   R* sb = reinterpret_cast<R*>(smraw);
   R *Q = sb, *MFX = sb + SA, *MFY = sb + 2 * SA, *FXO = sb + 3 * SA, *FYO = sb + 4 * SA, *D0 = sb + 5 * SA,
     *D1 = sb + 6 * SA;
-  TS<R> S;
+  TS<R, MR> S;
   S.CRX = sb + 7 * SA; S.XFX = sb + 8 * SA; S.CRY = sb + 9 * SA; S.YFX = sb + 10 * SA;
   S.FY2 = sb + 11 * SA; S.FX2 = sb + 12 * SA; S.QIJ = sb + 13 * SA; S.LAP = sb + 14 * SA; S.AL = sb + 15 * SA;
   assign_extra(S, sb + 16 * SA, SA, false);  // no damping of tracers
@@ -1320,7 +1343,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
   const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
-  const TM<R> m = tile_metric(a.M, g, it.t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R fr = R(1) / R(*a.nsplt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
@@ -1411,13 +1434,13 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4) k_trac
 // fluxes), every level of every tile of every member.  The same transport as
 // inside d_sw and tracer_2d, with the fluxes written out.
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY>
+template <typename R, int BX, int BY, typename MR = R>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SA = SX * (BY + 7);
   R* sb = reinterpret_cast<R*>(smraw);
   R *Q = sb, *MFX = sb + SA, *MFY = sb + 2 * SA, *FXO = sb + 3 * SA, *FYO = sb + 4 * SA;
-  TS<R> S;
+  TS<R, MR> S;
   S.CRX = sb + 5 * SA; S.XFX = sb + 6 * SA; S.CRY = sb + 7 * SA; S.YFX = sb + 8 * SA;
   S.FY2 = sb + 9 * SA; S.FX2 = sb + 10 * SA; S.QIJ = sb + 11 * SA; S.LAP = sb + 12 * SA; S.AL = sb + 13 * SA;
   assign_extra(S, sb + 14 * SA, SA, true);
@@ -1431,7 +1454,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
   Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
   const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
-  const TM<R> m = tile_metric(a.M, g, it.t);
+  const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
   stage_metric(S, B, m, damp != R(0));  // read after the first barrier of the level loop
@@ -1661,20 +1684,28 @@ static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork) {
 // the d_sw and tracer kernels exist with and without learned face values
 // (separate instantiations: the network's fragments need registers the
 // plain kernel does not)
-template <typename R, int X, int Y, bool L>
+template <typename R, int X, int Y, bool L, typename MR>
 static void launch_d_sw(const Ctx& c, const StepArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
-  set_smem(k_d_sw<R, X, Y, L>, sm);
-  k_d_sw<R, X, Y, L><<<work_grid(c, k_d_sw<R, X, Y, L>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork);
+  set_smem(k_d_sw<R, X, Y, L, MR>, sm);
+  k_d_sw<R, X, Y, L, MR><<<work_grid(c, k_d_sw<R, X, Y, L, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk,
+                                                                                                  nwork);
 }
 
-template <typename R, int X, int Y, bool L>
+template <typename R, int X, int Y, bool L, typename MR>
 static void launch_tracer(const Ctx& c, const TracerArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
-  set_smem(k_tracer<R, X, Y, L>, sm);
-  k_tracer<R, X, Y, L><<<work_grid(c, k_tracer<R, X, Y, L>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork);
+  set_smem(k_tracer<R, X, Y, L, MR>, sm);
+  k_tracer<R, X, Y, L, MR><<<work_grid(c, k_tracer<R, X, Y, L, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk,
+                                                                                                      nwork);
 }
 
 [[maybe_unused]] static size_t blk_smem(const Ctx& c, int arrays) {
   return (size_t)arrays * (c.BX + 7) * (c.BY + 7) * c.esize;
+}
+
+// base arrays of R plus the metric arrays of MR (extra_bytes)
+template <typename R, typename MR>
+[[maybe_unused]] static size_t blk_smem_mr(const Ctx& c, int arrays, bool weights) {
+  return blk_smem(c, arrays) + extra_bytes<R, MR>((c.BX + 7) * (c.BY + 7), weights);
 }
 
 #if FV3_TU_MAIN
@@ -1721,13 +1752,14 @@ void enqueue_halo_prognostics(Ctx& c, const StateView& s, cudaStream_t st) {
 #endif
 
 
-template <typename R>
+template <typename R, typename MR = R>
 static void substep_t(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool acc,
                       cudaStream_t st, int stop_after, int only) {
   StepArgs<R> a{};
   a.geo = c.geo_d;
   a.items = c.items_hz;
   a.M = metric_of<R>(c);
+  a.Md = c.Md;
   a.P = P;
   a.u = (const R*)in.u; a.v = (const R*)in.v; a.w = (const R*)in.w;
   a.delp = (const R*)in.delp; a.pt = (const R*)in.pt; a.delz = (const R*)in.delz;
@@ -1762,8 +1794,8 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(1)) {  // c_sw
     const size_t sm = blk_smem(c, 13);
 #define FV3_CSW(X, Y)                                                                  \
-  set_smem(k_c_sw<R, X, Y>, sm);                                                       \
-  k_c_sw<R, X, Y><<<work_grid(c, k_c_sw<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
+  set_smem(k_c_sw<R, X, Y, MR>, sm);                                                   \
+  k_c_sw<R, X, Y, MR><<<work_grid(c, k_c_sw<R, X, Y, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_CSW);
 #undef FV3_CSW
     ++c.launches;
@@ -1771,7 +1803,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(2)) {  // update_dz_c
     StepArgs<R> b = a;
     b.items = c.items_dz;
-    k_update_dz_c<R><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
     ++c.launches;
   }
   if (run(3)) {  // riem_solver_c
@@ -1784,7 +1816,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     F.push_back(hf(c, K_CELL1, c.gz, nullptr, c.nz + 1, 1));
     enqueue_halo_fields(c, F, st);
     const int nb = (c.max_n + 1 + 15) / 16;
-    k_p_grad_c<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+    k_p_grad_c<R, MR><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
     ++c.launches;
   }
   if (run(5)) {  // C-grid winds into the halo
@@ -1793,23 +1825,24 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     enqueue_halo_fields(c, F, st);
   }
   if (run(6)) {  // d_sw
-    const size_t sm = blk_smem(c, 19 + extra_arrays<R>(true));
+    const size_t sm = blk_smem_mr<R, MR>(c, 19, true);
     const bool learn = P.hord == 1 && P.mlp;
 #define FV3_DSW(X, Y)                                                                  \
-  (learn ? launch_d_sw<R, X, Y, true>(c, a, sm, nwork, st) : launch_d_sw<R, X, Y, false>(c, a, sm, nwork, st))
+  (learn ? launch_d_sw<R, X, Y, true, MR>(c, a, sm, nwork, st)                         \
+         : launch_d_sw<R, X, Y, false, MR>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
 #undef FV3_DSW
     ++c.launches;
   }
   if (run(6) && (P.d2_bg > 0.0 || P.dddmp > 0.0)) {  // divergence damping of d_sw's winds
     const int nb = (c.max_n + 1 + 15) / 16;
-    k_div_damp<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+    k_div_damp<R, MR><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
     ++c.launches;
   }
   if (run(7)) {  // update_dz_d: the D-grid area fluxes of d_sw over the state delz
     StepArgs<R> b = a;
     b.items = c.items_dz;
-    k_update_dz_c<R><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
     ++c.launches;
   }
   if (run(8)) {  // riem_solver3 on the state after d_sw
@@ -1828,7 +1861,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     F.push_back(hf(c, K_CELL3, c.gz, nullptr, c.nz + 1, 1));
     enqueue_halo_fields(c, F, st);
     const int nb = (c.max_n + 1 + 15) / 16;
-    k_p_grad_d<R><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+    k_p_grad_d<R, MR><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
     ++c.launches;
   }
 }
@@ -1845,10 +1878,17 @@ void enqueue_substep_f32(Ctx& c, const StateView& in, const StateView& out, cons
   substep_t<float>(c, in, out, P, accumulate, st, stop_after, only);
 }
 #endif
+#if FV3_TU_F32M64
+void enqueue_substep_f32m64(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
+                            cudaStream_t st, int stop_after, int only) {
+  substep_t<float, double>(c, in, out, P, accumulate, st, stop_after, only);
+}
+#endif
 #if FV3_TU_MAIN
 void enqueue_substep(Ctx& c, const StateView& in, const StateView& out, const Params& P, bool accumulate,
                      cudaStream_t st, int stop_after, int only) {
   if (c.prec == 0) enqueue_substep_f64(c, in, out, P, accumulate, st, stop_after, only);
+  else if (c.prec == 2) enqueue_substep_f32m64(c, in, out, P, accumulate, st, stop_after, only);
   else enqueue_substep_f32(c, in, out, P, accumulate, st, stop_after, only);
 }
 #endif
@@ -1909,7 +1949,7 @@ void enqueue_save_dpstart(Ctx& c, const void* delp, cudaStream_t st) {
 #endif
 
 
-template <typename R>
+template <typename R, typename MR = R>
 static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
   std::vector<HaloField> F;
   F.push_back(hf(c, K_CGRID, c.amfx, c.amfy, c.nz, 0));
@@ -1929,6 +1969,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   a.geo = c.geo_d;
   a.items = c.items_hz;
   a.M = metric_of<R>(c);
+  a.Md = c.Md;
   a.nq = s.nq;
   a.nsplt = c.nsplt;
   for (int q = 0; q < s.nq; ++q) {
@@ -1944,14 +1985,15 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
   const bool pair = a.learn ? kTracerPair<R, true> : kTracerPair<R, false>;
-  const size_t sm = blk_smem(c, 16 + extra_arrays<R>(false) + (pair ? 6 : 0));
+  const size_t sm = blk_smem_mr<R, MR>(c, 16 + (pair ? 6 : 0), false);
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
     enqueue_halo_fields(c, Q, st);
     a.it = it;
 #define FV3_TRC(X, Y)                                                                  \
-  (a.learn ? launch_tracer<R, X, Y, true>(c, a, sm, nwork, st) : launch_tracer<R, X, Y, false>(c, a, sm, nwork, st))
+  (a.learn ? launch_tracer<R, X, Y, true, MR>(c, a, sm, nwork, st)                     \
+           : launch_tracer<R, X, Y, false, MR>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TRC);
 #undef FV3_TRC
     ++c.launches;
@@ -1972,12 +2014,18 @@ void enqueue_tracers_f32(Ctx& c, const StateView& s, const Params& P, cudaStream
   tracers_t<float>(c, s, P, st);
 }
 #endif
-template <typename R>
+#if FV3_TU_F32M64
+void enqueue_tracers_f32m64(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
+  tracers_t<float, double>(c, s, P, st);
+}
+#endif
+template <typename R, typename MR = R>
 static void fv_tp_2d_t(Ctx& c, const TpPtrs& p, cudaStream_t st) {
   TpArgs<R> a{};
   a.geo = c.geo_d;
   a.items = c.items_hz;
   a.M = metric_of<R>(c);
+  a.Md = c.Md;
   a.q = (const R*)p.q; a.crx = (const R*)p.crx; a.cry = (const R*)p.cry;
   a.xfx = (const R*)p.xfx; a.yfx = (const R*)p.yfx;
   a.mfx = (const R*)p.mfx; a.mfy = (const R*)p.mfy;
@@ -1985,10 +2033,11 @@ static void fv_tp_2d_t(Ctx& c, const TpPtrs& p, cudaStream_t st) {
   a.damp = p.damp;
   const int kz = (c.nz + c.kchunk - 1) / c.kchunk;
   const int nwork = c.n_items_hz * kz;
-  const size_t sm = blk_smem(c, 14 + extra_arrays<R>(true));
+  const size_t sm = blk_smem_mr<R, MR>(c, 14, true);
 #define FV3_TP(X, Y)                                                                   \
-  set_smem(k_fv_tp_2d<R, X, Y>, sm);                                                   \
-  k_fv_tp_2d<R, X, Y><<<work_grid(c, k_fv_tp_2d<R, X, Y>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
+  set_smem(k_fv_tp_2d<R, X, Y, MR>, sm);                                               \
+  k_fv_tp_2d<R, X, Y, MR><<<work_grid(c, k_fv_tp_2d<R, X, Y, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, \
+                                                                                                     nwork)
   FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TP);
 #undef FV3_TP
   ++c.launches;
@@ -1998,6 +2047,9 @@ void enqueue_fv_tp_2d_f64(Ctx& c, const TpPtrs& p, cudaStream_t st) { fv_tp_2d_t
 #endif
 #if FV3_TU_F32
 void enqueue_fv_tp_2d_f32(Ctx& c, const TpPtrs& p, cudaStream_t st) { fv_tp_2d_t<float>(c, p, st); }
+#endif
+#if FV3_TU_F32M64
+void enqueue_fv_tp_2d_f32m64(Ctx& c, const TpPtrs& p, cudaStream_t st) { fv_tp_2d_t<float, double>(c, p, st); }
 #endif
 
 #if FV3_TU_MAIN
@@ -2009,12 +2061,14 @@ void enqueue_fv_tp_2d(Ctx& c, const TpPtrs& p, cudaStream_t st) {
   if (p.mfx) F.push_back(hf(c, K_CGRID, p.mfx, p.mfy, c.nz, 0));
   enqueue_halo_fields(c, F, st);
   if (c.prec == 0) enqueue_fv_tp_2d_f64(c, p, st);
+  else if (c.prec == 2) enqueue_fv_tp_2d_f32m64(c, p, st);
   else enqueue_fv_tp_2d_f32(c, p, st);
 }
 
 void enqueue_tracers(Ctx& c, const StateView& s, const Params& P, cudaStream_t st) {
   if (s.nq <= 0) return;
   if (c.prec == 0) enqueue_tracers_f64(c, s, P, st);
+  else if (c.prec == 2) enqueue_tracers_f32m64(c, s, P, st);
   else enqueue_tracers_f32(c, s, P, st);
 }
 #endif

@@ -20,7 +20,7 @@ FV3_OK = 0
 STATUS = {0: "FV3_OK", -1: "FV3_ERR_ARG", -2: "FV3_ERR_SHAPE", -3: "FV3_ERR_ALIGN", -4: "FV3_ERR_CUDA",
           -5: "FV3_ERR_NONFINITE", -6: "FV3_ERR_CFL", -7: "FV3_ERR_TIMEOUT", -8: "FV3_ERR_UNSUPPORTED"}
 GRID_PERIODIC, GRID_CUBED = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_M64 = 0, 1, 2
 KIND_CELL, KIND_XFACE, KIND_YFACE, KIND_IFACE = 0, 1, 2, 3
 DENSE_DEVICE, DENSE_HOST, DENSE_HOST_ASYNC = 0, 1, 2
 HALO_WIND, HALO_W, HALO_DELP, HALO_PT, HALO_DELZ, HALO_TRACERS = 1, 2, 4, 8, 16, 32

@@ -84,9 +84,11 @@ def test_zero_steps_and_limits():
         fv3.Grid(fv3.GRID_CUBED, 64, 2, n_members=200)          # rows beyond one launch's grid
 
 
-def test_c192x80_fp32_substep(orc):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_m64"])
+def test_c192x80_fp32_substep(orc, precision):
     """The FP32-bulk bench configuration (C192 x 80, 32 x 8 blocks, four levels
-    per work item) against the FP64 oracle after one substep.  Bound: every
+    per work item; metric terms in FP32 or in FP64) against the FP64 oracle
+    after one substep.  Bound: every
     stored FP32 field is a few tens of roundings (2^-24 ~ 6e-8 each) away from
     the FP64 values it is formed from, so within 1e-6 of the field's maximum
     (measured: <= 2.2e-7); FP64 mass sums of the FP32 delp conserve to FP32
@@ -95,7 +97,7 @@ def test_c192x80_fp32_substep(orc):
     from paper_2205_04148_gb300 import inputs as I
     n, nz = 192, 80
     st = I.cubed_state(n, nz, seed=0, ntracers=0)
-    g = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=fv3.FP32)
+    g = fv3.Grid(fv3.GRID_CUBED, n, nz, precision=fv3.FP32 if precision == "fp32" else fv3.FP32_M64)
     gs = g.alloc_state()
     g.load(gs, st)
     g.set_tiles(32, 8, 4)

@@ -54,7 +54,7 @@ def oracle_fluxes(orc, cubed, n, q, crx, cry, xfx, yfx, damp=0.0):
 
 
 @pytest.mark.parametrize("cubed", [False, True])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_fv_tp_2d_matches_oracle(orc, cubed, precision):
     from paper_2205_04148_gb300 import fv3
     n, nz = 20, 3

@@ -245,6 +245,35 @@ def test_fp32_bulk_close(orc):
         assert e <= 2e-4, (f, e)
 
 
+@pytest.mark.parametrize("cubed", [False, True])
+def test_fp32_metric64_close(orc, cubed):
+    """FP32 bulk with the metric terms in FP64 (FV3_FP32_M64): at FP32
+    rounding scale against the FP64 oracle after one substep and after a
+    remapping step with tracers, and not the same arithmetic as the FP32
+    metric copies"""
+    from paper_2205_04148_gb300 import fv3
+    n, nz = (16, 5) if cubed else (24, 4)
+    g, gs, d, s, st = pair(orc, cubed, n, nz, seed=19, nq=2, precision=fv3.FP32_M64)
+    g.substep(gs)
+    s.substep()
+    for f in ("u", "v", "delp", "pt"):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= 2e-4, (f, e)
+    if cubed:   # the cube's metric terms are not exact in float
+        g2, gs2, _, _, _ = pair(orc, cubed, n, nz, seed=19, nq=2, precision=fv3.FP32)
+        g2.substep(gs2)
+        assert any(not np.array_equal(g.read(gs, f), g2.read(gs2, f)) for f in ("u", "v", "delp", "pt"))
+    g.load(gs, st)
+    s2 = orc.State(d, 2)
+    s2.load(st)
+    g.run_dyn(gs, fv3.params(n_split=3), 1)
+    s2.run_dyn(orc.params(n_split=3), 1)
+    for f in FIELDS + ("q0", "q1"):
+        e = relerr(g.read(gs, f), s2.get(f))
+        assert e <= 2e-4, (f, e)
+    assert g.check_status() == 0
+
+
 def test_courant_guard_reports():
     """A flow with Courant number above 1 is reported by fv3_check_status."""
     from paper_2205_04148_gb300 import fv3
