@@ -407,10 +407,112 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
 // damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
 // Every PPM sweep first computes each edge value once (AL), then the face
 // values; the Laplacian of the damping is the divergence of face gradients.
+// The same transport for the FP32 path in four phases: on the FP32 pipe an
+// edge value costs less than the shared-memory round trip, the loop
+// overhead and the barrier of a separate edge phase, so each face value
+// forms its two edge values itself (ppm_face: the same operations as
+// ppm_edge + ppm_face_al, the same bits), the inner x-update goes to the
+// edge array, which is free, and the phases that do not read each other's
+// results share a barrier:
+//   1  y-faces of Q (FY2) and the damping gradients GY
+//   2  inner y-update (QIJ), x-faces of Q (FX2) and the gradients GX
+//   3  Laplacian (LAP) and inner x-update (into AL)
+//   4  outer x-faces of QIJ and outer y-faces of the x-updated field, fluxes
+// The damping gradients live in the output arrays until the Laplacian is
+// formed, as in transport().
+template <typename R, typename MR>
+__device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx, const R* mfy,
+                                R damp, const R* wdp, R* FXO, R* FYO) {
+  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const bool dmp = damp != R(0);
+  R* const GX = FXO;
+  R* const GY = FYO;
+  R* const QJ = S.AL;  // the x-updated field
+  __syncthreads();  // Q (and the strips the corner turn reads) complete
+  if (cc) {  // blocks at a cube corner: the missing quadrant for the y-sweep
+    corner_roles(Q, B, n, 1);
+    __syncthreads();
+  }
+  // 1: y-faces of the plain field (y-role corners)
+  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
+  });
+  if (dmp)
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+      const int l = B.L(i, j);
+      GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
+    });
+  __syncthreads();
+  // 2: inner y-update in every column of the block and its halo
+  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
+  });
+  if (cc) {  // x-role corners: touches only missing-quadrant cells, which
+             // the inner y-update does not read; the x-faces below do
+    corner_roles(Q, B, n, 0);
+    __syncthreads();
+  }
+  // x-faces of the plain field (x-role corners)
+  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
+  });
+  if (dmp)
+    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
+    });
+  __syncthreads();
+  // 3: Laplacian of the damping, inner x-update in every row of the block
+  // and its halo
+  if (dmp)
+    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+      const int l = B.L(i, j);
+      S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
+    });
+  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    const int l = B.L(i, j);
+    QJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
+  });
+  __syncthreads();
+  // 4: outer x-faces of the y-updated field and outer y-faces of the
+  // x-updated field; fluxes = mean face value x (mass or area) flux, plus
+  // the del-4 damping flux
+  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
+    R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
+    if (dmp) {
+      R d = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
+      if (wdp) d = d * (R(0.5) * (wdp[l - 1] + wdp[l]));
+      fl = fl + d;
+    }
+    FXO[l] = fl;
+  });
+  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    const int l = B.L(i, j);
+    const R f = ppm_face(QJ + l, SX, S.CRY[l]);
+    R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
+    if (dmp) {
+      R d = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
+      if (wdp) d = d * (R(0.5) * (wdp[l - SX] + wdp[l]));
+      fl = fl + d;
+    }
+    FYO[l] = fl;
+  });
+  __syncthreads();
+}
+
 template <typename R, bool LEARN = false, typename MR = R>
 __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  if constexpr (sizeof(R) == 4 && !LEARN) {
+    transport_fused(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
+    return;
+  }
   const bool dmp = damp != R(0);
   // the damping gradients live in the output arrays until the Laplacian is
   // formed; the fluxes are written only after it
