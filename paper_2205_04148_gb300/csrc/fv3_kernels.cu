@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     // pef of the interface below layer k
     double pef;
     if (k == nz - 1) pef = pe_bot + ppn;
-    else pef = (k + 1 < nz ? 0.0 : 0.0) + s_pe[(long long)(k + 1) * NC + col] + 0.5 * (ppn + ppn_below);
+    else pef = s_pe[(long long)(k + 1) * NC + col] + 0.5 * (ppn + ppn_below);
     a.pef[oib] = (R)pef;
     ppn_below = ppn;
     Wn = Wk;

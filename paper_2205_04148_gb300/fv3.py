@@ -198,13 +198,19 @@ def halo_plan(grid_type, npx, npz, kind=PLAN_CELL, member=0, precision=FP64, n_m
                     dx, radius, omega)
     total = C.c_size_t()
     lay = Layout()
-    rc = L.fv3_halo_plan(C.byref(desc), member, kind, None, 0, C.byref(total), C.byref(lay))
+    n = member_npx[member] if member_npx is not None else npx
+    # every halo slot of both arrays of a pair, on six tiles, bounds the plan:
+    # one call builds it (the metric behind it is built once)
+    cap = 2 * 6 * ((n + 7) * (n + 7) - n * n)
+    buf = (HaloEntry * cap)()
+    rc = L.fv3_halo_plan(C.byref(desc), member, kind, buf, cap, C.byref(total), C.byref(lay))
     if rc != FV3_OK:
         raise Fv3Error("%s: fv3_halo_plan" % STATUS.get(rc, rc))
-    buf = (HaloEntry * max(1, total.value))()
-    rc = L.fv3_halo_plan(C.byref(desc), member, kind, buf, total.value, C.byref(total), None)
-    if rc != FV3_OK:
-        raise Fv3Error("%s: fv3_halo_plan" % STATUS.get(rc, rc))
+    if total.value > cap:   # not expected; ask again with the exact size
+        buf = (HaloEntry * total.value)()
+        rc = L.fv3_halo_plan(C.byref(desc), member, kind, buf, total.value, C.byref(total), None)
+        if rc != FV3_OK:
+            raise Fv3Error("%s: fv3_halo_plan" % STATUS.get(rc, rc))
     a = np.frombuffer(buf, dtype=np.int32).reshape(-1, 6)[: total.value].astype(np.int64)
     names = ("dst", "src", "dst_tile", "src_tile", "sign", "flags")
     return {nm: a[:, k].copy() for k, nm in enumerate(names)}, lay
