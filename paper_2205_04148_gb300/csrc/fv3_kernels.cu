@@ -1132,8 +1132,14 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
 // FULL (riem_solver3, reading R17): the whole substep dt instead of dt/2,
 // and the new layer w (mean of its two interface values) and delz written
 // back (w_o, delz_o)
+// One warp per CTA: the columns of a tile are few for this GPU (one thread
+// each, 7 to 12 warps per SM at C96 / C192), so the work is spread over the
+// SMs in units of one warp; with CTAs of four warps (some partly empty) some
+// SMs held twice the FP64 work of others.
+constexpr int kRiemCols = 32;
+
 template <typename R, bool FULL>
-__global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* rows) {
+__global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowItem* rows) {
   const RowItem r = rows[blockIdx.y];
   const Geo g = a.geo[r.m];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1155,9 +1161,18 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
   const double rgrav = 1.0 / grav, rdt = 1.0 / dt, cC = aimp * dt * gama, rd_g = rd / grav;
   const long long q = (long long)r.j * g.pitch + i;
   double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
-  for (int k = 0; k < nz; ++k) {
-    const long long o = fld0(g, g.off3, nz, r.t, k) + q;
-    const double dpk = (double)a.delpc[o], ptk = (double)a.ptc[o], wck = (double)a.wc[o], dzk = (double)a.delzc[o];
+  // Software pipeline over the levels: iteration k forms the coefficients of
+  // level k + 1 (gas-law and hydrostatic pressures, C, the tridiagonal row)
+  // and runs the elimination step of level k.  The two chains do not depend
+  // on each other, so the scheduler interleaves them (a warp's sweep is
+  // sequential and FP64 latency would otherwise stall it); the loads run two
+  // levels ahead.  The arithmetic of every value is the one-level-at-a-time
+  // sweep's.
+  const long long o0 = fld0(g, g.off3, nz, r.t, 0) + q;
+  const long long plane = g.plane;
+  struct Row { double la, di, up, rhs; };
+  auto coef = [&](int k, R dpr, R ptr, R wcr, R dzr) -> Row {
+    const double dpk = (double)dpr, ptk = (double)ptr, wck = (double)wcr, dzk = (double)dzr;
     const double pen = pe + dpk;
     const double rdz = rcp(dzk);
     const double p = -dpk * rd_g * ptk * rdz;
@@ -1166,23 +1181,12 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     const double C = -cC * p * rdz;
     const double mm = k == 0 ? 0.5 * dpk * rgrav : 0.5 * (dpp + dpk) * rgrav;
     const double wn = k == 0 ? wck : 0.5 * (wcp + wck);
-    const double la = -Cp;                    // lower (layer above the interface)
-    const double di = mm * rdt + Cp + C;      // diagonal
-    const double up = k < nz - 1 ? -C : 0.0;  // upper
-    const double rhs = mm * rdt * wn + pp - ppp;
-    double cpk, dpt;
-    if (k == 0) {
-      const double rden = rcp(di);
-      cpk = up * rden;
-      dpt = rhs * rden;
-    } else {
-      const double rden = rcp(di - la * cpp);
-      cpk = up * rden;
-      dpt = (rhs - la * dpv) * rden;
-    }
+    Row w;
+    w.la = -Cp;                      // lower (layer above the interface)
+    w.di = mm * rdt + Cp + C;        // diagonal
+    w.up = k < nz - 1 ? -C : 0.0;    // upper
+    w.rhs = mm * rdt * wn + pp - ppp;
     const long long sidx = (long long)k * NC + col;
-    s_cp[sidx] = cpk;
-    s_dp[sidx] = dpt;
     s_C[sidx] = C;
     s_pp[sidx] = pp;
     s_pe[sidx] = pe;
@@ -1191,23 +1195,62 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     wcp = wck;
     Cp = C;
     ppp = pp;
+    return w;
+  };
+  auto eliminate = [&](int k, const Row& w) {
+    double cpk, dpt;
+    if (k == 0) {
+      const double rden = rcp(w.di);
+      cpk = w.up * rden;
+      dpt = w.rhs * rden;
+    } else {
+      const double rden = rcp(w.di - w.la * cpp);
+      cpk = w.up * rden;
+      dpt = (w.rhs - w.la * dpv) * rden;
+    }
+    const long long sidx = (long long)k * NC + col;
+    s_cp[sidx] = cpk;
+    s_dp[sidx] = dpt;
     cpp = cpk;
     dpv = dpt;
+  };
+  R ndp = a.delpc[o0], npt = a.ptc[o0], nwc = a.wc[o0], ndz = a.delzc[o0];
+  Row cur = coef(0, ndp, npt, nwc, ndz);
+  {
+    const long long on = o0 + plane;  // nz >= 2
+    ndp = a.delpc[on]; npt = a.ptc[on]; nwc = a.wc[on]; ndz = a.delzc[on];
   }
-  // bottom-up
+  for (int k = 0; k < nz - 1; ++k) {
+    const R dpr = ndp, ptr = npt, wcr = nwc, dzr = ndz;
+    const long long on = o0 + (long long)min(k + 2, nz - 1) * plane;
+    ndp = a.delpc[on]; npt = a.ptc[on]; nwc = a.wc[on]; ndz = a.delzc[on];
+    const Row nxt = coef(k + 1, dpr, ptr, wcr, dzr);
+    eliminate(k, cur);
+    cur = nxt;
+  }
+  eliminate(nz - 1, cur);
   const double pe_bot = pe, raimp = 1.0 / aimp;
   double Wn = 0.0, gzv = 0.0, ppn_below = 0.0;
   {
     const long long ob = fld0(g, g.offi, nz + 1, r.t, nz) + q;
     a.gz[ob] = R(0);
   }
+  // bottom-up, the loads of level k - 1 issued before level k is computed
+  long long sidx = (long long)(nz - 1) * NC + col;
+  double bdp = s_dp[sidx], bcp = s_cp[sidx], bpp = s_pp[sidx], bC = s_C[sidx], bpe = 0.0;
+  R bdz = a.delzc[fld0(g, g.off3, nz, r.t, nz - 1) + q];
   for (int k = nz - 1; k >= 0; --k) {
-    const long long sidx = (long long)k * NC + col;
-    const double Wk = s_dp[sidx] - s_cp[sidx] * Wn;
+    const double dpk = bdp, cpk = bcp, ppk = bpp, Ck = bC, pek = bpe, dzk = (double)bdz;
     const long long o = fld0(g, g.off3, nz, r.t, k) + q;
-    const double dzk = (double)a.delzc[o];
+    if (k > 0) {
+      bpe = s_pe[sidx];  // hydrostatic pressure of the interface below layer k - 1
+      sidx -= NC;
+      bdp = s_dp[sidx]; bcp = s_cp[sidx]; bpp = s_pp[sidx]; bC = s_C[sidx];
+      bdz = a.delzc[o - g.plane];
+    }
+    const double Wk = dpk - cpk * Wn;
     const double dzn = dzk + dt * (Wn - Wk);
-    const double ppn = s_pp[sidx] + s_C[sidx] * (Wn - Wk) * raimp;
+    const double ppn = ppk + Ck * (Wn - Wk) * raimp;
     if (FULL) {
       a.w_o[o] = (R)(0.5 * (Wk + Wn));
       a.delz_o[o] = (R)dzn;
@@ -1219,7 +1262,7 @@ __global__ void __launch_bounds__(128) k_riem_c(StepArgs<R> a, const RowItem* ro
     // pef of the interface below layer k
     double pef;
     if (k == nz - 1) pef = pe_bot + ppn;
-    else pef = s_pe[(long long)(k + 1) * NC + col] + 0.5 * (ppn + ppn_below);
+    else pef = pek + 0.5 * (ppn + ppn_below);
     a.pef[oib] = (R)pef;
     ppn_below = ppn;
     Wn = Wk;
@@ -1909,7 +1952,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     ++c.launches;
   }
   if (run(3)) {  // riem_solver_c
-    k_riem_c<R, false><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(a, c.rows);
+    k_riem_c<R, false><<<dim3((c.max_n + kRiemCols - 1) / kRiemCols, c.n_rows), kRiemCols, 0, st>>>(a, c.rows);
     ++c.launches;
   }
   if (run(4)) {  // pef, gz one ring into the halo, then p_grad_c
@@ -1952,7 +1995,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     b.delpc = (R*)out.delp;
     b.ptc = (R*)out.pt;
     b.wc = (R*)out.w;
-    k_riem_c<R, true><<<dim3((c.max_n + 127) / 128, c.n_rows), 128, 0, st>>>(b, c.rows);
+    k_riem_c<R, true><<<dim3((c.max_n + kRiemCols - 1) / kRiemCols, c.n_rows), kRiemCols, 0, st>>>(b, c.rows);
     ++c.launches;
   }
   if (run(9)) {  // pef, gz into the halo, then the D-grid pressure gradient

@@ -99,19 +99,28 @@ __device__ __forceinline__ double log_ratio(double pen, double pe, double dp) {
 //     - 10719068v^6/638512875 - 25865068v^7/1915538625
 //     - 5472607916v^8/488462349375 - ...
 // (the coefficients of the series division, exact rationals).  For |u| <= 1/8
-// the terms through v^8 leave a truncation below 1e-18 relative: one
-// reciprocal and a polynomial instead of the logarithm's series and a second
-// reciprocal.  The thin upper layers (larger u) divide by the library log.
+// the terms through v^8 leave a truncation below 1e-18 relative, for |u| <=
+// 1/32 (most layers below the top ones) the terms through v^4 one below 2e-17
+// (the next term is 0.022 v^5): one reciprocal and a polynomial instead of
+// the logarithm's series and a second reciprocal.  The thin upper layers
+// (larger u) divide by the library log.  The tiers are chosen on the integer
+// bits of |u|.
 __device__ __forceinline__ double layer_mean_pressure(double pen, double pe, double dp) {
   const double sum = pe + pen;
   const double u = dp * rcp(sum);
-  if (fabs(u) > 0.125) return dp / log(pen / pe);
+  const long long mag = __double_as_longlong(u) & 0x7fffffffffffffffLL;
+  if (mag > 0x3fc0000000000000LL) return dp / log(pen / pe);  // |u| > 1/8
   const double v = u * u;
-  double r = -5472607916.0 / 488462349375.0;
-  r = fma(r, v, -25865068.0 / 1915538625.0);
-  r = fma(r, v, -10719068.0 / 638512875.0);
-  r = fma(r, v, -10196.0 / 467775.0);
-  r = fma(r, v, -428.0 / 14175.0);
+  double r;
+  if (mag <= 0x3fa0000000000000LL) {  // |u| <= 1/32
+    r = -428.0 / 14175.0;
+  } else {
+    r = -5472607916.0 / 488462349375.0;
+    r = fma(r, v, -25865068.0 / 1915538625.0);
+    r = fma(r, v, -10719068.0 / 638512875.0);
+    r = fma(r, v, -10196.0 / 467775.0);
+    r = fma(r, v, -428.0 / 14175.0);
+  }
   r = fma(r, v, -44.0 / 945.0);
   r = fma(r, v, -4.0 / 45.0);
   r = fma(r, v, -1.0 / 3.0);
