@@ -164,18 +164,42 @@ struct Blk {
 // block so that every warp but the last is full (the ranges are a few cells
 // wider than a warp; a row-per-warp loop would leave most lanes of a second
 // pass idle, and on this GPU an FP64 warp instruction costs its full pipe
-// time whatever its active lanes).  Row j = floor((e + 1/2) / w) from a float
-// reciprocal: the fractional part of (e + 1/2) / w is at least 1/(2w) away
-// from an integer, far more than the float error for these sizes.
-template <typename F>
+// time whatever its active lanes).  Runtime extents: row j = floor((e + 1/2)
+// / w) from a float reciprocal (the fractional part of (e + 1/2) / w is at
+// least 1/(2w) away from an integer, far more than the float error for these
+// sizes).  CW: the caller's extents fold to constants (a full block of a
+// compile-time shape), and the index arithmetic per point is a few integer
+// adds.
+template <bool CW = false, typename F>
 __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
   const int w = ihi - ilo, h = jhi - jlo;
   if (w <= 0 || h <= 0) return;
-  const int total = w * h, nthr = (int)(blockDim.x * blockDim.y);
-  const float rw = 1.0f / (float)w;
-  for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < total; e += nthr) {
-    const int j = (int)(((float)e + 0.5f) * rw);
-    f(ilo + (e - j * w), jlo + j);
+  const int total = w * h;
+  if constexpr (CW) {
+    // extents known at compile time (full blocks, 256 threads as (32, 8)):
+    // the first point by a division by the constant width, then steps of
+    // 256 points as constant increments of (i, j)
+    constexpr int NT = 256;
+    const int tid = (int)(threadIdx.y * 32 + threadIdx.x);
+    int j = tid / w, i = tid - j * w;
+    const int dj = NT / w, di = NT - dj * w;
+#pragma unroll 1
+    for (int e = tid; e < total; e += NT) {
+      f(ilo + i, jlo + j);
+      i += di;
+      j += dj;
+      if (i >= w) {
+        i -= w;
+        ++j;
+      }
+    }
+  } else {
+    const int nthr = (int)(blockDim.x * blockDim.y);
+    const float rw = 1.0f / (float)w;
+    for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < total; e += nthr) {
+      const int j = (int)(((float)e + 0.5f) * rw);
+      f(ilo + (e - j * w), jlo + j);
+    }
   }
 }
 
@@ -316,17 +340,17 @@ __device__ __forceinline__ void assign_extra(TS<R, MR>& S, R* base, int SA, bool
 
 // the metric terms of the block's tile into shared memory: area and 1/area
 // over the tile, wx and wy over the faces the damping reads
-template <typename R, typename MR>
+template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
 __device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights) {
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
-  for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
+  for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AREA[l] = MT(area, j, i);
     S.RAREA[l] = MT(rarea, j, i);
   });
   if (weights) {
-    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
+    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
   }
 }
 
@@ -420,10 +444,10 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
 //   4  outer x-faces of QIJ and outer y-faces of the x-updated field, fluxes
 // The damping gradients live in the output arrays until the Laplacian is
 // formed, as in transport().
-template <typename R, typename MR>
+template <int BX, int BY, bool FULL, typename R, typename MR>
 __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx, const R* mfy,
                                 R damp, const R* wdp, R* FXO, R* FYO) {
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   const bool dmp = damp != R(0);
   R* const GX = FXO;
   R* const GY = FYO;
@@ -434,18 +458,18 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     __syncthreads();
   }
   // 1: y-faces of the plain field (y-role corners)
-  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
   });
   if (dmp)
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
   __syncthreads();
   // 2: inner y-update in every column of the block and its halo
-  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL>(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -455,12 +479,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     __syncthreads();
   }
   // x-faces of the plain field (x-role corners)
-  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
   });
   if (dmp)
-    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -468,11 +492,11 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 3: Laplacian of the damping, inner x-update in every row of the block
   // and its halo
   if (dmp)
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
-  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     QJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
@@ -480,7 +504,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 4: outer x-faces of the y-updated field and outer y-faces of the
   // x-updated field; fluxes = mean face value x (mass or area) flux, plus
   // the del-4 damping flux
-  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+  for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
     R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
@@ -491,7 +515,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     }
     FXO[l] = fl;
   });
-  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R f = ppm_face(QJ + l, SX, S.CRY[l]);
     R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
@@ -505,12 +529,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   __syncthreads();
 }
 
-template <typename R, bool LEARN = false, typename MR = R>
+template <typename R, bool LEARN = false, int BX = 0, int BY = 0, bool FULL = false, typename MR = R>
 __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   if constexpr (sizeof(R) == 4 && !LEARN) {
-    transport_fused(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
+    transport_fused<BX, BY, FULL>(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
     return;
   }
   const bool dmp = damp != R(0);
@@ -539,12 +563,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // y-sweep of the plain field (y-role corners): edges, then faces
-  for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
   });
   if (dmp)
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
@@ -552,13 +576,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRY, S.FY2, x0 - 3, x1 + 3, y0, y1 + 1, SX, B, F);
   else
-    for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
     });
   __syncthreads();
   // inner y-update in every column of the block and its halo
-  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL>(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -569,12 +593,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // x-sweep of the plain field (x-role corners)
-  for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
   });
   if (dmp)
-    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -582,18 +606,18 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRX, S.FX2, x0, x1 + 1, y0 - 3, y1 + 3, 1, B, F);
   else
-    for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
     });
   if (dmp)
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
   __syncthreads();
   // outer x-sweep of the y-updated field
-  for2(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+  for2<FULL>(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2], S.QIJ[l - 1], S.QIJ[l], S.QIJ[l + 1]);
   });
@@ -601,13 +625,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRX, FXO, x0, x1 + 1, y0, y1, 1, B, F);
     __syncthreads();
-    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R fl = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
       FXO[l] = dmp ? fl + damp_x(l) : fl;
     });
   } else {
-    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
       const R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
@@ -616,13 +640,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   }
   __syncthreads();
   // inner x-update in every row of the block and its halo
-  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
   __syncthreads();
   // outer y-sweep of the x-updated field
-  for2(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2 * SX], S.QIJ[l - SX], S.QIJ[l], S.QIJ[l + SX]);
   });
@@ -630,13 +654,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRY, FYO, x0, x1, y0, y1 + 1, SX, B, F);
     __syncthreads();
-    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R fl = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
       FYO[l] = dmp ? fl + damp_y(l) : fl;
     });
   } else {
-    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
       const R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
@@ -758,18 +782,18 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
 // Courant numbers and area fluxes (reading R11) into shared memory, plus the
 // reciprocal denominators of the two inner updates.  uc/vc: global, origin of
 // the level.
-template <typename R, typename MR>
+template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
 __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R, MR>& S, const Blk& B,
                         const TM<MR>& m, const Geo& g, R dt) {
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   const int P = g.pitch;
-  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     const auto ut = (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]) * MT(rsin2x, j, i);
     S.XFX[l] = dt * ut * MT(dy, j, i) * MT(sinx, j, i);
     S.CRX[l] = dt * ut * MT(sinx, j, i) * MT(rdxc, j, i);
   });
-  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const auto vt = (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]) * MT(rsin2y, j, i);
     S.YFX[l] = dt * vt * MT(dx, j, i) * MT(siny, j, i);
@@ -782,7 +806,10 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
 // ------------------------------------------------------------------------
 // d_sw (reading R11): one level of a block per loop iteration
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY, bool LEARN, typename MR = R>
+// FULL: every block of every member is a full BX x BY block (the tiles'
+// sizes are multiples of the block shape), so the extents of every 2-D loop
+// are compile-time constants
+template <typename R, int BX, int BY, bool LEARN, typename MR = R, bool FULL = false>
 __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(MR) == 8 ? 3 : 4))
     k_d_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -804,44 +831,44 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
   const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
-  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
+  Blk B{it.x0, FULL ? it.x0 + BX : min(it.x0 + BX, n), it.y0, FULL ? it.y0 + BY : min(it.y0 + BY, n), SX};
   const bool cc = g.cubed && (B.x0 == 0 || B.x1 == n) && (B.y0 == 0 || B.y1 == n);
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R dt = (R)a.P.dt;
   const double dd = a.P.d4_bg * g.da_min;
   const R damp = (R)(dd * dd);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
-  stage_metric(S, B, m, true);  // read after the first barrier of the level loop
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
+  stage_metric<BX, BY, FULL>(S, B, m, true);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
     const R *uc = a.uc + o, *vc = a.vc + o;
     auto G = [&](int j, int i) { return (long long)j * P + i; };
-    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = G(j, i);
       DP[l] = dp[q];
       PT[l] = pt[q];
       W[l] = w[q];
     });
-    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-    for2(x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+    for2<FULL>(x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     __syncthreads();
-    courant(uc, vc, V, U, S, B, m, g, dt);
+    courant<BX, BY, FULL>(uc, vc, V, U, S, B, m, g, dt);
     if (a.status) {  // Courant-number guard on the block's own faces
       bool bad = false;
-      for2(x0, x1, y0, y1, [&](int i, int j) {
+      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         bad |= !(fabs(S.CRX[l]) < R(1)) || !(fabs(S.CRY[l]) < R(1));
       });
       if (bad) atomicOr(a.status, ST_CFL);
     }
     // mass
-    transport<R, LEARN>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, MFX, MFY,
-                        a.mlp);
+    transport<R, LEARN, BX, BY, FULL>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+                                      (const R*)nullptr, MFX, MFY, a.mlp);
     R* dpo = a.delp_o + o;
-    for2(x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
       DPN[l] = rcp(d);  // reciprocal, used by pt and w
@@ -852,10 +879,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       R* Q = fld == 0 ? PT : W;
       R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
       if (LEARN && fld == 0)
-        transport<R, LEARN>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
+        transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
       else
-        transport<R, false>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
-      for2(x0, x1, y0, y1, [&](int i, int j) {
+        transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
             (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * DPN[l];
@@ -863,14 +890,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     }
     __syncthreads();
     // cell absolute vorticity (into PT)
-    for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
                V[l] * MT(dy, j, i)) * S.RAREA[l] + MT(fA, j, i);
     });
-    transport(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp, (const R*)nullptr, FXO, FYO);
+    transport<R, false, BX, BY, FULL>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+                                      (const R*)nullptr, FXO, FYO);
     // kinetic energy at corners from upwind-PPM corner winds
-    for2(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
       const R va = R(0.5) * (vc[G(j, i - 1)] + vc[G(j, i)]);
@@ -882,27 +910,27 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     });
     __syncthreads();
     R *uo = a.u_o + o, *vo = a.v_o + o;
-    for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
       const int l = B.L(i, j);
       uo[G(j, i)] = U[l] + (FYO[l] + KE[l] - KE[l + 1]) * MT(rdx, j, i);
     });
-    for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       vo[G(j, i)] = V[l] + (-FXO[l] + KE[l] - KE[l + SX]) * MT(rdy, j, i);
     });
     if (a.xfxd) {  // the D-grid area fluxes for update_dz_d (reading R17)
-      for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
-      for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
+      for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
+      for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
     }
     if (a.amfx) {
-      for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+      for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
         a.amfx[q] += MFX[l];
         a.acrx[q] += S.CRX[l];
         a.axfx[q] += S.XFX[l];
       });
-      for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+      for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
         a.amfy[q] += MFY[l];
@@ -918,7 +946,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
 // ------------------------------------------------------------------------
 // c_sw (reading R7)
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY, typename MR = R>
+template <typename R, int BX, int BY, typename MR = R, bool FULL = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R> a, int kchunk, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
@@ -932,8 +960,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
   const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
-  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  Blk B{it.x0, FULL ? it.x0 + BX : min(it.x0 + BX, n), it.y0, FULL ? it.y0 + BY : min(it.y0 + BY, n), SX};
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R dt2 = R(0.5 * a.P.dt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
@@ -943,13 +971,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
     const bool ord4 = a.P.d2c_ord == 4;
     if (ord4) {  // the fourth-order stencils reach one ring further
-      for2(x0 - 3, x1 + 3, y0 - 2, y1 + 3, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-      for2(x0 - 2, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+      for2<FULL>(x0 - 3, x1 + 3, y0 - 2, y1 + 3, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+      for2<FULL>(x0 - 2, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     } else {
-      for2(x0 - 2, x1 + 2, y0 - 1, y1 + 2, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-      for2(x0 - 1, x1 + 2, y0 - 2, y1 + 2, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+      for2<FULL>(x0 - 2, x1 + 2, y0 - 1, y1 + 2, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+      for2<FULL>(x0 - 1, x1 + 2, y0 - 2, y1 + 2, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     }
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = G(j, i);
       DP[l] = dp[q];
@@ -961,7 +989,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     // (reading R7) or four-point Lagrange interpolation (-1, 9, 9, -1) / 16
     // along the component's direction, then across (reading R18)
     auto lag4 = [](R a0, R a1, R a2, R a3) { return R(0.0625) * (R(9) * (a1 + a2) - (a0 + a3)); };
-    for2(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       R c0;
       if (ord4) {
@@ -973,7 +1001,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
       UC0[l] = c0;
       UT[l] = (c0 - MT(cosx, j, i) * V[l]) * MT(rsin2x, j, i);
     });
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       R c0;
       if (ord4) {
@@ -987,25 +1015,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     });
     __syncthreads();
     R *fx1 = a.fx1 + o, *fy1 = a.fy1 + o;
-    for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = dt2 * UT[l] * MT(dy, j, i) * MT(sinx, j, i);
       FX1[l] = f;
       if (i < x1 || x1 == n) fx1[G(j, i)] = f;
     });
-    for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = dt2 * VT[l] * MT(dx, j, i) * MT(siny, j, i);
       FY1[l] = f;
       if (j < y1 || y1 == n) fy1[G(j, i)] = f;
     });
-    for2(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R ua = R(0.5) * (UT[l] + UT[l + 1]);
       const R va = R(0.5) * (VT[l] + VT[l + SX]);
       KE[l] = R(0.5) * dt2 * (ua * ua + va * va);
     });
-    for2(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R ts = UC0[l - SX] * MT(dxc, j - 1, i);
       R te = VC0[l] * MT(dyc, j, i);
@@ -1019,7 +1047,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     });
     __syncthreads();
     R *dpc = a.delpc + o, *ptc = a.ptc + o, *wcc = a.wc + o;
-    for2(x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const int up[4] = {FX1[l] > R(0) ? l - 1 : l, FX1[l + 1] > R(0) ? l : l + 1, FY1[l] > R(0) ? l - SX : l,
                          FY1[l + SX] > R(0) ? l : l + SX};
@@ -1039,11 +1067,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
       wcc[G(j, i)] = (W[l] * DP[l] + (fw[0] - fw[1] + fw[2] - fw[3]) * ra) * rdn;
     });
     R *uco = a.uc + o, *vco = a.vc + o;
-    for2(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       uco[G(j, i)] = UC0[l] + dt2 * R(0.5) * (VO[l] + VO[l + SX]) * V[l] + (KE[l - 1] - KE[l]) * MT(rdxc, j, i);
     });
-    for2(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
       const int l = B.L(i, j);
       vco[G(j, i)] = VC0[l] - dt2 * R(0.5) * (VO[l] + VO[l + 1]) * U[l] + (KE[l - SX] - KE[l]) * MT(rdyc, j, i);
     });
@@ -1461,7 +1489,7 @@ __global__ void k_halo(const HaloBatch b, const Geo* geo) {
 // ------------------------------------------------------------------------
 // tracer_2d subcycle (reading R12)
 // ------------------------------------------------------------------------
-template <typename R, int BX, int BY, bool LEARN, typename MR = R>
+template <typename R, int BX, int BY, bool LEARN, typename MR = R, bool FULL = false>
 __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
     k_tracer(TracerArgs<R> a, int kchunk, int nwork) {
   if (a.it >= *a.nsplt) return;
@@ -1485,24 +1513,24 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
   const Item it = a.items[wi / kz];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch;
-  Blk B{it.x0, min(it.x0 + BX, n), it.y0, min(it.y0 + BY, n), SX};
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1;
+  Blk B{it.x0, FULL ? it.x0 + BX : min(it.x0 + BX, n), it.y0, FULL ? it.y0 + BY : min(it.y0 + BY, n), SX};
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R fr = R(1) / R(*a.nsplt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
-  stage_metric(S, B, m, false);  // read after the first barrier of the level loop
+  stage_metric<BX, BY, FULL>(S, B, m, false);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
-    for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
       S.CRX[l] = a.acrx[q] * fr;
       S.XFX[l] = a.axfx[q] * fr;
       MFX[l] = a.amfx[q] * fr;
     });
-    for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
       S.CRY[l] = a.acry[q] * fr;
@@ -1511,7 +1539,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
     });
     __syncthreads();
     inner_denominators(S, B);
-    for2(x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
       const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
@@ -1538,11 +1566,11 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
         if (two)
           transport_pair(TFP, S, B, n, cc, MFX, MFY);
         else
-          transport<R, false>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+          transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
         for (int f = 0; f < (two ? 2 : 1); ++f) {
           R* qo = a.q_o[tq + f] + o;
           const TF<R>& T = TFP[f];
-          for2(x0, x1, y0, y1, [&](int i, int j) {
+          for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
             const int l = B.L(i, j);
             qo[G(j, i)] =
                 (T.Q[l] * D0[l] + (T.FXO[l] - T.FXO[l + 1] + T.FYO[l] - T.FYO[l + SX]) * S.RAREA[l]) * D1[l];
@@ -1555,14 +1583,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
       __syncthreads();
       if (LEARN) {
         const R* q = a.q[tq] + o;
-        for2(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
+        for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
       } else {
         tile_put<NPRE>(Q, pre, B);
         if (tq + 1 < a.nq) tile_fetch<NPRE>(a.q[tq + 1] + o, pre, B, P);
       }
-      transport<R, LEARN>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
+      transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
       R* qo = a.q_o[tq] + o;
-      for2(x0, x1, y0, y1, [&](int i, int j) {
+      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * D1[l];
       });
@@ -1829,18 +1857,32 @@ static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork) {
 // the d_sw and tracer kernels exist with and without learned face values
 // (separate instantiations: the network's fragments need registers the
 // plain kernel does not)
-template <typename R, int X, int Y, bool L, typename MR>
+template <typename R, int X, int Y, bool L, typename MR, bool F = false>
 static void launch_d_sw(const Ctx& c, const StepArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
-  set_smem(k_d_sw<R, X, Y, L, MR>, sm);
-  k_d_sw<R, X, Y, L, MR><<<work_grid(c, k_d_sw<R, X, Y, L, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk,
+  set_smem(k_d_sw<R, X, Y, L, MR, F>, sm);
+  k_d_sw<R, X, Y, L, MR, F><<<work_grid(c, k_d_sw<R, X, Y, L, MR, F>, sm, nwork), dim3(32, 8), sm, st>>>(
+      a, c.kchunk, nwork);
+}
+
+template <typename R, int X, int Y, typename MR, bool F = false>
+static void launch_c_sw(const Ctx& c, const StepArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
+  set_smem(k_c_sw<R, X, Y, MR, F>, sm);
+  k_c_sw<R, X, Y, MR, F><<<work_grid(c, k_c_sw<R, X, Y, MR, F>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk,
                                                                                                   nwork);
 }
 
-template <typename R, int X, int Y, bool L, typename MR>
+// every member's tiles are made of full blocks of the current shape
+[[maybe_unused]] static bool full_blocks(const Ctx& c) {
+  for (const Geo& g : c.geo)
+    if (g.n % c.BX != 0 || g.n % c.BY != 0) return false;
+  return true;
+}
+
+template <typename R, int X, int Y, bool L, typename MR, bool F = false>
 static void launch_tracer(const Ctx& c, const TracerArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
-  set_smem(k_tracer<R, X, Y, L, MR>, sm);
-  k_tracer<R, X, Y, L, MR><<<work_grid(c, k_tracer<R, X, Y, L, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk,
-                                                                                                      nwork);
+  set_smem(k_tracer<R, X, Y, L, MR, F>, sm);
+  k_tracer<R, X, Y, L, MR, F><<<work_grid(c, k_tracer<R, X, Y, L, MR, F>, sm, nwork), dim3(32, 8), sm, st>>>(
+      a, c.kchunk, nwork);
 }
 
 [[maybe_unused]] static size_t blk_smem(const Ctx& c, int arrays) {
@@ -1938,9 +1980,9 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(0)) enqueue_halo_prognostics(c, in, st);
   if (run(1)) {  // c_sw
     const size_t sm = blk_smem(c, 13);
+    const bool full = full_blocks(c);
 #define FV3_CSW(X, Y)                                                                  \
-  set_smem(k_c_sw<R, X, Y, MR>, sm);                                                   \
-  k_c_sw<R, X, Y, MR><<<work_grid(c, k_c_sw<R, X, Y, MR>, sm, nwork), dim3(32, 8), sm, st>>>(a, c.kchunk, nwork)
+  (full ? launch_c_sw<R, X, Y, MR, true>(c, a, sm, nwork, st) : launch_c_sw<R, X, Y, MR>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_CSW);
 #undef FV3_CSW
     ++c.launches;
@@ -1972,9 +2014,11 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(6)) {  // d_sw
     const size_t sm = blk_smem_mr<R, MR>(c, 19, true);
     const bool learn = P.hord == 1 && P.mlp;
+    const bool full = full_blocks(c);
 #define FV3_DSW(X, Y)                                                                  \
-  (learn ? launch_d_sw<R, X, Y, true, MR>(c, a, sm, nwork, st)                         \
-         : launch_d_sw<R, X, Y, false, MR>(c, a, sm, nwork, st))
+  (learn  ? launch_d_sw<R, X, Y, true, MR>(c, a, sm, nwork, st)                        \
+   : full ? launch_d_sw<R, X, Y, false, MR, true>(c, a, sm, nwork, st)                 \
+          : launch_d_sw<R, X, Y, false, MR>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_DSW);
 #undef FV3_DSW
     ++c.launches;
@@ -2131,6 +2175,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
   const int nwork = c.n_items_hz * kz;
   const bool pair = a.learn ? kTracerPair<R, true> : kTracerPair<R, false>;
   const size_t sm = blk_smem_mr<R, MR>(c, 16 + (pair ? 6 : 0), false);
+  const bool full = full_blocks(c);
   for (int it = 0; it < NSPLT_MAX; ++it) {
     std::vector<HaloField> Q;
     for (int q = 0; q < s.nq; ++q) Q.push_back(hf(c, K_CELL3, s.q[q], nullptr, c.nz, 0));
@@ -2138,6 +2183,7 @@ static void tracers_t(Ctx& c, const StateView& s, const Params& P, cudaStream_t 
     a.it = it;
 #define FV3_TRC(X, Y)                                                                  \
   (a.learn ? launch_tracer<R, X, Y, true, MR>(c, a, sm, nwork, st)                     \
+   : full  ? launch_tracer<R, X, Y, false, MR, true>(c, a, sm, nwork, st)                \
            : launch_tracer<R, X, Y, false, MR>(c, a, sm, nwork, st))
     FV3_DISPATCH_SHAPE(c.BX, c.BY, FV3_TRC);
 #undef FV3_TRC
