@@ -578,14 +578,20 @@ def batched_measure(a, ws, rank, steps, local=0):
     sp = C.c_void_p(stream.cuda_stream)
     cells = sum(6 * n * n * nz for n in sizes)
 
-    # transfer tuning: search on one C96 member, apply to the ensemble
-    gt = fv3.Grid(fv3.GRID_CUBED, 96, nz, precision=fv3.FP32)
-    gts = gt.alloc_state()
-    gt.load(gts, base[96])
-    (bx, by, kc), tuned_ms = gt.autotune(gts, prm)
-    pers = gt.persistent()
-    gt.close()
-    del gts
+    # transfer tuning: search on one C96 member among the block shapes that
+    # cover every member's tiles with whole blocks, apply to the ensemble (or
+    # the shape given by --tiles)
+    if a.tiles:
+        bx, by, kc, pm = (int(x) for x in a.tiles.split(","))
+        pers, tuned_ms = bool(pm), None
+    else:
+        gt = fv3.Grid(fv3.GRID_CUBED, 96, nz, precision=fv3.FP32)
+        gts = gt.alloc_state()
+        gt.load(gts, base[96])
+        (bx, by, kc), tuned_ms = gt.autotune(gts, prm, sizes=sorted(set(sizes)))
+        pers = gt.persistent()
+        gt.close()
+        del gts
 
     g = fv3.Grid(fv3.GRID_CUBED, max(sizes), nz, n_members=len(sizes), member_npx=sizes, precision=fv3.FP32)
     gs = g.alloc_state()

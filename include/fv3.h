@@ -369,6 +369,16 @@ fv3_status fv3_get_persistent(const fv3_ctx* ctx, int* on);
 fv3_status fv3_autotune(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream,
                         double* best_ms);
 
+/* fv3_autotune for a shape that will be transferred to other grids (the
+ * paper's transfer tuning, Section VII-B): only block shapes that cover every
+ * tile size in sizes[n_sizes] (cells per tile edge) with whole blocks are
+ * tried, when at least one does (the kernels have full-block instantiations
+ * whose loops have compile-time extents); otherwise every shape.  Errors as
+ * fv3_autotune, and FV3_ERR_ARG for n_sizes < 0, sizes NULL with n_sizes > 0,
+ * or a size < 1. */
+fv3_status fv3_autotune_for(fv3_ctx* ctx, const fv3_state* state, const fv3_params* params, fv3_stream stream,
+                            double* best_ms, const int* sizes, int n_sizes);
+
 /* ---- learned face values (reading R14; the paper has no learned part) ----
  * Network: 6 -> 32 -> 32 -> 1 with tanh, parameters float[1313] on the device
  * (W1[6][32] at 0, b1 at 192, W2[32][32] at 224, b2 at 1248, W3[32] at 1280,

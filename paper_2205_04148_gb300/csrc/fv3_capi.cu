@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -856,8 +857,11 @@ extern "C" fv3_status fv3_get_tiles(const fv3_ctx* x, int* bx, int* by, int* kch
 // searches transformation configurations on representative cutouts and
 // transfers the best ones; here the search space is the compiled block
 // shapes x level chunks, timed with events on the full d_sw + c_sw stages).
-extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream,
-                                   double* best_ms) {
+namespace {
+// the search of fv3_autotune; sizes: tile sizes (cells per edge) whose tiles
+// the chosen block shape must cover with whole blocks, if any shape does
+fv3_status autotune_impl(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream, double* best_ms,
+                         const std::vector<int>& sizes) {
   if (!x) return FV3_ERR_ARG;
   fv3_status r = check_state(x, s, false);
   if (r != FV3_OK) return r;
@@ -865,7 +869,17 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
   if (r != FV3_OK) return r;
   Ctx& c = x->c;
   cudaStream_t st = (cudaStream_t)stream;
-  const int shapes[4][2] = {{32, 8}, {32, 16}, {64, 8}, {16, 16}};
+  const int all_shapes[4][2] = {{32, 8}, {32, 16}, {64, 8}, {16, 16}};
+  // shapes that make every tile of the given sizes whole blocks (the kernels
+  // then run their full-block instantiation); all shapes if none does
+  std::vector<std::array<int, 2>> shapes;
+  for (const auto& sh : all_shapes) {
+    bool whole = true;
+    for (int n : sizes) whole = whole && n % sh[0] == 0 && n % sh[1] == 0;
+    if (whole) shapes.push_back({sh[0], sh[1]});
+  }
+  if (shapes.empty())
+    for (const auto& sh : all_shapes) shapes.push_back({sh[0], sh[1]});
   const int chunks[3] = {1, 4, 16};
   const int pmodes[2] = {0, 1};
   const StateView in = view(s);
@@ -910,6 +924,21 @@ extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_par
   c.persistent = bb[3];
   if (best_ms) *best_ms = best;
   return r;
+}
+}  // namespace
+
+extern "C" fv3_status fv3_autotune(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream,
+                                   double* best_ms) {
+  return autotune_impl(x, s, p, stream, best_ms, {});
+}
+
+extern "C" fv3_status fv3_autotune_for(fv3_ctx* x, const fv3_state* s, const fv3_params* p, fv3_stream stream,
+                                       double* best_ms, const int* sizes, int n_sizes) {
+  if (n_sizes < 0 || (n_sizes > 0 && !sizes)) return FV3_ERR_ARG;
+  std::vector<int> v(sizes, sizes + n_sizes);
+  for (int n : v)
+    if (n < 1) return FV3_ERR_ARG;
+  return autotune_impl(x, s, p, stream, best_ms, v);
 }
 
 // ------------------------------------------------------------------------

@@ -30,7 +30,7 @@ SYMBOLS = ("fv3_init_grid", "fv3_destroy", "fv3_last_error", "fv3_field_elems", 
            "fv3_get_layout", "fv3_import", "fv3_export", "fv3_halo_fill", "fv3_acoustic_substep",
            "fv3_run_dyn", "fv3_mass_sum", "fv3_check_status", "fv3_get_metric", "fv3_stage",
            "fv3_get_intermediate", "fv3_launch_stage", "fv3_kernel_launches", "fv3_calibrate",
-           "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_riem_solver_c_noalloc",
+           "fv3_set_tiles", "fv3_get_tiles", "fv3_autotune", "fv3_autotune_for", "fv3_riem_solver_c_noalloc",
            "fv3_mlp_forward", "fv3_mlp_work_floats", "fv3_mlp_grad", "fv3_mlp_adam", "fv3_set_persistent",
            "fv3_get_persistent", "fv3_fv_tp_2d", "fv3_math_check", "fv3_vertical_remap",
            "fv3_mlp_grad_fp32", "fv3_mlp_work_floats_fp32", "fv3_check_finite", "fv3_halo_plan",
@@ -143,6 +143,8 @@ def load(path=LIB_PATH):
     L.fv3_get_tiles.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     L.fv3_autotune.restype = st
     L.fv3_autotune.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp, C.POINTER(d)]
+    L.fv3_autotune_for.restype = st
+    L.fv3_autotune_for.argtypes = [vp, C.POINTER(State), C.POINTER(Params), vp, C.POINTER(d), C.POINTER(i), i]
     L.fv3_mlp_forward.restype = st
     L.fv3_mlp_forward.argtypes = [vp, vp, i, i, vp, vp]
     L.fv3_halo_gather.restype = st
@@ -427,11 +429,18 @@ class Grid:
         self.check(self.L.fv3_get_tiles(self.ptr, C.byref(bx), C.byref(by), C.byref(kc)))
         return bx.value, by.value, kc.value
 
-    def autotune(self, st, prm=None, stream=None):
+    def autotune(self, st, prm=None, stream=None, sizes=None):
+        """fv3_autotune; with ``sizes`` (tile sizes the result will be
+        transferred to) fv3_autotune_for"""
         s = self.cstate(st)
         prm = prm or params()
         best = C.c_double()
-        self.check(self.L.fv3_autotune(self.ptr, C.byref(s), C.byref(prm), _stream(stream), C.byref(best)))
+        if sizes:
+            arr = (C.c_int * len(sizes))(*sizes)
+            self.check(self.L.fv3_autotune_for(self.ptr, C.byref(s), C.byref(prm), _stream(stream), C.byref(best),
+                                               arr, len(sizes)))
+        else:
+            self.check(self.L.fv3_autotune(self.ptr, C.byref(s), C.byref(prm), _stream(stream), C.byref(best)))
         return self.tiles(), best.value
 
     def fv_tp_2d(self, q, crx, cry, xfx, yfx, mfx=None, mfy=None, damp=0.0, fx=None, fy=None, stream=None):

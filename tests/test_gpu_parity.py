@@ -314,6 +314,30 @@ def test_block_shapes(orc, shape):
         assert e <= TOL64, (shape, f, e)
 
 
+def test_transfer_tuning_keeps_whole_blocks(orc):
+    """fv3_autotune_for: tuned on one member for sizes 48, 96 and 128, only
+    shapes that cover all three with whole blocks are tried (here 16 x 16),
+    and the ensemble run with the result matches the oracle"""
+    from paper_2205_04148_gb300 import fv3
+    g, gs, d, s, st = pair(orc, True, 24, 4, seed=31)
+    (bx, by, kc), best = g.autotune(gs, sizes=[48, 96, 128])
+    assert (bx, by) == (16, 16) and best > 0
+    g2 = fv3.Grid(fv3.GRID_CUBED, 16, 3, n_members=2, member_npx=[16, 32])
+    g2.set_tiles(bx, by, kc)
+    gs2 = g2.alloc_state()
+    sts = [seeded(True, n, 3, seed=40 + m) for m, n in enumerate((16, 32))]
+    for m, stm in enumerate(sts):
+        g2.load(gs2, stm, member=m)
+    g2.substep(gs2)
+    for m, (n, stm) in enumerate(zip((16, 32), sts)):
+        so = orc.State(orc.Domain(True, n, 3))
+        so.load(stm)
+        so.substep()
+        for f in FIELDS:
+            e = relerr(g2.read(gs2, f, member=m), so.get(f))
+            assert e <= TOL64, (m, f, e)
+
+
 def test_autotune_keeps_parity(orc):
     from paper_2205_04148_gb300 import fv3
     g, gs, d, s, st = pair(orc, True, 24, 6, seed=29, nq=1)
