@@ -51,7 +51,10 @@ METRIC = "cell-substeps/s"
 # written (each add, subtract, multiply, divide = 1): Courant numbers and
 # area fluxes 20, delp transport + damping + update 138, pt and w 146 each,
 # vorticity 9 + transport 106 + damping 26, corner kinetic energy 55, wind
-# update 9.
+# update 9.  The kernel's executed FP64 flops per cell, counted by ncu
+# (an FMA = 2; each edge value formed once, the halo of a block formed again
+# by its neighbours, Newton reciprocals), are carried beside it from the
+# capture record.
 DSW_FLOPS_PER_CELL = 655
 # Algorithmic HBM bytes per cell of one d_sw launch: reads u, v, w, delp, pt,
 # uc, vc and writes u, v, w, delp, pt (12 words).
@@ -75,7 +78,8 @@ def dram_traffic(kernel, prec, bx, by, kc, persistent, cells):
     for c in caps:
         if (c["kernel"], c["precision"], c["bx"], c["by"], c["kchunk"], bool(c["persistent"])) == \
                 (kernel, prec, bx, by, kc, bool(persistent)):
-            rec = {k: c[k] for k in ("bytes_per_cell", "capture_cells", "capture", "commit") if k in c}
+            rec = {k: c[k] for k in ("bytes_per_cell", "capture_cells", "capture", "commit", "fp64_flops_per_cell")
+                   if k in c}
             rec["scaled"] = "bytes per cell of the capture x cells of the timed launch"
             return c["bytes_per_cell"] * cells, rec
     return None, None
@@ -383,6 +387,7 @@ def ours(a):
                 "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": traffic, "traffic_capture": traffic_rec,
                 "kernel": "k_d_sw<double>",
                 "ms_per_launch": t_dsw * 1e3, "flops_per_cell": DSW_FLOPS_PER_CELL,
+                "flops_per_cell_executed": (traffic_rec or {}).get("fp64_flops_per_cell"),
                 "peak_measured_fma": fp64_meas,
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it",
                 "hbm": hbm_obj}
