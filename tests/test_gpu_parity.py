@@ -314,6 +314,25 @@ def test_block_shapes(orc, shape):
         assert e <= TOL64, (shape, f, e)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(16, 16), (32, 8), (32, 16), (64, 8)])
+def test_whole_and_partial_block_kernels(orc, precision, shape):
+    """n = 32 on the cube: 16 x 16, 32 x 8 and 32 x 16 blocks cover every tile
+    whole (the full-block instantiations of c_sw, d_sw and tracer_2d run),
+    64 x 8 does not (the runtime-extent ones run); a remapping step with
+    tracers against the oracle in each case"""
+    from paper_2205_04148_gb300 import fv3
+    g, gs, d, s, st = pair(orc, True, 32, 3, seed=51, nq=2, precision=precision)
+    g.set_tiles(shape[0], shape[1], 2)
+    g.run_dyn(gs, fv3.params(n_split=2), 1)
+    s.run_dyn(orc.params(n_split=2), 1)
+    tol = TOL64 if precision == 0 else 2e-4
+    for f in FIELDS + ("q0", "q1"):
+        e = relerr(g.read(gs, f), s.get(f))
+        assert e <= tol, (f, e)
+    assert g.check_status() == 0
+
+
 def test_transfer_tuning_keeps_whole_blocks(orc):
     """fv3_autotune_for: tuned on one member for sizes 48, 96 and 128, only
     shapes that cover all three with whole blocks are tried (here 16 x 16),
