@@ -923,19 +923,23 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
     }
     if (a.amfx) {
+      // the remapping step's sums: each face has one writer per launch, so
+      // an addition performed at the memory side (a reduction whose result
+      // is not read back) gives the sum a load-add-store gives, without the
+      // load's round trip
       for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
-        a.amfx[q] += MFX[l];
-        a.acrx[q] += S.CRX[l];
-        a.axfx[q] += S.XFX[l];
+        atomicAdd(a.amfx + q, MFX[l]);
+        atomicAdd(a.acrx + q, S.CRX[l]);
+        atomicAdd(a.axfx + q, S.XFX[l]);
       });
       for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
-        a.amfy[q] += MFY[l];
-        a.acry[q] += S.CRY[l];
-        a.ayfx[q] += S.YFX[l];
+        atomicAdd(a.amfy + q, MFY[l]);
+        atomicAdd(a.acry + q, S.CRY[l]);
+        atomicAdd(a.ayfx + q, S.YFX[l]);
       });
     }
     __syncthreads();
