@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "fv3_kernels.cuh"
 #include "fv3_math.cuh"
@@ -49,6 +50,17 @@ template <>
 __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 template <>
 __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+
+// *p += v for an element with one writer per launch: with v of the element's
+// type an addition performed at the memory side (a reduction whose result
+// is not read back: the same sum, without the load's round trip); with a
+// wider v (FP64 metric products on an FP32 field) the sum is formed in the
+// wider type and rounded once, as the expression p[0] + v is
+template <typename R, typename T>
+__device__ __forceinline__ void add_to(R* p, T v) {
+  if constexpr (std::is_same_v<R, T>) atomicAdd(p, v);
+  else *p = (R)((T)*p + v);
+}
 
 // ------------------------------------------------------------------------
 // PPM (reading R4)
@@ -1329,11 +1341,11 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
   const long long B = (long long)j * g.pitch + i;
   if (j < n) {
     const long long A = B - 1;
-    a.uc[o + B] += dt2 * MT(rdxc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]);
+    add_to(a.uc + o + B, dt2 * MT(rdxc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]));
   }
   if (i < n) {
     const long long A = B - g.pitch;
-    a.vc[o + B] += dt2 * MT(rdyc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]);
+    add_to(a.vc + o + B, dt2 * MT(rdyc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]));
   }
 }
 
@@ -1400,8 +1412,8 @@ __global__ void __launch_bounds__(256) k_div_damp(StepArgs<R> a, const int4* pla
   if (i > n || j > n) return;
   const R c0 = s_cd[threadIdx.y][threadIdx.x];
   const long long q = o + (long long)j * g.pitch + i;
-  if (i < n) a.u_o[q] += (s_cd[threadIdx.y][threadIdx.x + 1] - c0) * MT(rdx, j, i);
-  if (j < n) a.v_o[q] += (s_cd[threadIdx.y + 1][threadIdx.x] - c0) * MT(rdy, j, i);
+  if (i < n) add_to(a.u_o + q, (s_cd[threadIdx.y][threadIdx.x + 1] - c0) * MT(rdx, j, i));
+  if (j < n) add_to(a.v_o + q, (s_cd[threadIdx.y + 1][threadIdx.x] - c0) * MT(rdy, j, i));
 }
 
 // ------------------------------------------------------------------------
@@ -1458,11 +1470,13 @@ __global__ void __launch_bounds__(256) k_p_grad_d(StepArgs<R> a, const int4* pla
   const R dt = (R)a.P.dt;
   const R pA0 = s_c[0][ty][tx], pA1 = s_c[1][ty][tx], gA0 = s_c[2][ty][tx], gA1 = s_c[3][ty][tx];
   if (i < n)  // u on the y-face (i, j): corners (i, j) and (i + 1, j)
-    a.u_o[o] += dt * MT(rdx, j, i) *
-                pgrad(gA0, gA1, s_c[2][ty][tx + 1], s_c[3][ty][tx + 1], pA0, pA1, s_c[0][ty][tx + 1], s_c[1][ty][tx + 1]);
+    add_to(a.u_o + o, dt * MT(rdx, j, i) *
+                          pgrad(gA0, gA1, s_c[2][ty][tx + 1], s_c[3][ty][tx + 1], pA0, pA1, s_c[0][ty][tx + 1],
+                                s_c[1][ty][tx + 1]));
   if (j < n)  // v on the x-face (i, j): corners (i, j) and (i, j + 1)
-    a.v_o[o] += dt * MT(rdy, j, i) *
-                pgrad(gA0, gA1, s_c[2][ty + 1][tx], s_c[3][ty + 1][tx], pA0, pA1, s_c[0][ty + 1][tx], s_c[1][ty + 1][tx]);
+    add_to(a.v_o + o, dt * MT(rdy, j, i) *
+                          pgrad(gA0, gA1, s_c[2][ty + 1][tx], s_c[3][ty + 1][tx], pA0, pA1, s_c[0][ty + 1][tx],
+                                s_c[1][ty + 1][tx]));
 }
 
 // ------------------------------------------------------------------------
