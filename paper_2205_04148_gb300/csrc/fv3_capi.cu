@@ -268,14 +268,15 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
 
   // metric: concatenate members, FP64 and FP32 copies
   {
-    const int NM = 21;
+    const int NM = 25;
     std::vector<double> all[NM];
     for (int q = 0; q < NM; ++q) all[q].assign(c.elems2, NAN);
     for (int m = 0; m < c.nmem; ++m) {
       const HostMetric& M = HM[m];
       const std::vector<double>* src[NM] = {&M.area, &M.rarea, &M.fA, &M.dx, &M.rdx, &M.dyc, &M.rdyc,
                                             &M.cosy, &M.siny, nullptr, &M.dy, &M.rdy, &M.dxc, &M.rdxc,
-                                            &M.cosx, &M.sinx, nullptr, &M.fC, &M.rareac, nullptr, nullptr};
+                                            &M.cosx, &M.sinx, nullptr, &M.fC, &M.rareac, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr, nullptr};
       const long long o = c.geo[m].off2;
       for (int q = 0; q < NM; ++q)
         if (src[q]) std::copy(src[q]->begin(), src[q]->end(), all[q].begin() + o);
@@ -284,6 +285,10 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
         all[16][o + e] = 1.0 / (M.sinx[e] * M.sinx[e]);
         all[19][o + e] = M.dy[e] * M.rdxc[e];
         all[20][o + e] = M.dx[e] * M.rdyc[e];
+        all[21][o + e] = M.dy[e] / M.sinx[e];
+        all[22][o + e] = M.rdxc[e] / M.sinx[e];
+        all[23][o + e] = M.dx[e] / M.siny[e];
+        all[24][o + e] = M.rdyc[e] / M.siny[e];
       }
     }
     double* dptr[NM];
@@ -300,6 +305,7 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
       M.cosy = p[7]; M.siny = p[8]; M.rsin2y = p[9]; M.dy = p[10]; M.rdy = p[11]; M.dxc = p[12]; M.rdxc = p[13];
       M.cosx = p[14]; M.sinx = p[15]; M.rsin2x = p[16]; M.fC = p[17]; M.rareac = p[18];
       M.wx = p[19]; M.wy = p[20];
+      M.kfx = p[21]; M.kcx = p[22]; M.kfy = p[23]; M.kcy = p[24];
     };
     fill(c.Md, dptr);
     fill(c.Mf, fptr);

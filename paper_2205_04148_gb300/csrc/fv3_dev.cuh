@@ -45,6 +45,10 @@ struct Metric {
   const R *dy, *rdy, *dxc, *rdxc, *cosx, *sinx, *rsin2x; // x-faces
   const R *fC, *rareac;                                // corners
   const R *wx, *wy;  // dy/dxc on x-faces, dx/dyc on y-faces (damping weights)
+  // area-flux and Courant-number factors of the contravariant wind:
+  // dy / sin and 1 / (dxc sin) on x-faces, dx / sin and 1 / (dyc sin) on
+  // y-faces (xfx = dt (uc - cos v) kfx, crx = dt (uc - cos v) kcx)
+  const R *kfx, *kcx, *kfy, *kcy;
 };
 
 struct Params {

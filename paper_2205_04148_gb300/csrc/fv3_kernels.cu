@@ -133,7 +133,7 @@ __device__ __forceinline__ double ppm_face<double>(const double* q, int s, doubl
 template <typename R>
 struct TM {
   const R *area, *rarea, *fA, *dx, *rdx, *dyc, *rdyc, *cosy, *siny, *rsin2y, *dy, *rdy, *dxc, *rdxc, *cosx, *sinx,
-      *rsin2x, *fC, *rareac, *wx, *wy;
+      *rsin2x, *fC, *rareac, *wx, *wy, *kfx, *kcx, *kfy, *kcy;
   int pitch;
 };
 #define MT(name, j, i) __ldg(m.name + (long long)(j) * m.pitch + (i))
@@ -149,6 +149,7 @@ __device__ __forceinline__ TM<R> tile_metric(const Metric<R>& M, const Geo& g, i
   m.cosx = M.cosx + o; m.sinx = M.sinx + o; m.rsin2x = M.rsin2x + o;
   m.fC = M.fC + o; m.rareac = M.rareac + o;
   m.wx = M.wx + o; m.wy = M.wy + o;
+  m.kfx = M.kfx + o; m.kcx = M.kcx + o; m.kfy = M.kfy + o; m.kcy = M.kcy + o;
   m.pitch = g.pitch;
   return m;
 }
@@ -801,15 +802,16 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
   const int P = g.pitch;
   for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
-    const auto ut = (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]) * MT(rsin2x, j, i);
-    S.XFX[l] = dt * ut * MT(dy, j, i) * MT(sinx, j, i);
-    S.CRX[l] = dt * ut * MT(sinx, j, i) * MT(rdxc, j, i);
+    // dt ut dy sin and dt ut sin / dxc with ut = (uc - cos v) / sin^2
+    const auto du = dt * (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]);
+    S.XFX[l] = du * MT(kfx, j, i);
+    S.CRX[l] = du * MT(kcx, j, i);
   });
   for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const auto vt = (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]) * MT(rsin2y, j, i);
-    S.YFX[l] = dt * vt * MT(dx, j, i) * MT(siny, j, i);
-    S.CRY[l] = dt * vt * MT(siny, j, i) * MT(rdyc, j, i);
+    const auto dv = dt * (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]);
+    S.YFX[l] = dv * MT(kfy, j, i);
+    S.CRY[l] = dv * MT(kcy, j, i);
   });
   __syncthreads();
   inner_denominators(S, B);
