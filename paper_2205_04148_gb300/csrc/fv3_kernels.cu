@@ -371,6 +371,13 @@ template <typename R>
 __device__ __forceinline__ bool positive(R c) { return c > R(0); }
 template <>
 __device__ __forceinline__ bool positive<double>(double c) { return __double_as_longlong(c) > 0; }
+// |c| < 1 (false for NaN; FP64 on the integer pipe)
+template <typename R>
+__device__ __forceinline__ bool below_one(R c) { return fabs(c) < R(1); }
+template <>
+__device__ __forceinline__ bool below_one<double>(double c) {
+  return (__double_as_longlong(c) & 0x7fffffffffffffffLL) < 0x3ff0000000000000LL;
+}
 template <typename R>
 __device__ __forceinline__ R magnitude(R c) { return fabs(c); }
 template <>
@@ -874,7 +881,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       bool bad = false;
       for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
-        bad |= !(fabs(S.CRX[l]) < R(1)) || !(fabs(S.CRY[l]) < R(1));
+        bad |= !below_one(S.CRX[l]) || !below_one(S.CRY[l]);
       });
       if (bad) atomicOr(a.status, ST_CFL);
     }
@@ -916,8 +923,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       const int l = B.L(i, j);
       const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
       const R va = R(0.5) * (vc[G(j, i - 1)] + vc[G(j, i)]);
-      const R cu = dt * ua * (ua > R(0) ? MT(rdx, j, i - 1) : MT(rdx, j, i));
-      const R cv = dt * va * (va > R(0) ? MT(rdy, j - 1, i) : MT(rdy, j, i));
+      // the upwind edge length's reciprocal: one load of the chosen face
+      const R cu = dt * ua * MT(rdx, j, positive(ua) ? i - 1 : i);
+      const R cv = dt * va * MT(rdy, positive(va) ? j - 1 : j, i);
       const R ub = ppm_face(U + l, 1, cu);
       const R vb = ppm_face(V + l, SX, cv);
       KE[l] = R(0.5) * dt * (ub * ua + vb * va);
@@ -1067,8 +1075,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     R *dpc = a.delpc + o, *ptc = a.ptc + o, *wcc = a.wc + o;
     for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const int up[4] = {FX1[l] > R(0) ? l - 1 : l, FX1[l + 1] > R(0) ? l : l + 1, FY1[l] > R(0) ? l - SX : l,
-                         FY1[l + SX] > R(0) ? l : l + SX};
+      const int up[4] = {positive(FX1[l]) ? l - 1 : l, positive(FX1[l + 1]) ? l : l + 1,
+                         positive(FY1[l]) ? l - SX : l, positive(FY1[l + SX]) ? l : l + SX};
       const R F[4] = {FX1[l], FX1[l + 1], FY1[l], FY1[l + SX]};
       R fm[4], fp[4], fw[4];
 #pragma unroll
@@ -1157,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
       const R S[4] = {SXF[l], SXF[l + 1], SYF[l], SYF[l + TXW]};
       R Gf[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) Gf[f] = S[f] * (S[f] > R(0) ? GZ[lo[f]] : GZ[hi[f]]);
+      for (int f = 0; f < 4; ++f) Gf[f] = S[f] * (positive(S[f]) ? GZ[lo[f]] : GZ[hi[f]]);
       const R gzn = (GZ[l] * ar2 + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar2 + S[0] - S[1] + S[2] - S[3]);
       a.delzc[o + q] = fmin((gzn_below - gzn) * rgrav, -dzmin);
       gzn_below = gzn;
