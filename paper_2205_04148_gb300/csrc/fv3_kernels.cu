@@ -183,21 +183,28 @@ struct Blk {
 // sizes).  CW: the caller's extents fold to constants (a full block of a
 // compile-time shape), and the index arithmetic per point is a few integer
 // adds.
+// rot (in warps, running over the loops between two barriers): the loop's
+// first pass starts at warp rot, so its last, partial pass falls on the
+// warps after the ones that took the previous loop's last pass, and the
+// loops of one barrier interval share out their passes as one flat loop
+// would (without it the low warps take the extra pass of every loop and the
+// barrier waits for them).  Blocks of 256 threads (8 warps).
 template <bool CW = false, typename F>
-__device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
+__device__ __forceinline__ void for2(int& rot, int ilo, int ihi, int jlo, int jhi, F f) {
   const int w = ihi - ilo, h = jhi - jlo;
   if (w <= 0 || h <= 0) return;
   const int total = w * h;
+  constexpr int NT = 256;
+  const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+  const int e0 = (tid - 32 * rot) & (NT - 1);
   if constexpr (CW) {
-    // extents known at compile time (full blocks, 256 threads as (32, 8)):
-    // the first point by a division by the constant width, then steps of
-    // 256 points as constant increments of (i, j)
-    constexpr int NT = 256;
-    const int tid = (int)(threadIdx.y * 32 + threadIdx.x);
-    int j = tid / w, i = tid - j * w;
+    // extents known at compile time (full blocks): the first point by a
+    // division by the constant width, then steps of 256 points as constant
+    // increments of (i, j)
+    int j = e0 / w, i = e0 - j * w;
     const int dj = NT / w, di = NT - dj * w;
 #pragma unroll 1
-    for (int e = tid; e < total; e += NT) {
+    for (int e = e0; e < total; e += NT) {
       f(ilo + i, jlo + j);
       i += di;
       j += dj;
@@ -207,13 +214,20 @@ __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
       }
     }
   } else {
-    const int nthr = (int)(blockDim.x * blockDim.y);
     const float rw = 1.0f / (float)w;
-    for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < total; e += nthr) {
+    for (int e = e0; e < total; e += NT) {
       const int j = (int)(((float)e + 0.5f) * rw);
       f(ilo + (e - j * w), jlo + j);
     }
   }
+  rot = (rot + (total + 31) / 32) & (NT / 32 - 1);
+}
+
+// a loop on its own (the warps' first pass from warp 0)
+template <bool CW = false, typename F>
+__device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
+  int rot = 0;
+  for2<CW>(rot, ilo, ihi, jlo, jhi, f);
 }
 
 // The block's tile with its halo of 3 ([x0 - 3, x1 + 3) x [y0 - 3, y1 + 3)),
@@ -318,11 +332,12 @@ template <typename R, typename MR>
 __device__ __forceinline__ void inner_denominators(const TS<R, MR>& S, const Blk& B) {
   if constexpr (kStoreRD<R>) {
     const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
-    for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    int rot = 0;
+    for2(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
     });
-    for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
     });
@@ -356,14 +371,15 @@ __device__ __forceinline__ void assign_extra(TS<R, MR>& S, R* base, int SA, bool
 template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
 __device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
-  for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+  int rot = 0;
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AREA[l] = MT(area, j, i);
     S.RAREA[l] = MT(rarea, j, i);
   });
   if (weights) {
-    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
-    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
+    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
   }
 }
 
@@ -472,24 +488,25 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   R* const GX = FXO;
   R* const GY = FYO;
   R* const QJ = S.AL;  // the x-updated field
+  int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
   __syncthreads();  // Q (and the strips the corner turn reads) complete
   if (cc) {  // blocks at a cube corner: the missing quadrant for the y-sweep
     corner_roles(Q, B, n, 1);
     __syncthreads();
   }
   // 1: y-faces of the plain field (y-role corners)
-  for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
   });
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
   __syncthreads();
   // 2: inner y-update in every column of the block and its halo
-  for2<FULL>(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -499,12 +516,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     __syncthreads();
   }
   // x-faces of the plain field (x-role corners)
-  for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
   });
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -512,11 +529,11 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 3: Laplacian of the damping, inner x-update in every row of the block
   // and its halo
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
-  for2<FULL>(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     QJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
@@ -524,7 +541,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 4: outer x-faces of the y-updated field and outer y-faces of the
   // x-updated field; fluxes = mean face value x (mass or area) flux, plus
   // the del-4 damping flux
-  for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
     R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
@@ -535,7 +552,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     }
     FXO[l] = fl;
   });
-  for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R f = ppm_face(QJ + l, SX, S.CRY[l]);
     R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
@@ -558,6 +575,7 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     return;
   }
   const bool dmp = damp != R(0);
+  int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
   // the damping gradients live in the output arrays until the Laplacian is
   // formed; the fluxes are written only after it
   R* const GX = FXO;
@@ -583,12 +601,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // y-sweep of the plain field (y-role corners): edges, then faces
-  for2<FULL>(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
   });
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
@@ -596,13 +614,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRY, S.FY2, x0 - 3, x1 + 3, y0, y1 + 1, SX, B, F);
   else
-    for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
     });
   __syncthreads();
   // inner y-update in every column of the block and its halo
-  for2<FULL>(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -613,12 +631,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // x-sweep of the plain field (x-role corners)
-  for2<FULL>(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
   });
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -626,18 +644,18 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRX, S.FX2, x0, x1 + 1, y0 - 3, y1 + 3, 1, B, F);
   else
-    for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
     });
   if (dmp)
-    for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
   __syncthreads();
   // outer x-sweep of the y-updated field
-  for2<FULL>(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2], S.QIJ[l - 1], S.QIJ[l], S.QIJ[l + 1]);
   });
@@ -645,13 +663,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRX, FXO, x0, x1 + 1, y0, y1, 1, B, F);
     __syncthreads();
-    for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R fl = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
       FXO[l] = dmp ? fl + damp_x(l) : fl;
     });
   } else {
-    for2<FULL>(x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
       const R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
@@ -660,13 +678,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   }
   __syncthreads();
   // inner x-update in every row of the block and its halo
-  for2<FULL>(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
   __syncthreads();
   // outer y-sweep of the x-updated field
-  for2<FULL>(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2 * SX], S.QIJ[l - SX], S.QIJ[l], S.QIJ[l + SX]);
   });
@@ -674,13 +692,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRY, FYO, x0, x1, y0, y1 + 1, SX, B, F);
     __syncthreads();
-    for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R fl = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
       FYO[l] = dmp ? fl + damp_y(l) : fl;
     });
   } else {
-    for2<FULL>(x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
       const R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
@@ -699,17 +717,18 @@ struct TF {
   R *Q, *AL, *FY2, *FX2, *QIJ, *FXO, *FYO;
 };
 
-template <typename R, typename MR>
+template <int BX, int BY, bool FULL, typename R, typename MR>
 __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx,
                                const R* mfy) {
-  const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
+  int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
   __syncthreads();  // both tiles complete
   if (cc) {
     corner_roles(F[0].Q, B, n, 1);
     corner_roles(F[1].Q, B, n, 1);
     __syncthreads();
   }
-  for2(x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -718,13 +737,13 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     }
   });
   __syncthreads();
-  for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) F[f].FY2[l] = ppm_face_al(F[f].Q, F[f].AL, l, SX, S.CRY[l]);
   });
   __syncthreads();
-  for2(x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     const MR rd = inner_rdy(S, l, SX);
 #pragma unroll
@@ -736,7 +755,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     corner_roles(F[1].Q, B, n, 0);
     __syncthreads();
   }
-  for2(x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -745,13 +764,13 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     }
   });
   __syncthreads();
-  for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) F[f].FX2[l] = ppm_face_al(F[f].Q, F[f].AL, l, 1, S.CRX[l]);
   });
   __syncthreads();
-  for2(x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -760,7 +779,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     }
   });
   __syncthreads();
-  for2(x0, x1 + 1, y0, y1, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R w = mfx[l];
 #pragma unroll
@@ -770,7 +789,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     }
   });
   __syncthreads();
-  for2(x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     const MR rd = inner_rdx(S, l);
 #pragma unroll
@@ -778,7 +797,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
       F[f].QIJ[l] = (F[f].Q[l] * S.AREA[l] + F[f].FX2[l] * S.XFX[l] - F[f].FX2[l + 1] * S.XFX[l + 1]) * rd;
   });
   __syncthreads();
-  for2(x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -787,7 +806,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
     }
   });
   __syncthreads();
-  for2(x0, x1, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const R w = mfy[l];
 #pragma unroll
@@ -807,14 +826,15 @@ __device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
                         const TM<MR>& m, const Geo& g, R dt) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   const int P = g.pitch;
-  for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  int rot = 0;
+  for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     // dt ut dy sin and dt ut sin / dxc with ut = (uc - cos v) / sin^2
     const auto du = dt * (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]);
     S.XFX[l] = du * MT(kfx, j, i);
     S.CRX[l] = du * MT(kcx, j, i);
   });
-  for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const auto dv = dt * (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]);
     S.YFX[l] = dv * MT(kfy, j, i);
@@ -865,21 +885,22 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
     const R *uc = a.uc + o, *vc = a.vc + o;
+    int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
     auto G = [&](int j, int i) { return (long long)j * P + i; };
-    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = G(j, i);
       DP[l] = dp[q];
       PT[l] = pt[q];
       W[l] = w[q];
     });
-    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-    for2<FULL>(x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+    for2<FULL>(rot, x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     __syncthreads();
     courant<BX, BY, FULL>(uc, vc, V, U, S, B, m, g, dt);
     if (a.status) {  // Courant-number guard on the block's own faces
       bool bad = false;
-      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+      for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         bad |= !below_one(S.CRX[l]) || !below_one(S.CRY[l]);
       });
@@ -889,7 +910,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     transport<R, LEARN, BX, BY, FULL>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, MFX, MFY, a.mlp);
     R* dpo = a.delp_o + o;
-    for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
       DPN[l] = rcp(d);  // reciprocal, used by pt and w
@@ -903,7 +924,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
         transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
       else
         transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
-      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+      for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
             (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * DPN[l];
@@ -911,7 +932,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     }
     __syncthreads();
     // cell absolute vorticity (into PT)
-    for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
                V[l] * MT(dy, j, i)) * S.RAREA[l] + MT(fA, j, i);
@@ -919,7 +940,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     transport<R, false, BX, BY, FULL>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, FXO, FYO);
     // kinetic energy at corners from upwind-PPM corner winds
-    for2<FULL>(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
       const R va = R(0.5) * (vc[G(j, i - 1)] + vc[G(j, i)]);
@@ -932,31 +953,31 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     });
     __syncthreads();
     R *uo = a.u_o + o, *vo = a.v_o + o;
-    for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+    for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
       const int l = B.L(i, j);
       uo[G(j, i)] = U[l] + (FYO[l] + KE[l] - KE[l + 1]) * MT(rdx, j, i);
     });
-    for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       vo[G(j, i)] = V[l] + (-FXO[l] + KE[l] - KE[l + SX]) * MT(rdy, j, i);
     });
     if (a.xfxd) {  // the D-grid area fluxes for update_dz_d (reading R17)
-      for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
-      for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
+      for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
+      for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
     }
     if (a.amfx) {
       // the remapping step's sums: each face has one writer per launch, so
       // an addition performed at the memory side (a reduction whose result
       // is not read back) gives the sum a load-add-store gives, without the
       // load's round trip
-      for2<FULL>(x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+      for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
         atomicAdd(a.amfx + q, MFX[l]);
         atomicAdd(a.acrx + q, S.CRX[l]);
         atomicAdd(a.axfx + q, S.XFX[l]);
       });
-      for2<FULL>(x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+      for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
         atomicAdd(a.amfy + q, MFY[l]);
@@ -1551,14 +1572,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
   stage_metric<BX, BY, FULL>(S, B, m, false);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
-    for2<FULL>(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
+    for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
       S.CRX[l] = a.acrx[q] * fr;
       S.XFX[l] = a.axfx[q] * fr;
       MFX[l] = a.amfx[q] * fr;
     });
-    for2<FULL>(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
       S.CRY[l] = a.acry[q] * fr;
@@ -1567,7 +1589,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
     });
     __syncthreads();
     inner_denominators(S, B);
-    for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
       const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
@@ -1592,13 +1614,13 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
         if (tq + 2 < a.nq) tile_fetch<NPRE>(a.q[tq + 2] + o, pre, B, P);
         if (tq + 3 < a.nq) tile_fetch<NPRE>(a.q[tq + 3] + o, pre2, B, P);
         if (two)
-          transport_pair(TFP, S, B, n, cc, MFX, MFY);
+          transport_pair<BX, BY, FULL>(TFP, S, B, n, cc, MFX, MFY);
         else
           transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
         for (int f = 0; f < (two ? 2 : 1); ++f) {
           R* qo = a.q_o[tq + f] + o;
           const TF<R>& T = TFP[f];
-          for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+          for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
             const int l = B.L(i, j);
             qo[G(j, i)] =
                 (T.Q[l] * D0[l] + (T.FXO[l] - T.FXO[l + 1] + T.FYO[l] - T.FYO[l + SX]) * S.RAREA[l]) * D1[l];
@@ -1611,14 +1633,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
       __syncthreads();
       if (LEARN) {
         const R* q = a.q[tq] + o;
-        for2<FULL>(x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
+        for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) { Q[B.L(i, j)] = q[G(j, i)]; });
       } else {
         tile_put<NPRE>(Q, pre, B);
         if (tq + 1 < a.nq) tile_fetch<NPRE>(a.q[tq + 1] + o, pre, B, P);
       }
       transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
       R* qo = a.q_o[tq] + o;
-      for2<FULL>(x0, x1, y0, y1, [&](int i, int j) {
+      for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * D1[l];
       });
