@@ -341,8 +341,12 @@ fv3_status fv3_calibrate(fv3_ctx* ctx, int what, fv3_stream stream, double* work
  * what = 1: out = ln((x + y) / x), the log pressure ratio (atanh series for
  * small y / (2x + y)); what = 2: out = y / ln((x + y) / x), the layer pressure
  * of the column solve's gas-law split (series of u / atanh(u) for small
- * u = y / (2x + y)).  FV3_ERR_ARG for an unknown `what`, n < 0 or a NULL
- * array; FV3_ERR_CUDA if the launch fails. */
+ * u = y / (2x + y)); what = 3: out = 1/x from one reciprocal of x y (the
+ * column solve's thickness and pressure-sum reciprocals together, x y in the
+ * normal range); what = 4: out = x rounded to float and widened back to
+ * double by the integer-pipe conversion of the column solve's FP32 inputs.
+ * FV3_ERR_ARG for an unknown `what`, n < 0 or a NULL array;
+ * FV3_ERR_CUDA if the launch fails. */
 fv3_status fv3_math_check(int what, const double* x, const double* y, double* out, int n, fv3_stream stream);
 
 /* Block shape (bx x by cells) and level chunk of the horizontal kernels

@@ -68,20 +68,30 @@ double enqueue_calibration(Ctx& c, int what, cudaStream_t st) {
 
 // element-wise FP64 helpers of the kernels, for their accuracy tests:
 // what 0: out = rcp(x); 1: out = log_ratio(x + y, x, y);
-// 2: out = layer_mean_pressure(x + y, x, y)
+// 2: out = layer_mean_pressure(x + y, x, y); 3: out = 1 / x from
+// rcp_pair(x, y); 4: out = to_f64((float)x), the integer-pipe widening of a
+// float
 __global__ void k_math_check(int what, const double* x, const double* y, double* out, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  out[e] = what == 0 ? rcp(x[e])
-         : what == 1 ? log_ratio(x[e] + y[e], x[e], y[e])
-                     : layer_mean_pressure(x[e] + y[e], x[e], y[e]);
+  double v;
+  if (what == 0) v = rcp(x[e]);
+  else if (what == 1) v = log_ratio(x[e] + y[e], x[e], y[e]);
+  else if (what == 2) v = layer_mean_pressure(x[e] + y[e], x[e], y[e]);
+  else if (what == 3) {
+    double rb;
+    rcp_pair(x[e], y[e], v, rb);
+  } else {
+    v = to_f64(__double2float_rn(x[e]));
+  }
+  out[e] = v;
 }
 
 }  // namespace fv3
 
 extern "C" fv3_status fv3_math_check(int what, const double* x, const double* y, double* out, int n,
                                      fv3_stream stream) {
-  if (n < 0 || what < 0 || what > 2 || (n > 0 && (!x || !out || (what >= 1 && !y)))) return FV3_ERR_ARG;
+  if (n < 0 || what < 0 || what > 4 || (n > 0 && (!x || !out || (what >= 1 && !y)))) return FV3_ERR_ARG;
   if (n == 0) return FV3_OK;
   fv3::k_math_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(what, x, y, out, n);
   return cudaGetLastError() == cudaSuccess ? FV3_OK : FV3_ERR_CUDA;

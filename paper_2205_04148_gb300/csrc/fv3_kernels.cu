@@ -1229,11 +1229,13 @@ __global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowIt
   double* s_pe = a.scratch + 4LL * nz * NC;
   const double dt = FULL ? a.P.dt : 0.5 * a.P.dt, grav = a.P.grav, rd = a.P.rdgas, aimp = a.P.a_imp;
   const double kappa = a.P.rdgas / a.P.cp_air, gama = 1.0 / (1.0 - kappa);
-  // the loop-invariant quotients once; per level the reciprocals of the
-  // thickness, of the interface pressure sum (inside layer_mean_pressure) and
-  // of the pivot (FP64 here is 2 lanes per SM per clock, and a quotient costs
-  // several of them)
+  // the loop-invariant quotients once; per level one reciprocal for the
+  // thickness and the interface pressure sum together (rcp_pair) and one for
+  // the pivot (FP64 here is 2 lanes per SM per clock, and a quotient costs
+  // several of them).  kA2: a quarter of 1 / (g dt), so that (dp above + dp)
+  // kA2 is half the interface mass term m / dt of the tridiagonal row.
   const double rgrav = 1.0 / grav, rdt = 1.0 / dt, cC = aimp * dt * gama, rd_g = rd / grav;
+  const double kA2 = 0.25 * rgrav * rdt;
   const long long q = (long long)r.j * g.pitch + i;
   double pe = a.P.ptop, dpp = 0.0, wcp = 0.0, Cp = 0.0, ppp = 0.0, cpp = 0.0, dpv = 0.0;
   // Software pipeline over the levels: iteration k forms the coefficients of
@@ -1247,20 +1249,24 @@ __global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowIt
   const long long plane = g.plane;
   struct Row { double la, di, up, rhs; };
   auto coef = [&](int k, R dpr, R ptr, R wcr, R dzr) -> Row {
-    const double dpk = (double)dpr, ptk = (double)ptr, wck = (double)wcr, dzk = (double)dzr;
-    const double pen = pe + dpk;
-    const double rdz = rcp(dzk);
+    const double dpk = to_f64(dpr), ptk = to_f64(ptr), wck = to_f64(wcr), dzk = to_f64(dzr);
+    const double pen = pe + dpk, sum = pe + pen;
+    double rdz, rsum;
+    rcp_pair(dzk, sum, rdz, rsum);
     const double p = -dpk * rd_g * ptk * rdz;
-    const double ph = layer_mean_pressure(pen, pe, dpk);
+    const double ph = layer_mean_pressure(sum, rsum, pen, pe, dpk);
     const double pp = p - ph;
     const double C = -cC * p * rdz;
-    const double mm = k == 0 ? 0.5 * dpk * rgrav : 0.5 * (dpp + dpk) * rgrav;
-    const double wn = k == 0 ? wck : 0.5 * (wcp + wck);
+    // the interface mass over dt is m / dt = 2 A2 (the top interface: half
+    // its layer, dpp = 0 there), and its w the mean of the two layers'
+    // (the top interface: its layer's; wcp = wck there), so that
+    // m / dt * w = A2 (wcp + wck)
+    const double A2 = (dpp + dpk) * kA2;
     Row w;
-    w.la = -Cp;                      // lower (layer above the interface)
-    w.di = mm * rdt + Cp + C;        // diagonal
-    w.up = k < nz - 1 ? -C : 0.0;    // upper
-    w.rhs = mm * rdt * wn + pp - ppp;
+    w.la = -Cp;                        // lower (layer above the interface)
+    w.di = fma(2.0, A2, Cp) + C;       // diagonal
+    w.up = k < nz - 1 ? -C : 0.0;      // upper
+    w.rhs = fma(A2, wcp + wck, pp) - ppp;
     const long long sidx = (long long)k * NC + col;
     s_C[sidx] = C;
     s_pp[sidx] = pp;
@@ -1290,6 +1296,7 @@ __global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowIt
     dpv = dpt;
   };
   R ndp = a.delpc[o0], npt = a.ptc[o0], nwc = a.wc[o0], ndz = a.delzc[o0];
+  wcp = to_f64(nwc);
   Row cur = coef(0, ndp, npt, nwc, ndz);
   {
     const long long on = o0 + plane;  // nz >= 2
@@ -1315,7 +1322,7 @@ __global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowIt
   double bdp = s_dp[sidx], bcp = s_cp[sidx], bpp = s_pp[sidx], bC = s_C[sidx], bpe = 0.0;
   R bdz = a.delzc[fld0(g, g.off3, nz, r.t, nz - 1) + q];
   for (int k = nz - 1; k >= 0; --k) {
-    const double dpk = bdp, cpk = bcp, ppk = bpp, Ck = bC, pek = bpe, dzk = (double)bdz;
+    const double dpk = bdp, cpk = bcp, ppk = bpp, Ck = bC, pek = bpe, dzk = to_f64(bdz);
     const long long o = fld0(g, g.off3, nz, r.t, k) + q;
     if (k > 0) {
       bpe = s_pe[sidx];  // hydrostatic pressure of the interface below layer k - 1

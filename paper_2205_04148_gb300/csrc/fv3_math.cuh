@@ -90,6 +90,43 @@ __device__ __forceinline__ double log_ratio(double pen, double pe, double dp) {
   return 2.0 * u * s;
 }
 
+// x as a double.  A float is widened on the integer pipe (the conversion
+// instruction runs on the FP64 pipe, which the column solve keeps busy): the
+// exponent rebiased from 127 to 1023 and the fraction moved to the top of the
+// 52-bit field; subnormal floats normalised with a leading-zero count;
+// zeros and infinities keep their sign, a NaN its payload, made quiet.
+// Exact, as the conversion is.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) {
+  const unsigned b = __float_as_uint(x), a = b & 0x7fffffffu;
+  unsigned hi, lo;
+  if (a >= 0x7f800000u) {  // infinity, NaN (quiet)
+    hi = 0x7ff00000u | ((a & 0x007fffffu) >> 3) | (a > 0x7f800000u ? 0x00080000u : 0u);
+    lo = a << 29;
+  } else if (a >= 0x00800000u) {  // normal
+    hi = (a >> 3) + (896u << 20);
+    lo = a << 29;
+  } else if (a == 0u) {
+    hi = 0u;
+    lo = 0u;
+  } else {  // subnormal: a x 2^-149, the leading one moved to bit 23
+    const int sh = __clz((int)a) - 8;
+    const unsigned f = (a << sh) & 0x007fffffu;
+    hi = ((unsigned)(897 - sh) << 20) | (f >> 3);
+    lo = f << 29;
+  }
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// 1 / a and 1 / b from one reciprocal: r = 1 / (a b), then 1 / a = r b and
+// 1 / b = r a (two products instead of a second Newton-refined reciprocal;
+// within two ulps for a b in the normal range)
+__device__ __forceinline__ void rcp_pair(double a, double b, double& ra, double& rb) {
+  const double r = rcp(a * b);
+  ra = r * b;
+  rb = r * a;
+}
+
 // dp / ln(pen / pe) for pen = pe + dp, pe > 0, pen > 0: the pressure that
 // splits the gas-law pressure of a layer from its hydrostatic part in the
 // column solve.  With u = dp / (pe + pen), ln(pen / pe) = 2 atanh(u), so
@@ -98,34 +135,39 @@ __device__ __forceinline__ double log_ratio(double pen, double pe, double dp) {
 //   1 - v/3 - 4v^2/45 - 44v^3/945 - 428v^4/14175 - 10196v^5/467775
 //     - 10719068v^6/638512875 - 25865068v^7/1915538625
 //     - 5472607916v^8/488462349375 - ...
-// (the coefficients of the series division, exact rationals).  For |u| <= 1/8
-// the terms through v^8 leave a truncation below 1e-18 relative, for |u| <=
-// 1/32 (most layers below the top ones) the terms through v^4 one below 2e-17
-// (the next term is 0.022 v^5): one reciprocal and a polynomial instead of
-// the logarithm's series and a second reciprocal.  The thin upper layers
-// (larger u) divide by the library log.  The tiers are chosen on the integer
-// bits of |u|.
-__device__ __forceinline__ double layer_mean_pressure(double pen, double pe, double dp) {
-  const double sum = pe + pen;
-  const double u = dp * rcp(sum);
+// (the coefficients of the series division, exact rationals; below they are
+// halved, which carries the factor 1/2 through the polynomial without a
+// rounding).  For |u| <= 1/8 the terms through v^8 leave a truncation below
+// 1e-18 relative, for |u| <= 1/32 (most layers below the top ones) the terms
+// through v^4 one below 2e-17 (the next term is 0.022 v^5): one reciprocal
+// and a polynomial instead of the logarithm's series and a second
+// reciprocal.  The thin upper layers (larger u) divide by the library log.
+// The tiers are chosen on the integer bits of |u|.  sum = pe + pen, rsum its
+// reciprocal.
+__device__ __forceinline__ double layer_mean_pressure(double sum, double rsum, double pen, double pe, double dp) {
+  const double u = dp * rsum;
   const long long mag = __double_as_longlong(u) & 0x7fffffffffffffffLL;
   if (mag > 0x3fc0000000000000LL) return dp / log(pen / pe);  // |u| > 1/8
   const double v = u * u;
   double r;
   if (mag <= 0x3fa0000000000000LL) {  // |u| <= 1/32
-    r = -428.0 / 14175.0;
+    r = -214.0 / 14175.0;
   } else {
-    r = -5472607916.0 / 488462349375.0;
-    r = fma(r, v, -25865068.0 / 1915538625.0);
-    r = fma(r, v, -10719068.0 / 638512875.0);
-    r = fma(r, v, -10196.0 / 467775.0);
-    r = fma(r, v, -428.0 / 14175.0);
+    r = -2736303958.0 / 488462349375.0;
+    r = fma(r, v, -12932534.0 / 1915538625.0);
+    r = fma(r, v, -5359534.0 / 638512875.0);
+    r = fma(r, v, -5098.0 / 467775.0);
+    r = fma(r, v, -214.0 / 14175.0);
   }
-  r = fma(r, v, -44.0 / 945.0);
-  r = fma(r, v, -4.0 / 45.0);
-  r = fma(r, v, -1.0 / 3.0);
-  r = fma(r, v, 1.0);
-  return 0.5 * sum * r;
+  r = fma(r, v, -22.0 / 945.0);
+  r = fma(r, v, -2.0 / 45.0);
+  r = fma(r, v, -1.0 / 6.0);
+  r = fma(r, v, 0.5);
+  return sum * r;
+}
+__device__ __forceinline__ double layer_mean_pressure(double pen, double pe, double dp) {
+  const double sum = pe + pen;
+  return layer_mean_pressure(sum, rcp(sum), pen, pe, dp);
 }
 
 }  // namespace fv3

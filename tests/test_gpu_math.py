@@ -1,7 +1,9 @@
 """Accuracy of the kernels' FP64 helpers against exact references: the
 Newton-refined hardware reciprocal (used for the transport denominators and
-the column solve's pivots) and the log pressure ratio of the column solve
-(atanh series for thin layers, the library logarithm otherwise)."""
+the column solve's pivots), the paired reciprocal of the column solve (1/dz
+and 1/(pe + pen) from one reciprocal) and the log pressure ratio of the
+column solve (atanh series for thin layers, the library logarithm
+otherwise)."""
 import ctypes as C
 
 import numpy as np
@@ -34,6 +36,43 @@ def test_reciprocal_within_an_ulp():
     ulp = np.spacing(np.abs(exact))
     assert np.abs(r - exact).max() / ulp.max() <= 1.0
     assert (np.abs(r - exact) <= ulp).all()
+
+
+def test_paired_reciprocal_within_two_ulps():
+    """1/a as r b with r the reciprocal of a b: the reciprocal's ulp, the
+    rounding of a b and of the product r b, over the ranges of the column
+    solve (thickness -1e-1 .. -1e4 m, pressure sums 1e1 .. 3e5 Pa) and
+    beyond"""
+    rng = np.random.default_rng(4)
+    a = -(10.0 ** rng.uniform(-1, 4, 200000))
+    b = 10.0 ** rng.uniform(1, 5.5, 200000)
+    r = run(3, a, b)
+    exact = 1.0 / a
+    assert (np.abs(r - exact) <= 2 * np.spacing(np.abs(exact))).all()
+    a = 10.0 ** rng.uniform(-100, 100, 200000) * rng.choice([-1.0, 1.0], 200000)
+    b = 10.0 ** rng.uniform(-100, 100, 200000)
+    r = run(3, a, b)
+    exact = 1.0 / a
+    assert (np.abs(r - exact) <= 2 * np.spacing(np.abs(exact))).all()
+
+
+def test_float_widening_is_the_conversion():
+    """the column solve's integer-pipe widening of its FP32 inputs gives the
+    bits of the conversion: normal floats over the whole exponent range,
+    subnormal floats, signed zeros and infinities; NaNs stay NaNs"""
+    rng = np.random.default_rng(5)
+    bits = np.concatenate([rng.integers(0, 2**32, 400000, dtype=np.uint64),
+                           np.arange(0, 2**12, dtype=np.uint64),                 # small subnormals
+                           np.arange(0x007ff000, 0x00801000, dtype=np.uint64),   # largest subnormals, smallest normals
+                           np.arange(0x7f7ff000, 0x7f801000, dtype=np.uint64),   # largest normals, infinity, NaNs
+                           np.array([0x80000000, 0x80000001, 0xff800000, 0xffc00001, 0x7fc00000], dtype=np.uint64)])
+    f = bits.astype(np.uint32).view(np.float32)
+    with np.errstate(invalid="ignore"):   # signalling NaNs are made quiet
+        x = f.astype(np.float64)          # exact; the device rounds it back to the same float
+    got = run(4, x)
+    nan = np.isnan(x)
+    assert nan.any() and np.isnan(got[nan]).all()
+    assert np.array_equal(got[~nan].view(np.uint64), x[~nan].view(np.uint64))
 
 
 def test_log_ratio_matches_log1p():
