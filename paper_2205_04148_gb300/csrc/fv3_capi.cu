@@ -329,8 +329,8 @@ extern "C" fv3_status fv3_init_grid(fv3_ctx** out, const fv3_grid_desc* d, fv3_s
       const Geo& g = c.geo[m];
       mfirst.push_back((int)planes.size());
       for (int t = 0; t < nt; ++t) {
-        for (int y0 = 0; y0 < g.n; y0 += c.BYc)
-          for (int x0 = 0; x0 < g.n; x0 += c.BXc) dz.push_back({m, t, x0, y0});
+        for (int y0 = 0; y0 < g.n; y0 += kDzBY)
+          for (int x0 = 0; x0 < g.n; x0 += kDzBX) dz.push_back({m, t, x0, y0});
         for (int j = 0; j < g.n; ++j) rows.push_back({m, t, j, 0});
         for (int j = 0; j <= g.n; ++j) rows_f.push_back({m, t, j, 0});
         for (int k = 0; k < c.nz; ++k) planes.push_back(make_int4(m, t, k, 0));

@@ -429,6 +429,14 @@ __device__ __forceinline__ bool within_cells<double>(double a, double qa, double
   return ka >= lo && ka <= hi && ka >= 0;
 }
 
+// damping of a transport: none, always, or where the coefficient is not zero
+enum { DAMP_NO = 0, DAMP_YES = 1, DAMP_RT = 2 };
+template <int DM, typename R>
+__device__ __forceinline__ bool damped(R damp) {
+  if constexpr (DM == DAMP_RT) return damp != R(0);
+  else return DM == DAMP_YES;
+}
+
 // Learned face values (reading R14) over a 2-D range of faces with stride s
 // along the sweep: the plain PPM face value plus the mirror-symmetric
 // network's correction sig * y, or the plain value alone where the sum leaves
@@ -480,11 +488,11 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
 //   4  outer x-faces of QIJ and outer y-faces of the x-updated field, fluxes
 // The damping gradients live in the output arrays until the Laplacian is
 // formed, as in transport().
-template <int BX, int BY, bool FULL, typename R, typename MR>
+template <int BX, int BY, bool FULL, int DM, bool WDP, typename R, typename MR>
 __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx, const R* mfy,
                                 R damp, const R* wdp, R* FXO, R* FYO) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
-  const bool dmp = damp != R(0);
+  const bool dmp = damped<DM>(damp);
   R* const GX = FXO;
   R* const GY = FYO;
   R* const QJ = S.AL;  // the x-updated field
@@ -547,7 +555,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
     if (dmp) {
       R d = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
-      if (wdp) d = d * (R(0.5) * (wdp[l - 1] + wdp[l]));
+      if constexpr (WDP) d = d * (R(0.5) * (wdp[l - 1] + wdp[l]));
       fl = fl + d;
     }
     FXO[l] = fl;
@@ -558,7 +566,7 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
     if (dmp) {
       R d = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
-      if (wdp) d = d * (R(0.5) * (wdp[l - SX] + wdp[l]));
+      if constexpr (WDP) d = d * (R(0.5) * (wdp[l - SX] + wdp[l]));
       fl = fl + d;
     }
     FYO[l] = fl;
@@ -566,15 +574,23 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   __syncthreads();
 }
 
-template <typename R, bool LEARN = false, int BX = 0, int BY = 0, bool FULL = false, typename MR = R>
+// DM: DAMP_NO (no damping), DAMP_YES (the del-4 terms formed whatever the
+// coefficient; a zero coefficient adds zeros) or DAMP_RT (damping where the
+// coefficient is not zero, decided at run time); WDP: the damping flux is
+// weighted by the mean of wdp over the face.  Compile-time choices keep the
+// terms a transport does not form out of its loops altogether (a term
+// switched off at run time inside a loop may still be issued, with no lane
+// active, and FP64 instructions cost their pipe time either way).
+template <typename R, bool LEARN = false, int BX = 0, int BY = 0, bool FULL = false, int DM = DAMP_RT,
+          bool WDP = false, typename MR = R>
 __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   if constexpr (sizeof(R) == 4 && !LEARN) {
-    transport_fused<BX, BY, FULL>(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
+    transport_fused<BX, BY, FULL, DM, WDP>(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
     return;
   }
-  const bool dmp = damp != R(0);
+  const bool dmp = damped<DM>(damp);
   int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
   // the damping gradients live in the output arrays until the Laplacian is
   // formed; the fluxes are written only after it
@@ -587,12 +603,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   // formed (the Laplacian is complete by then)
   auto damp_x = [&](int l) -> R {
     R f = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
-    if (wdp) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
+    if constexpr (WDP) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
     return f;
   };
   auto damp_y = [&](int l) -> R {
     R f = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
-    if (wdp) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
+    if constexpr (WDP) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
     return f;
   };
   __syncthreads();  // Q (and the strips the corner turn reads) complete
@@ -907,7 +923,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       if (bad) atomicOr(a.status, ST_CFL);
     }
     // mass
-    transport<R, LEARN, BX, BY, FULL>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+    transport<R, LEARN, BX, BY, FULL, DAMP_YES>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, MFX, MFY, a.mlp);
     R* dpo = a.delp_o + o;
     for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
@@ -921,9 +937,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       R* Q = fld == 0 ? PT : W;
       R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
       if (LEARN && fld == 0)
-        transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
+        transport<R, LEARN, BX, BY, FULL, DAMP_YES, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
       else
-        transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+        transport<R, false, BX, BY, FULL, DAMP_YES, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
       for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
@@ -937,7 +953,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
                V[l] * MT(dy, j, i)) * S.RAREA[l] + MT(fA, j, i);
     });
-    transport<R, false, BX, BY, FULL>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+    transport<R, false, BX, BY, FULL, DAMP_YES>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, FXO, FYO);
     // kinetic energy at corners from upwind-PPM corner winds
     for2<FULL>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
@@ -1128,62 +1144,94 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
 }
 
 // ------------------------------------------------------------------------
-// update_dz_c (reading R8): blocks of columns marching up from the surface,
-// the interface geopotential of the block and its ring exchanged in shared
-// memory level by level.  Block: (BXc + 2) x (BYc + 2) threads.
+// update_dz_c (reading R8): blocks of 16 x 8 columns marching up from the
+// surface, the interface geopotential of the block and of its ring (the
+// columns around it, corners excluded) exchanged in shared memory level by
+// level.  128 threads: thread t owns the inner column (t % 16, t / 16) and
+// its west and south faces; threads 0 .. 47 also own one ring column (8 on
+// the west and east sides, 16 on the south and north sides), the east ring
+// the block's last x-face and the north ring its last y-face.  Every warp
+// holds inner columns, so the FP64 update of the inner cells runs on full
+// warps (ring threads of their own would issue it with no lane active).
+// The blocks are small so that a C96 sphere (55,296 columns, 432 blocks)
+// spreads evenly over the SMs: a block's level march is sequential, and the
+// busiest SM sets the time.
 // ------------------------------------------------------------------------
 template <typename R, typename MR = R>
-__global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int BYc) {
-  __shared__ R GZ[256];
-  __shared__ R SXF[256], SYF[256];  // twice the level-mean flux of each thread's west and south face
+__global__ void __launch_bounds__(kDzBX * kDzBY) k_update_dz_c(StepArgs<R> a) {
+  constexpr int BX = kDzBX, BY = kDzBY, W = BX + 2, H = BY + 2;
+  __shared__ R GZ[W * H];
+  __shared__ R SXF[W * H], SYF[W * H];  // twice the level-mean flux of the west / south face of a frame cell
   const Item it = a.items[blockIdx.x];
   const Geo g = a.geo[it.m];
   const int n = g.n, P = g.pitch, nz = g.nz;
-  const int x0 = it.x0, y0 = it.y0, x1 = min(x0 + BXc, n), y1 = min(y0 + BYc, n);
-  const int tx = threadIdx.x, ty = threadIdx.y, TXW = blockDim.x;
-  const int i = x0 - 1 + tx, j = y0 - 1 + ty;
-  const bool ring = (i == x0 - 1 || i == x1) , ringy = (j == y0 - 1 || j == y1);
-  const bool valid = i >= x0 - 1 && i <= x1 && j >= y0 - 1 && j <= y1 && !(ring && ringy);
-  const bool inner = i >= x0 && i < x1 && j >= y0 && j < y1;
-  // the thread forms the flux of its west x-face (faces x0 .. x1 of the
-  // block's rows) and of its south y-face (faces y0 .. y1 of its columns);
-  // a cell reads its east and north faces from the neighbours
-  const bool fxo = i >= x0 && i <= x1 && j >= y0 && j < y1;
-  const bool fyo = j >= y0 && j <= y1 && i >= x0 && i < x1;
+  const int x0 = it.x0, y0 = it.y0, x1 = min(x0 + BX, n), y1 = min(y0 + BY, n);
+  const int t = (int)threadIdx.x;
+  const int i = x0 + t % BX, j = y0 + t / BX;
+  const bool inner = i < x1 && j < y1;
+  const int l = (j - y0 + 1) * W + (i - x0 + 1);
+  // the ring column of threads 0 .. 2 (BX + BY) - 1: west, east, south, north
+  const int side = t < BY ? 0 : (t < 2 * BY ? 1 : (t < 2 * BY + BX ? 2 : 3));
+  const int pos = side == 0 ? t : (side == 1 ? t - BY : (side == 2 ? t - 2 * BY : t - 2 * BY - BX));
+  const int ri = side == 0 ? x0 - 1 : (side == 1 ? x1 : x0 + pos);
+  const int rj = side <= 1 ? y0 + pos : (side == 2 ? y0 - 1 : y1);
+  const bool ring = t < 2 * (BX + BY) && (side <= 1 ? rj < y1 : ri < x1);
+  const bool rfx = ring && side == 1, rfy = ring && side == 3;
+  const int rl = (rj - y0 + 1) * W + (ri - x0 + 1);
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const R grav = (R)a.P.grav, dzmin = (R)a.P.dz_min, rgrav = (R)(1.0 / a.P.grav);
-  const long long q = (long long)j * P + i;
-  R gzr = R(0), gzn_below = R(0);
-  const int l = ty * TXW + tx;
-  const int lo[4] = {l - 1, l, l - TXW, l};
-  const int hi[4] = {l, l + 1, l, l + TXW};
-  auto fx = [&](int K) { return a.fx1[fld0(g, g.off3, nz, it.t, K) + q]; };
-  auto fy = [&](int K) { return a.fy1[fld0(g, g.off3, nz, it.t, K) + q]; };
+  const long long q = (long long)j * P + i, rq = (long long)rj * P + ri;
+  const int lo[4] = {l - 1, l, l - W, l};
+  const int hi[4] = {l, l + 1, l, l + W};
+  auto lev = [&](int K) { return fld0(g, g.off3, nz, it.t, K); };
   // The level loop is sequential: the loads run ahead of it (delz one level,
   // the fluxes two levels), so their latency overlaps the level before.  The
   // update is written with twice the level-mean fluxes S = fx(K-1) + fx(K)
   // (2 fx(0) at the top) and twice the area: numerator and denominator both
   // scale by exactly 2, so the quotient is the one of the mean fluxes.
   const MR ar2 = inner ? MR(2) * MT(area, j, i) : MR(1);
+  R gzr = R(0), gzn_below = R(0), rgz = R(0);
   R xb = R(0), xa = R(0), xn = R(0), yb = R(0), ya = R(0), yn = R(0);  // levels K, K - 1, K - 2
-  R dzk = valid ? a.delz[fld0(g, g.off3, nz, it.t, nz - 1) + q] : R(0);
-  if (fxo) { xb = fx(nz - 1); xa = fx(nz - 2); }  // nz >= 2
-  if (fyo) { yb = fy(nz - 1); ya = fy(nz - 2); }
+  R fb = R(0), fa = R(0), fn = R(0);                                    // the ring face's flux
+  const R* rflux = rfx ? a.fx1 : a.fy1;
+  R dzk = R(0), rdz = R(0);
+  {
+    const long long o = lev(nz - 1), o1 = lev(nz - 2);  // nz >= 2
+    if (inner) {
+      dzk = a.delz[o + q];
+      xb = a.fx1[o + q]; xa = a.fx1[o1 + q];
+      yb = a.fy1[o + q]; ya = a.fy1[o1 + q];
+    }
+    if (ring) rdz = a.delz[o + rq];
+    if (rfx || rfy) { fb = rflux[o + rq]; fa = rflux[o1 + rq]; }
+  }
   for (int K = nz - 1; K >= 0; --K) {
-    const long long o = fld0(g, g.off3, nz, it.t, K);
-    R dzn = R(0);
-    if (valid && K > 0) dzn = a.delz[o - g.plane + q];
-    if (fxo && K >= 2) xn = fx(K - 2);
-    if (fyo && K >= 2) yn = fy(K - 2);
-    if (valid) {
+    const long long o = lev(K);
+    R dzn = R(0), rdzn = R(0);
+    if (K > 0) {
+      if (inner) dzn = a.delz[o - g.plane + q];
+      if (ring) rdzn = a.delz[o - g.plane + rq];
+    }
+    if (K >= 2) {
+      const long long o2 = o - 2 * g.plane;
+      if (inner) { xn = a.fx1[o2 + q]; yn = a.fy1[o2 + q]; }
+      if (rfx || rfy) fn = rflux[o2 + rq];
+    }
+    if (inner) {
       gzr = gzr - grav * dzk;
       GZ[l] = gzr;
+      SXF[l] = K == 0 ? R(2) * xb : xa + xb;
+      SYF[l] = K == 0 ? R(2) * yb : ya + yb;
     }
-    if (fxo) SXF[l] = K == 0 ? R(2) * xb : xa + xb;
-    if (fyo) SYF[l] = K == 0 ? R(2) * yb : ya + yb;
+    if (ring) {
+      rgz = rgz - grav * rdz;
+      GZ[rl] = rgz;
+      if (rfx) SXF[rl] = K == 0 ? R(2) * fb : fa + fb;
+      if (rfy) SYF[rl] = K == 0 ? R(2) * fb : fa + fb;
+    }
     __syncthreads();
     if (inner) {
-      const R S[4] = {SXF[l], SXF[l + 1], SYF[l], SYF[l + TXW]};
+      const R S[4] = {SXF[l], SXF[l + 1], SYF[l], SYF[l + W]};
       R Gf[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) Gf[f] = S[f] * (positive(S[f]) ? GZ[lo[f]] : GZ[hi[f]]);
@@ -1192,7 +1240,9 @@ __global__ void __launch_bounds__(256) k_update_dz_c(StepArgs<R> a, int BXc, int
       gzn_below = gzn;
     }
     xb = xa; xa = xn; yb = ya; ya = yn;
+    fb = fa; fa = fn;
     dzk = dzn;
+    rdz = rdzn;
     __syncthreads();
   }
 }
@@ -1623,7 +1673,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
         if (two)
           transport_pair<BX, BY, FULL>(TFP, S, B, n, cc, MFX, MFY);
         else
-          transport<R, false, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
+          transport<R, false, BX, BY, FULL, DAMP_NO>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO);
         for (int f = 0; f < (two ? 2 : 1); ++f) {
           R* qo = a.q_o[tq + f] + o;
           const TF<R>& T = TFP[f];
@@ -1645,7 +1695,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
         tile_put<NPRE>(Q, pre, B);
         if (tq + 1 < a.nq) tile_fetch<NPRE>(a.q[tq + 1] + o, pre, B, P);
       }
-      transport<R, LEARN, BX, BY, FULL>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO, a.mlp);
+      transport<R, LEARN, BX, BY, FULL, DAMP_NO>(Q, S, B, m, n, cc, MFX, MFY, R(0), (const R*)nullptr, FXO, FYO,
+                                                  a.mlp);
       R* qo = a.q_o[tq] + o;
       for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
@@ -2047,7 +2098,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(2)) {  // update_dz_c
     StepArgs<R> b = a;
     b.items = c.items_dz;
-    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(kDzBX * kDzBY), 0, st>>>(b);
     ++c.launches;
   }
   if (run(3)) {  // riem_solver_c
@@ -2088,7 +2139,7 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
   if (run(7)) {  // update_dz_d: the D-grid area fluxes of d_sw over the state delz
     StepArgs<R> b = a;
     b.items = c.items_dz;
-    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(c.BXc + 2, c.BYc + 2), 0, st>>>(b, c.BXc, c.BYc);
+    k_update_dz_c<R, MR><<<dim3(c.n_items_dz), dim3(kDzBX * kDzBY), 0, st>>>(b);
     ++c.launches;
   }
   if (run(8)) {  // riem_solver3 on the state after d_sw

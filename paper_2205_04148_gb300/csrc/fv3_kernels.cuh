@@ -9,6 +9,7 @@
 namespace fv3 {
 
 constexpr int MAX_TRACERS = 16;
+constexpr int kDzBX = 16, kDzBY = 8;  // update_dz_c: blocks of 16 x 8 columns
 constexpr int MAX_HALO_FIELDS = 24;
 constexpr int NSPLT_MAX = 4;
 
@@ -97,7 +98,7 @@ struct Ctx {
   HaloEntry* plan_d[K_NUM] = {};
   int plan_n[K_NUM] = {};
   // work lists
-  int BX = 32, BY = 8, BXc = 30, BYc = 6, kchunk = 8;
+  int BX = 32, BY = 8, kchunk = 8;
   int persistent = 0;  // 1: horizontal kernels run on a GPU-filling persistent grid
   Item* items_hz = nullptr;
   int n_items_hz = 0;
