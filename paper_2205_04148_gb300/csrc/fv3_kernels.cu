@@ -1403,8 +1403,12 @@ __global__ void __launch_bounds__(kRiemCols) k_riem_c(StepArgs<R> a, const RowIt
 }
 
 // ------------------------------------------------------------------------
-// p_grad_c (reading R10): one thread per (i, j) updates the x-face and the
-// y-face at (i, j).  Plane list entries (m, t, k).
+// p_grad_c (reading R10): the first nbi x nbi blocks of a plane are 16 x 16
+// cells, one thread per cell (i, j) updating its west x-face and its south
+// y-face; the blocks after them take the east x-faces (i = n) and the north
+// y-faces (j = n) of the tile as one flat list, 32 to a warp (a block of
+// cells at the edge would hold one face per row).  Plane list entries
+// (m, t, k).
 // ------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R pgrad(R gA0, R gA1, R gB0, R gB1, R pA0, R pA1, R pB0, R pB1) {
@@ -1412,12 +1416,24 @@ __device__ __forceinline__ R pgrad(R gA0, R gA1, R gB0, R gB1, R pA0, R pA1, R p
 }
 
 template <typename R, typename MR = R>
-__global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
+__global__ void __launch_bounds__(256) k_p_grad_c(StepArgs<R> a, const int4* planes, int nbi) {
   const int4 pl = planes[blockIdx.z];
   const Geo g = a.geo[pl.x];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = g.n;
-  if (i > n || j > n) return;
+  const int n = g.n, b = (int)blockIdx.x;
+  int i, j;
+  bool xf = true, yf = true;
+  if (b < nbi * nbi) {
+    i = (b % nbi) * 16 + (int)threadIdx.x;
+    j = (b / nbi) * 16 + (int)threadIdx.y;
+    if (i >= n || j >= n) return;
+  } else {
+    const int e = (b - nbi * nbi) * 256 + (int)(threadIdx.y * 16 + threadIdx.x);
+    if (e >= 2 * n) return;
+    xf = e < n;
+    yf = !xf;
+    i = xf ? n : e - n;
+    j = xf ? e : n;
+  }
   const int t = pl.y, k = pl.z;
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, t);
   const R dt2 = R(0.5 * a.P.dt);
@@ -1427,11 +1443,11 @@ __global__ void k_p_grad_c(StepArgs<R> a, const int4* planes) {
   const R* z0 = a.gz + fld0(g, g.offi, g.nz + 1, t, k);
   const R* z1 = a.gz + fld0(g, g.offi, g.nz + 1, t, k + 1);
   const long long B = (long long)j * g.pitch + i;
-  if (j < n) {
+  if (xf) {
     const long long A = B - 1;
     add_to(a.uc + o + B, dt2 * MT(rdxc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]));
   }
-  if (i < n) {
+  if (yf) {
     const long long A = B - g.pitch;
     add_to(a.vc + o + B, dt2 * MT(rdyc, j, i) * pgrad(z0[A], z1[A], z0[B], z1[B], p0[A], p1[A], p0[B], p1[B]));
   }
@@ -2110,8 +2126,8 @@ static void substep_t(Ctx& c, const StateView& in, const StateView& out, const P
     F.push_back(hf(c, K_CELL1, c.pef, nullptr, c.nz + 1, 1));
     F.push_back(hf(c, K_CELL1, c.gz, nullptr, c.nz + 1, 1));
     enqueue_halo_fields(c, F, st);
-    const int nb = (c.max_n + 1 + 15) / 16;
-    k_p_grad_c<R, MR><<<dim3(nb, nb, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes);
+    const int nbi = (c.max_n + 15) / 16, ne = (2 * c.max_n + 255) / 256;
+    k_p_grad_c<R, MR><<<dim3(nbi * nbi + ne, 1, c.n_planes), dim3(16, 16), 0, st>>>(a, c.planes, nbi);
     ++c.launches;
   }
   if (run(5)) {  // C-grid winds into the halo
