@@ -1639,27 +1639,34 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   const bool cc = g.cubed && (x0 == 0 || x1 == n) && (y0 == 0 || y1 == n);
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
-  const R fr = R(1) / R(*a.nsplt);
+  const int nsplt = *a.nsplt;
+  const R fr = R(1) / R(nsplt);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
   stage_metric<BX, BY, FULL>(S, B, m, false);  // read after the first barrier of the level loop
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
-    for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
-      const int l = B.L(i, j);
-      const long long q = o + G(j, i);
-      S.CRX[l] = a.acrx[q] * fr;
-      S.XFX[l] = a.axfx[q] * fr;
-      MFX[l] = a.amfx[q] * fr;
-    });
-    for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
-      const int l = B.L(i, j);
-      const long long q = o + G(j, i);
-      S.CRY[l] = a.acry[q] * fr;
-      S.YFX[l] = a.ayfx[q] * fr;
-      MFY[l] = a.amfy[q] * fr;
-    });
+    // the remapping step's sums, divided among the subcycles (a multiply by
+    // 1 left out altogether when there is one: a branch for the whole block)
+    auto split = [&](bool one) {
+      for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+        const int l = B.L(i, j);
+        const long long q = o + G(j, i);
+        S.CRX[l] = one ? a.acrx[q] : a.acrx[q] * fr;
+        S.XFX[l] = one ? a.axfx[q] : a.axfx[q] * fr;
+        MFX[l] = one ? a.amfx[q] : a.amfx[q] * fr;
+      });
+      for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        const long long q = o + G(j, i);
+        S.CRY[l] = one ? a.acry[q] : a.acry[q] * fr;
+        S.YFX[l] = one ? a.ayfx[q] : a.ayfx[q] * fr;
+        MFY[l] = one ? a.amfy[q] : a.amfy[q] * fr;
+      });
+    };
+    if (nsplt == 1) split(true);
+    else split(false);
     __syncthreads();
     inner_denominators(S, B);
     for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
