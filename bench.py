@@ -34,6 +34,7 @@ C96 per step), on the host cores of this machine.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -62,15 +63,26 @@ DSW_WORDS_PER_CELL = 12
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (profiling recipe table)
 # DRAM bytes (read + write) per cell of one d_sw launch come from ncu
 # captures of the kernel in given launch configurations (precision, block
-# shape, level chunk, launch mode), recorded with the source commit of the
-# capture in profiles/dram_traffic.json; the roofline object scales them by
-# the cells of the timed launch (the traffic grows in proportion to the work
-# items) and says so.  A configuration without a capture reports null.
+# shape, level chunk, launch mode), recorded with a hash of the kernel
+# sources they were taken on in profiles/dram_traffic.json; the roofline
+# object scales them by the cells of the timed launch (the traffic grows in
+# proportion to the work items) and says so.  A configuration without a
+# capture, or whose capture was taken on other kernel sources, reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+KERNEL_SOURCES = ("fv3_kernels.cu", "fv3_kernels.cuh", "fv3_dev.cuh", "fv3_math.cuh")
+
+
+def source_sha():
+    """sha256 over the sources the stencil kernels are compiled from"""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2205_04148_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def dram_traffic(kernel, prec, bx, by, kc, persistent, cells):
-    """(bytes per launch scaled from a capture, the capture's record) or (None, None)"""
+    """(bytes per launch scaled from a capture, the capture's record) or (None, record or None)"""
     try:
         caps = json.load(open(TRAFFIC_FILE))["captures"]
     except (OSError, ValueError, KeyError):
@@ -78,8 +90,11 @@ def dram_traffic(kernel, prec, bx, by, kc, persistent, cells):
     for c in caps:
         if (c["kernel"], c["precision"], c["bx"], c["by"], c["kchunk"], bool(c["persistent"])) == \
                 (kernel, prec, bx, by, kc, bool(persistent)):
-            rec = {k: c[k] for k in ("bytes_per_cell", "capture_cells", "capture", "commit", "fp64_flops_per_cell")
-                   if k in c}
+            rec = {k: c[k] for k in ("bytes_per_cell", "capture_cells", "capture", "source_sha",
+                                     "fp64_flops_per_cell") if k in c}
+            if c.get("source_sha") != source_sha():
+                rec["stale"] = "the kernel sources changed since this capture: traffic not reported"
+                return None, rec
             rec["scaled"] = "bytes per cell of the capture x cells of the timed launch"
             return c["bytes_per_cell"] * cells, rec
     return None, None
