@@ -402,7 +402,8 @@ def ours(a):
                 "frac": ach / FP64_PEAK_NOMINAL_GFLOPS, "traffic": traffic, "traffic_capture": traffic_rec,
                 "kernel": "k_d_sw<double>",
                 "ms_per_launch": t_dsw * 1e3, "flops_per_cell": DSW_FLOPS_PER_CELL,
-                "flops_per_cell_executed": (traffic_rec or {}).get("fp64_flops_per_cell"),
+                "flops_per_cell_executed": (None if (traffic_rec or {}).get("stale")
+                                            else (traffic_rec or {}).get("fp64_flops_per_cell")),
                 "peak_measured_fma": fp64_meas,
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe; live DFMA calibration beside it",
                 "hbm": hbm_obj}
