@@ -79,14 +79,7 @@ __device__ __forceinline__ R ppm_face(const R* q, int s, R c) {
   const R qu = p[0];
   R bl = ppm_edge(p[-2 * s], p[-s], p[0], p[s]) - qu;
   R br = ppm_edge(p[-s], p[0], p[s], p[2 * s]) - qu;
-  if (bl * br >= R(0)) {
-    bl = R(0);
-    br = R(0);
-  } else if (fabs(bl) > R(2) * fabs(br)) {
-    bl = R(-2) * br;
-  } else if (fabs(br) > R(2) * fabs(bl)) {
-    br = R(-2) * bl;
-  }
+  ppm_limit(bl, br);
   const R ac = fabs(c);
   const R x = (c > R(0)) ? br : bl;
   return qu + (R(1) - ac) * (x - ac * (bl + br));

@@ -24,17 +24,18 @@ __device__ __forceinline__ long long twice_mag(long long m) {
 }
 
 // monotone limiter on the cell's deviations (generic, then FP64 on the
-// integer pipe -- see okey / twice_mag above)
+// integer pipe -- see okey / twice_mag above).  The cases are: a local
+// extremum (bl br >= 0: both zero), |bl| > 2|br| (bl = -2 br) and |br| > 2|bl|
+// (br = -2 bl); the last two cannot both hold, so each deviation is one
+// select of its own (no branch: the warp's lanes take different cases)
 template <typename R>
 __device__ __forceinline__ void ppm_limit(R& bl, R& br) {
-  if (bl * br >= R(0)) {
-    bl = R(0);
-    br = R(0);
-  } else if (fabs(bl) > R(2) * fabs(br)) {
-    bl = R(-2) * br;
-  } else if (fabs(br) > R(2) * fabs(bl)) {
-    br = R(-2) * bl;
-  }
+  const bool ext = bl * br >= R(0);
+  const R abl = fabs(bl), abr = fabs(br);
+  const R nl = abl > R(2) * abr ? R(-2) * br : bl;
+  const R nr = abr > R(2) * abl ? R(-2) * bl : br;
+  bl = ext ? R(0) : nl;
+  br = ext ? R(0) : nr;
 }
 template <>
 __device__ __forceinline__ void ppm_limit<double>(double& bl, double& br) {
@@ -55,9 +56,18 @@ __device__ __forceinline__ void ppm_limit<double>(double& bl, double& br) {
 // (rcp.approx.ftz.f64) refined by two Newton-Raphson steps
 // r <- r + r (1 - x r), each of which squares the relative error; within an
 // ulp of the quotient for normal x (checked against division by
-// fv3_math_check).  The float path divides.
+// fv3_math_check).  FP32: the hardware approximation (rcp.approx.ftz.f32,
+// within an ulp) and one Newton-Raphson step, three instructions where the
+// IEEE division takes a range check, a branch and several more (the FP32
+// stencils are bound by instruction issue); normal x only.
 template <typename R>
-__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+__device__ __forceinline__ R rcp(R x);
+template <>
+__device__ __forceinline__ float rcp<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 template <>
 __device__ __forceinline__ double rcp<double>(double x) {
   double r;
