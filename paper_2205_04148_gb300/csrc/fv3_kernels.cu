@@ -948,7 +948,22 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     });
     transport<R, false, BX, BY, FULL, DAMP_YES>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, FXO, FYO);
-    // kinetic energy at corners from upwind-PPM corner winds
+    // kinetic energy at corners from upwind-PPM corner winds.  FP64: the
+    // edge values of u along x and of v along y once each (into the free
+    // transport arrays AL and QIJ), as the transports do, instead of two per
+    // corner and wind; FP32 forms them in the corner loop (cheaper there than
+    // the barrier)
+    if constexpr (kStoreRD<R>) {
+      for2<FULL>(rot, x0 - 1, x1 + 2, y0, y1 + 1, [&](int i, int j) {
+        const int l = B.L(i, j);
+        S.AL[l] = ppm_edge(U[l - 2], U[l - 1], U[l], U[l + 1]);
+      });
+      for2<FULL>(rot, x0, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+        const int l = B.L(i, j);
+        S.QIJ[l] = ppm_edge(V[l - 2 * SX], V[l - SX], V[l], V[l + SX]);
+      });
+      __syncthreads();
+    }
     for2<FULL>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
@@ -956,8 +971,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       // the upwind edge length's reciprocal: one load of the chosen face
       const R cu = dt * ua * MT(rdx, j, positive(ua) ? i - 1 : i);
       const R cv = dt * va * MT(rdy, positive(va) ? j - 1 : j, i);
-      const R ub = ppm_face(U + l, 1, cu);
-      const R vb = ppm_face(V + l, SX, cv);
+      R ub, vb;
+      if constexpr (kStoreRD<R>) {
+        ub = ppm_face_al(U, S.AL, l, 1, cu);
+        vb = ppm_face_al(V, S.QIJ, l, SX, cv);
+      } else {
+        ub = ppm_face(U + l, 1, cu);
+        vb = ppm_face(V + l, SX, cv);
+      }
       KE[l] = R(0.5) * dt * (ub * ua + vb * va);
     });
     __syncthreads();
