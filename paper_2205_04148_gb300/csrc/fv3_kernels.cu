@@ -62,6 +62,25 @@ __device__ __forceinline__ void add_to(R* p, T v) {
   else *p = (R)((T)*p + v);
 }
 
+// sign and magnitude tests (FP64 on the integer pipe)
+template <typename R>
+__device__ __forceinline__ bool positive(R c) { return c > R(0); }
+template <>
+__device__ __forceinline__ bool positive<double>(double c) { return __double_as_longlong(c) > 0; }
+// |c| < 1 (false for NaN; FP64 on the integer pipe)
+template <typename R>
+__device__ __forceinline__ bool below_one(R c) { return fabs(c) < R(1); }
+template <>
+__device__ __forceinline__ bool below_one<double>(double c) {
+  return (__double_as_longlong(c) & 0x7fffffffffffffffLL) < 0x3ff0000000000000LL;
+}
+template <typename R>
+__device__ __forceinline__ R magnitude(R c) { return fabs(c); }
+template <>
+__device__ __forceinline__ double magnitude<double>(double c) {
+  return __longlong_as_double(__double_as_longlong(c) & 0x7fffffffffffffffLL);
+}
+
 // ------------------------------------------------------------------------
 // PPM (reading R4)
 // ------------------------------------------------------------------------
@@ -71,18 +90,51 @@ __device__ __forceinline__ R ppm_edge(R qm, R q0, R q1, R qp) {
   return fmin(fmax(al, fmin(q0, q1)), fmax(q0, q1));
 }
 
-// face value at the face left of q[0] (between q[-s] and q[0]) for Courant
-// number c; the upwind cell is picked first so the warp does one evaluation.
+// A face's Courant number c as the sweeps keep it: w = 1 - |c|, the part of
+// the upwind cell that does not cross the face in a step, carrying the sign
+// of the upwind side (+w when c > 0: the cell before the face is upwind; -w
+// when c <= 0; a zero weight keeps the side in its sign bit, see
+// upwind_before).  Formed once per face, it spares every face value of every
+// sweep and field a 1 - |c| of its own.  Requires |c| <= 1 (the Courant
+// guard flags |c| >= 1).
 template <typename R>
-__device__ __forceinline__ R ppm_face(const R* q, int s, R c) {
-  const R* p = (c > R(0)) ? q - s : q;
+__device__ __forceinline__ R upwind_weight(R c) {
+  const R w = R(1) - magnitude(c);
+  return positive(c) ? w : -w;
+}
+
+// the side an upwind weight names: the sign bit (so that |c| = 1, w = 0,
+// keeps its side: +0 before the face, -0 after it)
+template <typename R>
+__device__ __forceinline__ bool upwind_before(R cw) {
+  if constexpr (sizeof(R) == 8) return __double_as_longlong(cw) >= 0;
+  else return __float_as_int(cw) >= 0;
+}
+
+// the mean over the swept part of the upwind cell's limited parabola (mean
+// qu, deviations bl and br at its two edges): qu + w (w (bl + br) - y), y the
+// deviation at the cell's far edge from the face (bl when the cell before the
+// face is upwind) -- the value of qu + (1 - |c|) (x - |c| (bl + br)), x the
+// deviation at the near edge, since x - (bl + br) = -y
+template <typename R>
+__device__ __forceinline__ R swept_mean(R qu, R bl, R br, R cw) {
+  const R w = magnitude(cw);
+  const R y = upwind_before(cw) ? bl : br;
+  if constexpr (sizeof(R) == 8) return fma(w, fma(w, bl + br, -y), qu);
+  else return fmaf(w, fmaf(w, bl + br, -y), qu);
+}
+
+// face value at the face left of q[0] (between q[-s] and q[0]) for the
+// upwind weight cw of the face; the upwind cell is picked first so the warp
+// does one evaluation.
+template <typename R>
+__device__ __forceinline__ R ppm_face(const R* q, int s, R cw) {
+  const R* p = upwind_before(cw) ? q - s : q;
   const R qu = p[0];
   R bl = ppm_edge(p[-2 * s], p[-s], p[0], p[s]) - qu;
   R br = ppm_edge(p[-s], p[0], p[s], p[2 * s]) - qu;
   ppm_limit(bl, br);
-  const R ac = fabs(c);
-  const R x = (c > R(0)) ? br : bl;
-  return qu + (R(1) - ac) * (x - ac * (bl + br));
+  return swept_mean(qu, bl, br, cw);
 }
 
 // FP64 specialisations (order-preserving integer keys, fv3_math.cuh)
@@ -97,28 +149,12 @@ __device__ __forceinline__ double ppm_edge<double>(double qm, double q0, double 
 }
 
 template <>
-__device__ __forceinline__ double ppm_face<double>(const double* q, int s, double c) {
-  const long long cb = __double_as_longlong(c);
-  const bool pos = cb > 0;  // c > 0 (and not -0)
-  const double* p = pos ? q - s : q;
-  const double qu = p[0];
-  double bl = ppm_edge<double>(p[-2 * s], p[-s], p[0], p[s]) - qu;
-  double br = ppm_edge<double>(p[-s], p[0], p[s], p[2 * s]) - qu;
-  const long long sb = __double_as_longlong(bl), sr = __double_as_longlong(br);
-  const long long MAG = 0x7fffffffffffffffLL;
-  const long long mb = sb & MAG, mr = sr & MAG;
-  if ((sb ^ sr) >= 0 || mb == 0 || mr == 0) {  // bl * br >= 0: local extremum
-    bl = 0.0;
-    br = 0.0;
-  } else if (mb > twice_mag(mr)) {  // |bl| > 2|br|: bl = -2 br
-    bl = __longlong_as_double(twice_mag(mr) | (~sr & ~MAG));
-  } else if (mr > twice_mag(mb)) {  // |br| > 2|bl|: br = -2 bl
-    br = __longlong_as_double(twice_mag(mb) | (~sb & ~MAG));
-  }
-  const double ac = __longlong_as_double(cb & MAG);
-  const double x = pos ? br : bl;
-  return qu + (1.0 - ac) * (x - ac * (bl + br));
+__device__ __forceinline__ double upwind_weight<double>(double c) {
+  const long long b = __double_as_longlong(c);
+  const double w = 1.0 - __longlong_as_double(b & 0x7fffffffffffffffLL);
+  return __longlong_as_double(__double_as_longlong(w) ^ (b > 0 ? 0LL : (long long)0x8000000000000000ULL));
 }
+
 
 // ------------------------------------------------------------------------
 // per-tile metric view: element (i, j) at p[j * pitch + i]
@@ -376,36 +412,17 @@ __device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, c
   }
 }
 
-template <typename R>
-__device__ __forceinline__ bool positive(R c) { return c > R(0); }
-template <>
-__device__ __forceinline__ bool positive<double>(double c) { return __double_as_longlong(c) > 0; }
-// |c| < 1 (false for NaN; FP64 on the integer pipe)
-template <typename R>
-__device__ __forceinline__ bool below_one(R c) { return fabs(c) < R(1); }
-template <>
-__device__ __forceinline__ bool below_one<double>(double c) {
-  return (__double_as_longlong(c) & 0x7fffffffffffffffLL) < 0x3ff0000000000000LL;
-}
-template <typename R>
-__device__ __forceinline__ R magnitude(R c) { return fabs(c); }
-template <>
-__device__ __forceinline__ double magnitude<double>(double c) {
-  return __longlong_as_double(__double_as_longlong(c) & 0x7fffffffffffffffLL);
-}
 
 // face value at face l from precomputed edge values AL (AL[l] is the edge
-// between cells l - s and l): limited parabola of the upwind cell, swept mean
+// between cells l - s and l) for the upwind weight cw of the face: limited
+// parabola of the upwind cell, swept mean
 template <typename R>
-__device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, R c) {
-  const bool pos = positive(c);
-  const int p = pos ? l - s : l;
+__device__ __forceinline__ R ppm_face_al(const R* Q, const R* AL, int l, int s, R cw) {
+  const int p = upwind_before(cw) ? l - s : l;
   const R qu = Q[p];
   R bl = AL[p] - qu, br = AL[p + s] - qu;
   ppm_limit(bl, br);
-  const R ac = magnitude(c);
-  const R x = pos ? br : bl;
-  return qu + (R(1) - ac) * (x - ac * (bl + br));
+  return swept_mean(qu, bl, br, cw);
 }
 
 // a lies in [min(qa, qb), max(qa, qb)] and is not negative (FP64: on the
@@ -827,30 +844,52 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
   __syncthreads();
 }
 
-// Courant numbers and area fluxes (reading R11) into shared memory, plus the
-// reciprocal denominators of the two inner updates.  uc/vc: global, origin of
-// the level.
+// Courant numbers and area fluxes (reading R11) into shared memory (the
+// Courant numbers as upwind weights), plus the reciprocal denominators of the
+// two inner updates.  uc/vc: global, origin of the level.  guard: returns
+// whether a face of the block's own (|c| < 1 checked on the west and south
+// faces of its cells) breaks the Courant condition.  acx, afx, acy, afy
+// (level origins, or null): the remapping step's sums of the Courant numbers
+// and area fluxes, added for the faces the block writes (its cells' west and
+// south faces, and the tile's east and north edge faces).
 template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
-__device__ void courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R, MR>& S, const Blk& B,
-                        const TM<MR>& m, const Geo& g, R dt) {
-  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
+__device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R, MR>& S, const Blk& B,
+                        const TM<MR>& m, const Geo& g, R dt, bool guard, R* acx, R* afx, R* acy, R* afy) {
+  const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   const int P = g.pitch;
+  const bool xe = x1 == g.n, ye = y1 == g.n;
+  bool bad = false;
   int rot = 0;
   for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     // dt ut dy sin and dt ut sin / dxc with ut = (uc - cos v) / sin^2
     const auto du = dt * (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]);
-    S.XFX[l] = du * MT(kfx, j, i);
-    S.CRX[l] = du * MT(kcx, j, i);
+    const R fx = du * MT(kfx, j, i), c = du * MT(kcx, j, i);
+    S.XFX[l] = fx;
+    S.CRX[l] = upwind_weight(c);
+    const bool row = j >= y0 && j < y1;
+    if (guard && row && i < x1) bad |= !below_one(c);
+    if (acx && row && (i < x1 || xe)) {
+      atomicAdd(acx + (long long)j * P + i, c);
+      atomicAdd(afx + (long long)j * P + i, fx);
+    }
   });
   for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const auto dv = dt * (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]);
-    S.YFX[l] = dv * MT(kfy, j, i);
-    S.CRY[l] = dv * MT(kcy, j, i);
+    const R fy = dv * MT(kfy, j, i), c = dv * MT(kcy, j, i);
+    S.YFX[l] = fy;
+    S.CRY[l] = upwind_weight(c);
+    const bool col = i >= x0 && i < x1;
+    if (guard && col && j < y1) bad |= !below_one(c);
+    if (acy && col && (j < y1 || ye)) {
+      atomicAdd(acy + (long long)j * P + i, c);
+      atomicAdd(afy + (long long)j * P + i, fy);
+    }
   });
   __syncthreads();
   inner_denominators(S, B);
+  return bad;
 }
 
 // ------------------------------------------------------------------------
@@ -906,14 +945,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
     for2<FULL>(rot, x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     __syncthreads();
-    courant<BX, BY, FULL>(uc, vc, V, U, S, B, m, g, dt);
-    if (a.status) {  // Courant-number guard on the block's own faces
-      bool bad = false;
-      for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
-        const int l = B.L(i, j);
-        bad |= !below_one(S.CRX[l]) || !below_one(S.CRY[l]);
-      });
-      if (bad) atomicOr(a.status, ST_CFL);
+    {
+      R* const acx = a.amfx ? a.acrx + o : nullptr;
+      const bool bad = courant<BX, BY, FULL>(uc, vc, V, U, S, B, m, g, dt, a.status != nullptr, acx,
+                                             a.amfx ? a.axfx + o : nullptr, a.amfx ? a.acry + o : nullptr,
+                                             a.amfx ? a.ayfx + o : nullptr);
+      if (bad) atomicOr(a.status, ST_CFL);  // Courant-number guard on the block's own faces
     }
     // mass
     transport<R, LEARN, BX, BY, FULL, DAMP_YES>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
@@ -971,13 +1008,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       // the upwind edge length's reciprocal: one load of the chosen face
       const R cu = dt * ua * MT(rdx, j, positive(ua) ? i - 1 : i);
       const R cv = dt * va * MT(rdy, positive(va) ? j - 1 : j, i);
+      const R wu = upwind_weight(cu), wv = upwind_weight(cv);
       R ub, vb;
       if constexpr (kStoreRD<R>) {
-        ub = ppm_face_al(U, S.AL, l, 1, cu);
-        vb = ppm_face_al(V, S.QIJ, l, SX, cv);
+        ub = ppm_face_al(U, S.AL, l, 1, wu);
+        vb = ppm_face_al(V, S.QIJ, l, SX, wv);
       } else {
-        ub = ppm_face(U + l, 1, cu);
-        vb = ppm_face(V + l, SX, cv);
+        ub = ppm_face(U + l, 1, wu);
+        vb = ppm_face(V + l, SX, wv);
       }
       KE[l] = R(0.5) * dt * (ub * ua + vb * va);
     });
@@ -996,23 +1034,16 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
     }
     if (a.amfx) {
-      // the remapping step's sums: each face has one writer per launch, so
-      // an addition performed at the memory side (a reduction whose result
-      // is not read back) gives the sum a load-add-store gives, without the
-      // load's round trip
+      // the remapping step's sums (the Courant numbers and area fluxes were
+      // added where they were formed): each face has one writer per launch,
+      // so an addition performed at the memory side (a reduction whose
+      // result is not read back) gives the sum a load-add-store gives,
+      // without the load's round trip
       for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
-        const int l = B.L(i, j);
-        const long long q = o + G(j, i);
-        atomicAdd(a.amfx + q, MFX[l]);
-        atomicAdd(a.acrx + q, S.CRX[l]);
-        atomicAdd(a.axfx + q, S.XFX[l]);
+        atomicAdd(a.amfx + o + G(j, i), MFX[B.L(i, j)]);
       });
       for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
-        const int l = B.L(i, j);
-        const long long q = o + G(j, i);
-        atomicAdd(a.amfy + q, MFY[l]);
-        atomicAdd(a.acry + q, S.CRY[l]);
-        atomicAdd(a.ayfx + q, S.YFX[l]);
+        atomicAdd(a.amfy + o + G(j, i), MFY[B.L(i, j)]);
       });
     }
     __syncthreads();
@@ -1667,14 +1698,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
       for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
-        S.CRX[l] = one ? a.acrx[q] : a.acrx[q] * fr;
+        S.CRX[l] = upwind_weight(one ? a.acrx[q] : a.acrx[q] * fr);
         S.XFX[l] = one ? a.axfx[q] : a.axfx[q] * fr;
         MFX[l] = one ? a.amfx[q] : a.amfx[q] * fr;
       });
       for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
         const int l = B.L(i, j);
         const long long q = o + G(j, i);
-        S.CRY[l] = one ? a.acry[q] : a.acry[q] * fr;
+        S.CRY[l] = upwind_weight(one ? a.acry[q] : a.acry[q] * fr);
         S.YFX[l] = one ? a.ayfx[q] : a.ayfx[q] * fr;
         MFY[l] = one ? a.amfy[q] : a.amfy[q] * fr;
       });
@@ -1781,14 +1812,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
     for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
-      S.CRX[l] = a.crx[q];
+      S.CRX[l] = upwind_weight(a.crx[q]);
       S.XFX[l] = a.xfx[q];
       if (mass) MFX[l] = a.mfx[q];
     });
     for2(x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = o + G(j, i);
-      S.CRY[l] = a.cry[q];
+      S.CRY[l] = upwind_weight(a.cry[q]);
       S.YFX[l] = a.yfx[q];
       if (mass) MFY[l] = a.mfy[q];
     });
@@ -2489,7 +2520,7 @@ __global__ void __launch_bounds__(256) k_face_stencils(const double* q6, const d
       double al[5];
 #pragma unroll
       for (int l = 2; l <= 4; ++l) al[l] = ppm_edge<double>(q[l - 2], q[l - 1], q[l], q[l + 1]);
-      plain[f] = ppm_face_al<double>(q, al, 3, 1, cr[f]);
+      plain[f] = ppm_face_al<double>(q, al, 3, 1, upwind_weight(cr[f]));
     }
     if (edge) edge[f] = ppm_edge<double>(q[1], q[2], q[3], q[4]);
     if (x || sig) {
@@ -2523,7 +2554,7 @@ __global__ void __launch_bounds__(256) k_learned_stencils(const float* w, const 
       const int j = e / 6, k = e % 6;
       Q[B.L(k - 3, j)] = q6[6 * (long long)(f0 + j) + k];
     }
-    for (int j = tid; j < rows; j += 256) CC[B.L(0, j)] = cr[f0 + j];
+    for (int j = tid; j < rows; j += 256) CC[B.L(0, j)] = upwind_weight(cr[f0 + j]);
     __syncthreads();
     for (int e = tid; e < rows * 3; e += 256) {
       const int j = e / 3, i = e % 3 - 1;  // edges i = -1, 0, 1
