@@ -111,6 +111,13 @@ __device__ __forceinline__ bool upwind_before(R cw) {
   else return __float_as_int(cw) >= 0;
 }
 
+// a b + c with one rounding
+template <typename R>
+__device__ __forceinline__ R fmadd(R a, R b, R c) {
+  if constexpr (sizeof(R) == 8) return fma(a, b, c);
+  else return fmaf(a, b, c);
+}
+
 // the mean over the swept part of the upwind cell's limited parabola (mean
 // qu, deviations bl and br at its two edges): qu + w (w (bl + br) - y), y the
 // deviation at the cell's far edge from the face (bl when the cell before the
@@ -120,8 +127,7 @@ template <typename R>
 __device__ __forceinline__ R swept_mean(R qu, R bl, R br, R cw) {
   const R w = magnitude(cw);
   const R y = upwind_before(cw) ? bl : br;
-  if constexpr (sizeof(R) == 8) return fma(w, fma(w, bl + br, -y), qu);
-  else return fmaf(w, fmaf(w, bl + br, -y), qu);
+  return fmadd(w, fmadd(w, bl + br, -y), qu);
 }
 
 // face value at the face left of q[0] (between q[-s] and q[0]) for the
@@ -396,9 +402,13 @@ __device__ __forceinline__ void assign_extra(TS<R, MR>& S, R* base, int SA, bool
 }
 
 // the metric terms of the block's tile into shared memory: area and 1/area
-// over the tile, wx and wy over the faces the damping reads
+// over the tile, wx and wy over the faces the damping reads, times wscale
+// (the square root of the damping coefficient: the gradients and the
+// damping flux each take one factor, so the flux carries the coefficient
+// without a multiply of its own)
 template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
-__device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights) {
+__device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights,
+                                             MR wscale = MR(1)) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   int rot = 0;
   for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
@@ -407,8 +417,8 @@ __device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, c
     S.RAREA[l] = MT(rarea, j, i);
   });
   if (weights) {
-    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = MT(wx, j, i); });
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = MT(wy, j, i); });
+    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = wscale * MT(wx, j, i); });
+    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = wscale * MT(wy, j, i); });
   }
 }
 
@@ -479,10 +489,27 @@ __device__ void learned_faces(const R* Q, const R* AL, const R* CC, R* OUT, int 
   }
 }
 
+// The flux through a face from its outer face value f and the inner
+// sweep's face value fi: the mean of the two times the mass or area flux mf,
+// plus, if damped, the del-4 flux (lap - lapm) w, w the staged weight that
+// carries the square root of the coefficient (the Laplacians carry the
+// other), weighted by the mean of wdp over the face's two cells (at l - s
+// and l) if WDP.  As 0.5 (f + fi) mf + (lap - lapm) w [(wdp_l-s + wdp_l) / 2],
+// with the halving moved to where it costs no multiply of its own.
+template <bool WDP, typename R, typename MR>
+__device__ __forceinline__ R face_flux(R f, R fi, R mf, bool dmp, R lap, R lapm, MR w, const R* wdp, int l, int s) {
+  const R g = (f + fi) * mf;  // twice the advective flux
+  if (!dmp) return R(0.5) * g;
+  const R dl = (lap - lapm) * w;
+  if constexpr (WDP) return R(0.5) * fmadd(dl, wdp[l - s] + wdp[l], g);
+  else return fmadd(R(0.5), g, dl);
+}
+
 // fv_tp_2d (reading R5) + optional delnflux (R6) of the shared-memory scalar
 // Q on the block: fluxes on x-faces [x0, x1] x [y0, y1) -> FXO and y-faces
 // [x0, x1) x [y0, y1] -> FYO.  mfx/mfy: mass fluxes (null: area fluxes).
-// damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp.
+// damp > 0 adds the del-4 flux, weighted by 1/2 (wdp_{i-1} + wdp_i) if wdp;
+// the staged weights WX, WY carry the square root of damp (stage_metric).
 // Every PPM sweep first computes each edge value once (AL), then the face
 // values; the Laplacian of the damping is the divergence of face gradients.
 // The same transport for the FP32 path in four phases: on the FP32 pipe an
@@ -561,25 +588,13 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // the del-4 damping flux
   for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R f = ppm_face(S.QIJ + l, 1, S.CRX[l]);
-    R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
-    if (dmp) {
-      R d = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
-      if constexpr (WDP) d = d * (R(0.5) * (wdp[l - 1] + wdp[l]));
-      fl = fl + d;
-    }
-    FXO[l] = fl;
+    FXO[l] = face_flux<WDP>(ppm_face(S.QIJ + l, 1, S.CRX[l]), S.FX2[l], mfx ? mfx[l] : S.XFX[l], dmp, S.LAP[l],
+                            S.LAP[l - 1], S.WX[l], wdp, l, 1);
   });
   for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R f = ppm_face(QJ + l, SX, S.CRY[l]);
-    R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
-    if (dmp) {
-      R d = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
-      if constexpr (WDP) d = d * (R(0.5) * (wdp[l - SX] + wdp[l]));
-      fl = fl + d;
-    }
-    FYO[l] = fl;
+    FYO[l] = face_flux<WDP>(ppm_face(QJ + l, SX, S.CRY[l]), S.FY2[l], mfy ? mfy[l] : S.YFX[l], dmp, S.LAP[l],
+                            S.LAP[l - SX], S.WY[l], wdp, l, SX);
   });
   __syncthreads();
 }
@@ -609,17 +624,15 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   // the damped transports (d_sw, fv_tp_2d) have the weights wx, wy staged
   MlpFrag F;
   if (LEARN) mlp_load(mlp, F);
-  // del-4 damping fluxes at x-face / y-face l, added where the fluxes are
-  // formed (the Laplacian is complete by then)
-  auto damp_x = [&](int l) -> R {
-    R f = damp * (S.LAP[l] - S.LAP[l - 1]) * S.WX[l];
-    if constexpr (WDP) f = f * (R(0.5) * (wdp[l - 1] + wdp[l]));
-    return f;
+  // the fluxes of x-face / y-face l from its outer face value, with the
+  // del-4 damping added where they are formed (the Laplacian is complete by
+  // then)
+  auto flux_x = [&](int l, R f) -> R {
+    return face_flux<WDP>(f, S.FX2[l], mfx ? mfx[l] : S.XFX[l], dmp, S.LAP[l], S.LAP[l - 1], S.WX[l], wdp, l, 1);
   };
-  auto damp_y = [&](int l) -> R {
-    R f = damp * (S.LAP[l] - S.LAP[l - SX]) * S.WY[l];
-    if constexpr (WDP) f = f * (R(0.5) * (wdp[l - SX] + wdp[l]));
-    return f;
+  auto flux_y = [&](int l, R f) -> R {
+    return face_flux<WDP>(f, S.FY2[l], mfy ? mfy[l] : S.YFX[l], dmp, S.LAP[l], S.LAP[l - SX], S.WY[l], wdp, l,
+                          SX);
   };
   __syncthreads();  // Q (and the strips the corner turn reads) complete
   if (cc) {  // blocks at a cube corner: the missing quadrant for the y-sweep
@@ -691,15 +704,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
     for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R fl = R(0.5) * (FXO[l] + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
-      FXO[l] = dmp ? fl + damp_x(l) : fl;
+      FXO[l] = flux_x(l, FXO[l]);
     });
   } else {
     for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R f = ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]);
-      const R fl = R(0.5) * (f + S.FX2[l]) * (mfx ? mfx[l] : S.XFX[l]);
-      FXO[l] = dmp ? fl + damp_x(l) : fl;
+      FXO[l] = flux_x(l, ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]));
     });
   }
   __syncthreads();
@@ -720,15 +730,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
     for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R fl = R(0.5) * (FYO[l] + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
-      FYO[l] = dmp ? fl + damp_y(l) : fl;
+      FYO[l] = flux_y(l, FYO[l]);
     });
   } else {
     for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R f = ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]);
-      const R fl = R(0.5) * (f + S.FY2[l]) * (mfy ? mfy[l] : S.YFX[l]);
-      FYO[l] = dmp ? fl + damp_y(l) : fl;
+      FYO[l] = flux_y(l, ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]));
     });
   }
   __syncthreads();
@@ -928,7 +935,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
   const R damp = (R)(dd * dd);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
-  stage_metric<BX, BY, FULL>(S, B, m, true);  // read after the first barrier of the level loop
+  // read after the first barrier of the level loop; the damping weights
+  // carry d4_bg da_min, the square root of the coefficient
+  stage_metric<BX, BY, FULL>(S, B, m, true, (MR)dd);
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
@@ -1806,7 +1815,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_fv_tp_2d(TpArgs
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
-  stage_metric(S, B, m, damp != R(0));  // read after the first barrier of the level loop
+  // read after the first barrier of the level loop; the damping weights
+  // carry the square root of the coefficient
+  stage_metric(S, B, m, damp != R(0), (MR)sqrt(a.damp));
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     for2(x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
