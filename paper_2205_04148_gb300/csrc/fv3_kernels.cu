@@ -814,11 +814,11 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
   __syncthreads();
   for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R w = mfx[l];
+    const R hw = R(0.5) * mfx[l];  // half the mass flux, shared by the two fields
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       const R v = ppm_face_al(F[f].QIJ, F[f].AL, l, 1, S.CRX[l]);
-      F[f].FXO[l] = R(0.5) * (v + F[f].FX2[l]) * w;
+      F[f].FXO[l] = (v + F[f].FX2[l]) * hw;
     }
   });
   __syncthreads();
@@ -841,11 +841,11 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
   __syncthreads();
   for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
-    const R w = mfy[l];
+    const R hw = R(0.5) * mfy[l];  // half the mass flux, shared by the two fields
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       const R v = ppm_face_al(F[f].QIJ, F[f].AL, l, SX, S.CRY[l]);
-      F[f].FYO[l] = R(0.5) * (v + F[f].FY2[l]) * w;
+      F[f].FYO[l] = (v + F[f].FY2[l]) * hw;
     }
   });
   __syncthreads();
@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
   Blk B{it.x0, FULL ? it.x0 + BX : min(it.x0 + BX, n), it.y0, FULL ? it.y0 + BY : min(it.y0 + BY, n), SX};
   const bool cc = g.cubed && (B.x0 == 0 || B.x1 == n) && (B.y0 == 0 || B.y1 == n);
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
-  const R dt = (R)a.P.dt;
+  const R dt = (R)a.P.dt, hdt = R(0.5) * dt, qdt = R(0.25) * dt;
   const double dd = a.P.d4_bg * g.da_min;
   const R damp = (R)(dd * dd);
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
@@ -1012,11 +1012,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     }
     for2<FULL>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R ua = R(0.5) * (uc[G(j - 1, i)] + uc[G(j, i)]);
-      const R va = R(0.5) * (vc[G(j, i - 1)] + vc[G(j, i)]);
+      // twice the corner winds (their halvings moved into hdt and qdt)
+      const R ua2 = uc[G(j - 1, i)] + uc[G(j, i)];
+      const R va2 = vc[G(j, i - 1)] + vc[G(j, i)];
       // the upwind edge length's reciprocal: one load of the chosen face
-      const R cu = dt * ua * MT(rdx, j, positive(ua) ? i - 1 : i);
-      const R cv = dt * va * MT(rdy, positive(va) ? j - 1 : j, i);
+      const R cu = hdt * ua2 * MT(rdx, j, positive(ua2) ? i - 1 : i);
+      const R cv = hdt * va2 * MT(rdy, positive(va2) ? j - 1 : j, i);
       const R wu = upwind_weight(cu), wv = upwind_weight(cv);
       R ub, vb;
       if constexpr (kStoreRD<R>) {
@@ -1026,7 +1027,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
         ub = ppm_face(U + l, 1, wu);
         vb = ppm_face(V + l, SX, wv);
       }
-      KE[l] = R(0.5) * dt * (ub * ua + vb * va);
+      KE[l] = qdt * (ub * ua2 + vb * va2);
     });
     __syncthreads();
     R *uo = a.u_o + o, *vo = a.v_o + o;
