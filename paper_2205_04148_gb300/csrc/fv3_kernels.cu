@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
   Blk B{it.x0, FULL ? it.x0 + BX : min(it.x0 + BX, n), it.y0, FULL ? it.y0 + BY : min(it.y0 + BY, n), SX};
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   const TM<MR> m = tile_metric(metric_sel<MR>(a), g, it.t);
-  const R dt2 = R(0.5 * a.P.dt);
+  const R dt2 = R(0.5 * a.P.dt), dt2e = R(0.125) * dt2;
   const int k0 = (wi % kz) * kchunk, k1 = min(k0 + kchunk, g.nz);
   auto G = [&](int j, int i) { return (long long)j * P + i; };
   for (int k = k0; k < k1; ++k) {
@@ -1147,9 +1147,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 4) k_c_sw(StepArgs<R
     });
     for2<FULL>(x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
-      const R ua = R(0.5) * (UT[l] + UT[l + 1]);
-      const R va = R(0.5) * (VT[l] + VT[l + SX]);
-      KE[l] = R(0.5) * dt2 * (ua * ua + va * va);
+      // twice the cell-centre winds; their halvings squared fold into dt2 / 8
+      const R ua2 = UT[l] + UT[l + 1];
+      const R va2 = VT[l] + VT[l + SX];
+      KE[l] = dt2e * (ua2 * ua2 + va2 * va2);
     });
     for2<FULL>(x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
