@@ -74,6 +74,12 @@ template <>
 __device__ __forceinline__ bool below_one<double>(double c) {
   return (__double_as_longlong(c) & 0x7fffffffffffffffLL) < 0x3ff0000000000000LL;
 }
+// the smaller of a and b, as fmin for numbers (FP64: compared on the
+// integer pipe, on the order-preserving keys of the bit patterns)
+template <typename R>
+__device__ __forceinline__ R min_of(R a, R b) { return fmin(a, b); }
+template <>
+__device__ __forceinline__ double min_of<double>(double a, double b) { return okey(a) < okey(b) ? a : b; }
 template <typename R>
 __device__ __forceinline__ R magnitude(R c) { return fabs(c); }
 template <>
@@ -1292,7 +1298,7 @@ __global__ void __launch_bounds__(kDzBX * kDzBY) k_update_dz_c(StepArgs<R> a) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) Gf[f] = S[f] * (positive(S[f]) ? GZ[lo[f]] : GZ[hi[f]]);
       const R gzn = (GZ[l] * ar2 + Gf[0] - Gf[1] + Gf[2] - Gf[3]) * rcp(ar2 + S[0] - S[1] + S[2] - S[3]);
-      a.delzc[o + q] = fmin((gzn_below - gzn) * rgrav, -dzmin);
+      a.delzc[o + q] = min_of((gzn_below - gzn) * rgrav, -dzmin);
       gzn_below = gzn;
     }
     xb = xa; xa = xn; yb = ya; ya = yn;
@@ -1729,8 +1735,11 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
       const int l = B.L(i, j);
       const R d0 = a.dp0[o + G(j, i)];
       const R d1 = d0 + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
-      D0[l] = d0;
-      D1[l] = rcp(d1);  // reciprocal, shared by every tracer
+      // the factors every tracer's update takes: q_new = q dp0 / dp1 + (flux
+      // divergence) / (area dp1)
+      const R r = rcp(d1);
+      D0[l] = d0 * r;
+      D1[l] = S.RAREA[l] * r;
       a.dp1[o + G(j, i)] = d1;
     });
     // each tracer's tile (block + halo 3) is fetched into registers while the
@@ -1758,8 +1767,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
           const TF<R>& T = TFP[f];
           for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
             const int l = B.L(i, j);
-            qo[G(j, i)] =
-                (T.Q[l] * D0[l] + (T.FXO[l] - T.FXO[l + 1] + T.FYO[l] - T.FYO[l + SX]) * S.RAREA[l]) * D1[l];
+            qo[G(j, i)] = T.Q[l] * D0[l] + (T.FXO[l] - T.FXO[l + 1] + T.FYO[l] - T.FYO[l + SX]) * D1[l];
           });
         }
       }
@@ -1779,7 +1787,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : 4)
       R* qo = a.q_o[tq] + o;
       for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
-        qo[G(j, i)] = (Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * D1[l];
+        qo[G(j, i)] = Q[l] * D0[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * D1[l];
       });
     }
     }
