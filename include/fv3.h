@@ -278,7 +278,8 @@ fv3_status fv3_vertical_remap(fv3_ctx* ctx, const fv3_state* state, const fv3_pa
  * and mfy: both NULL (area fluxes) or both set.  The halo rings of q, crx/cry,
  * xfx/yfx and mfx/mfy are filled by this call (C-grid vector rule for the
  * face pairs), so they are written as well as read; fx and fy receive the
- * interior faces.  |crx|, |cry| must be below 1 (not checked here).
+ * interior faces.  |crx|, |cry| must not exceed 1 (not checked here; at 1 a
+ * face passes its upwind cell's mean exactly).
  * Errors: FV3_ERR_ARG (NULL pointer, mfx without mfy, damp < 0 or not
  * finite), FV3_ERR_ALIGN (a pointer not 128-byte aligned). */
 fv3_status fv3_fv_tp_2d(fv3_ctx* ctx, void* q, void* crx, void* cry, void* xfx, void* yfx, void* mfx, void* mfy,
