@@ -658,8 +658,12 @@ def batched_measure(a, ws, rank, steps, local=0):
     torch.cuda.empty_cache()
     hbm, hbm_src = hbm_peak()
     ach = DSW_WORDS_PER_CELL * 4 * cells / t_dsw / 1e9
-    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3, "peak_source": hbm_src}
+    # the capture is of one C192 sphere in the ensemble's launch configuration;
+    # every member's tiles are whole blocks, so the bytes per cell carry over
+    traffic, traffic_rec = dram_traffic("k_d_sw", "f32", bx, by, kc, pers, cells)
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "traffic_capture": traffic_rec, "kernel": "k_d_sw<float>", "ms_per_launch": t_dsw * 1e3,
+            "peak_source": hbm_src}
 
     # the same members one at a time: plain FP64 path and FP32 path
     per_member = {}
