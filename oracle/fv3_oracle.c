@@ -28,11 +28,16 @@
  * amplification), the column solve (Thomas vs dense LU brute force, resting
  * hydrostatic column, linearity), the grid (total area, symmetries, grid
  * angle), the halo fill (brute-force geometric matching of cells and rotated
- * winds), and the whole substep (mass conservation to 1e-14, constant tracer,
- * rest state, uniform translation, transpose symmetry).
- * Parity unpinned: agreement of c_sw, update_dz_c, p_grad_c and the wind
- * update of d_sw with FORTRAN FV3 -- the paper gives neither their equations
- * nor any field value, so only the invariants above hold them.
+ * winds), the whole substep (mass conservation to 1e-14, constant tracer,
+ * rest state, uniform translation, transpose symmetry), the wind updates of
+ * c_sw and d_sw (the vector-invariant balance of a steady shear flow, the
+ * cross-stream wind converging to zero at second order), p_grad_c (the
+ * closed-form acceleration of isothermal air under a surface-pressure bump),
+ * update_dz_c (the first-order upwind scheme it reduces to under
+ * layer-uniform winds) and the tracer sub-cycling (its passes repeated by
+ * hand through the single-plane transport).
+ * What no test can pin: agreement with FORTRAN FV3 itself -- the paper gives
+ * neither the equations nor any field value of it.
  *
  * Layout: every field is padded by a halo of h = 3 on each side of a tile,
  * i fastest.  Index (i, j) of the interior runs over [0, n).  Faces: x-face
