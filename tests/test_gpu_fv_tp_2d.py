@@ -93,20 +93,21 @@ def test_fv_tp_2d_mass_flux_form():
     assert np.array_equal(fx2, 2.0 * fx) and np.array_equal(fy2, 2.0 * fy)
 
 
-def test_fv_tp_2d_courant_one_translation():
-    """crx = 1 on the uniform periodic tile: one flux-form update is the shift
-    by one cell to round-off"""
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_fv_tp_2d_courant_one_translation(sign):
+    """crx = +1 / -1 on the uniform periodic tile: one flux-form update is the
+    shift by one cell (east / west) to round-off"""
     from paper_2205_04148_gb300 import fv3
     n, nz = 24, 2
     g = fv3.Grid(fv3.GRID_PERIODIC, n, nz)
     area = 1.0e10
     rng = np.random.default_rng(17)
     q = 1000.0 + 50.0 * rng.standard_normal((1, nz, n, n))
-    crx = np.ones((1, nz, n, n + 1))
+    crx = sign * np.ones((1, nz, n, n + 1))
     cry = np.zeros((1, nz, n + 1, n))
     fx, fy = gpu_fluxes(g, q, crx, cry, crx * area, cry * area)
     qn = q + (fx[..., :-1] - fx[..., 1:] + fy[..., :-1, :] - fy[..., 1:, :]) / area
-    assert np.abs(qn - np.roll(q, 1, axis=-1)).max() <= 4 * np.finfo(float).eps * np.abs(q).max()
+    assert np.abs(qn - np.roll(q, int(sign), axis=-1)).max() <= 4 * np.finfo(float).eps * np.abs(q).max()
 
 
 def test_fv_tp_2d_invalid_arguments():

@@ -22,6 +22,7 @@ def stencils(seed, n):
     c = rng.uniform(-0.95, 0.95, n)
     c[:20] = 0.0
     c[20:30] = 1.0
+    c[30:40] = -1.0
     return st, c
 
 
@@ -42,8 +43,10 @@ def test_plain_faces_and_edges_match_oracle(orc):
     e = out["edge"].cpu().numpy()
     ew = np.array([orc.ppm_edge(s[1:5]) for s in st])
     assert (np.abs(e - ew) <= 4e-16 * scale).all()
-    # Courant number 1 gives the upwind cell exactly
+    # Courant number +1 / -1 gives the upwind cell exactly (the cell before /
+    # after the face)
     assert np.array_equal(got[20:30], st[20:30, 2])
+    assert np.array_equal(got[30:40], st[30:40, 3])
 
 
 def test_network_inputs_within_float_error_of_fp64(orc):
