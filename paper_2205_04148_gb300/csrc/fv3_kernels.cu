@@ -229,15 +229,18 @@ struct Blk {
 // warps after the ones that took the previous loop's last pass, and the
 // loops of one barrier interval share out their passes as one flat loop
 // would (without it the low warps take the extra pass of every loop and the
-// barrier waits for them).  Blocks of 256 threads (8 warps).
-template <bool CW = false, typename F>
+// barrier waits for them).  Blocks of NT threads (a multiple of 32; 256 but
+// for the FP64 d_sw).
+template <bool CW = false, int NT = 256, typename F>
 __device__ __forceinline__ void for2(int& rot, int ilo, int ihi, int jlo, int jhi, F f) {
   const int w = ihi - ilo, h = jhi - jlo;
   if (w <= 0 || h <= 0) return;
   const int total = w * h;
-  constexpr int NT = 256;
   const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
-  const int e0 = (tid - 32 * rot) & (NT - 1);
+  constexpr bool POW2 = (NT & (NT - 1)) == 0;
+  int e0 = tid - 32 * rot;
+  if constexpr (POW2) e0 &= NT - 1;
+  else if (e0 < 0) e0 += NT;
   if constexpr (CW) {
     // extents known at compile time (full blocks): the first point by a
     // division by the constant width, then steps of 256 points as constant
@@ -261,14 +264,15 @@ __device__ __forceinline__ void for2(int& rot, int ilo, int ihi, int jlo, int jh
       f(ilo + (e - j * w), jlo + j);
     }
   }
-  rot = (rot + (total + 31) / 32) & (NT / 32 - 1);
+  if constexpr (POW2) rot = (rot + (total + 31) / 32) & (NT / 32 - 1);
+  else rot = (rot + (total + 31) / 32) % (NT / 32);
 }
 
 // a loop on its own (the warps' first pass from warp 0)
-template <bool CW = false, typename F>
+template <bool CW = false, int NT = 256, typename F>
 __device__ __forceinline__ void for2(int ilo, int ihi, int jlo, int jhi, F f) {
   int rot = 0;
-  for2<CW>(rot, ilo, ihi, jlo, jhi, f);
+  for2<CW, NT>(rot, ilo, ihi, jlo, jhi, f);
 }
 
 // The block's tile with its halo of 3 ([x0 - 3, x1 + 3) x [y0 - 3, y1 + 3)),
@@ -369,16 +373,16 @@ __device__ __forceinline__ MR inner_rdx(const TS<R, MR>& S, int l) {
 
 // the stored denominators (kStoreRD): y over [x0-3, x1+3) x [y0, y1), x over
 // [x0, x1) x [y0-3, y1+3); read after the next barrier
-template <typename R, typename MR>
+template <int NT = 256, typename R, typename MR>
 __device__ __forceinline__ void inner_denominators(const TS<R, MR>& S, const Blk& B) {
   if constexpr (kStoreRD<R>) {
     const int x0 = B.x0, x1 = B.x1, y0 = B.y0, y1 = B.y1, SX = B.SX;
     int rot = 0;
-    for2(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+    for2<false, NT>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.RDYd[l] = rcp(S.AREA[l] + S.YFX[l] - S.YFX[l + SX]);
     });
-    for2(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<false, NT>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       S.RDXd[l] = rcp(S.AREA[l] + S.XFX[l] - S.XFX[l + 1]);
     });
@@ -412,19 +416,19 @@ __device__ __forceinline__ void assign_extra(TS<R, MR>& S, R* base, int SA, bool
 // (the square root of the damping coefficient: the gradients and the
 // damping flux each take one factor, so the flux carries the coefficient
 // without a multiply of its own)
-template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
+template <int BX = 0, int BY = 0, bool FULL = false, int NT = 256, typename R, typename MR>
 __device__ __forceinline__ void stage_metric(const TS<R, MR>& S, const Blk& B, const TM<MR>& m, bool weights,
                                              MR wscale = MR(1)) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   int rot = 0;
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AREA[l] = MT(area, j, i);
     S.RAREA[l] = MT(rarea, j, i);
   });
   if (weights) {
-    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = wscale * MT(wx, j, i); });
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = wscale * MT(wy, j, i); });
+    for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) { S.WX[B.L(i, j)] = wscale * MT(wx, j, i); });
+    for2<FULL, NT>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) { S.WY[B.L(i, j)] = wscale * MT(wy, j, i); });
   }
 }
 
@@ -531,7 +535,7 @@ __device__ __forceinline__ R face_flux(R f, R fi, R mf, bool dmp, R lap, R lapm,
 //   4  outer x-faces of QIJ and outer y-faces of the x-updated field, fluxes
 // The damping gradients live in the output arrays until the Laplacian is
 // formed, as in transport().
-template <int BX, int BY, bool FULL, int DM, bool WDP, typename R, typename MR>
+template <int BX, int BY, bool FULL, int DM, bool WDP, int NT = 256, typename R, typename MR>
 __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, bool cc, const R* mfx, const R* mfy,
                                 R damp, const R* wdp, R* FXO, R* FYO) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
@@ -546,18 +550,18 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     __syncthreads();
   }
   // 1: y-faces of the plain field (y-role corners)
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FY2[l] = ppm_face(Q + l, SX, S.CRY[l]);
   });
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
   __syncthreads();
   // 2: inner y-update in every column of the block and its halo
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -567,12 +571,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
     __syncthreads();
   }
   // x-faces of the plain field (x-role corners)
-  for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.FX2[l] = ppm_face(Q + l, 1, S.CRX[l]);
   });
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -580,11 +584,11 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 3: Laplacian of the damping, inner x-update in every row of the block
   // and its halo
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
-  for2<FULL>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     QJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
@@ -592,12 +596,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
   // 4: outer x-faces of the y-updated field and outer y-faces of the
   // x-updated field; fluxes = mean face value x (mass or area) flux, plus
   // the del-4 damping flux
-  for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     FXO[l] = face_flux<WDP>(ppm_face(S.QIJ + l, 1, S.CRX[l]), S.FX2[l], mfx ? mfx[l] : S.XFX[l], dmp, S.LAP[l],
                             S.LAP[l - 1], S.WX[l], wdp, l, 1);
   });
-  for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     FYO[l] = face_flux<WDP>(ppm_face(QJ + l, SX, S.CRY[l]), S.FY2[l], mfy ? mfy[l] : S.YFX[l], dmp, S.LAP[l],
                             S.LAP[l - SX], S.WY[l], wdp, l, SX);
@@ -613,12 +617,12 @@ __device__ void transport_fused(R* Q, const TS<R, MR>& S, const Blk& B, int n, b
 // switched off at run time inside a loop may still be issued, with no lane
 // active, and FP64 instructions cost their pipe time either way).
 template <typename R, bool LEARN = false, int BX = 0, int BY = 0, bool FULL = false, int DM = DAMP_RT,
-          bool WDP = false, typename MR = R>
+          bool WDP = false, int NT = 256, typename MR = R>
 __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& m, int n, bool cc, const R* mfx,
                           const R* mfy, R damp, const R* wdp, R* FXO, R* FYO, const float* mlp = nullptr) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1, SX = B.SX;
   if constexpr (sizeof(R) == 4 && !LEARN) {
-    transport_fused<BX, BY, FULL, DM, WDP>(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
+    transport_fused<BX, BY, FULL, DM, WDP, NT>(Q, S, B, n, cc, mfx, mfy, damp, wdp, FXO, FYO);
     return;
   }
   const bool dmp = damped<DM>(damp);
@@ -646,12 +650,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // y-sweep of the plain field (y-role corners): edges, then faces
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2 * SX], Q[l - SX], Q[l], Q[l + SX]);
   });
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
       const int l = B.L(i, j);
       GY[l] = (Q[l] - Q[l - SX]) * S.WY[l];
     });
@@ -659,13 +663,13 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRY, S.FY2, x0 - 3, x1 + 3, y0, y1 + 1, SX, B, F);
   else
-    for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FY2[l] = ppm_face_al(Q, S.AL, l, SX, S.CRY[l]);
     });
   __syncthreads();
   // inner y-update in every column of the block and its halo
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FY2[l] * S.YFX[l] - S.FY2[l + SX] * S.YFX[l + SX]) * inner_rdy(S, l, SX);
   });
@@ -676,12 +680,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
     __syncthreads();
   }
   // x-sweep of the plain field (x-role corners)
-  for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(Q[l - 2], Q[l - 1], Q[l], Q[l + 1]);
   });
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       GX[l] = (Q[l] - Q[l - 1]) * S.WX[l];
     });
@@ -689,18 +693,18 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN)
     learned_faces(Q, S.AL, S.CRX, S.FX2, x0, x1 + 1, y0 - 3, y1 + 3, 1, B, F);
   else
-    for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       S.FX2[l] = ppm_face_al(Q, S.AL, l, 1, S.CRX[l]);
     });
   if (dmp)
-    for2<FULL>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 1, x1 + 1, y0 - 1, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       S.LAP[l] = (GX[l + 1] - GX[l] + GY[l + SX] - GY[l]) * S.RAREA[l];
     });
   __syncthreads();
   // outer x-sweep of the y-updated field
-  for2<FULL>(rot, x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0, y1, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2], S.QIJ[l - 1], S.QIJ[l], S.QIJ[l + 1]);
   });
@@ -708,25 +712,25 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRX, FXO, x0, x1 + 1, y0, y1, 1, B, F);
     __syncthreads();
-    for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       FXO[l] = flux_x(l, FXO[l]);
     });
   } else {
-    for2<FULL>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1 + 1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       FXO[l] = flux_x(l, ppm_face_al(S.QIJ, S.AL, l, 1, S.CRX[l]));
     });
   }
   __syncthreads();
   // inner x-update in every row of the block and its halo
-  for2<FULL>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     S.QIJ[l] = (Q[l] * S.AREA[l] + S.FX2[l] * S.XFX[l] - S.FX2[l + 1] * S.XFX[l + 1]) * inner_rdx(S, l);
   });
   __syncthreads();
   // outer y-sweep of the x-updated field
-  for2<FULL>(rot, x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1, y0 - 1, y1 + 2, [&](int i, int j) {
     const int l = B.L(i, j);
     S.AL[l] = ppm_edge(S.QIJ[l - 2 * SX], S.QIJ[l - SX], S.QIJ[l], S.QIJ[l + SX]);
   });
@@ -734,12 +738,12 @@ __device__ void transport(R* Q, const TS<R, MR>& S, const Blk& B, const TM<MR>& 
   if (LEARN) {
     learned_faces(S.QIJ, S.AL, S.CRY, FYO, x0, x1, y0, y1 + 1, SX, B, F);
     __syncthreads();
-    for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       FYO[l] = flux_y(l, FYO[l]);
     });
   } else {
-    for2<FULL>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       FYO[l] = flux_y(l, ppm_face_al(S.QIJ, S.AL, l, SX, S.CRY[l]));
     });
@@ -865,7 +869,7 @@ __device__ void transport_pair(const TF<R>* F, const TS<R, MR>& S, const Blk& B,
 // (level origins, or null): the remapping step's sums of the Courant numbers
 // and area fluxes, added for the faces the block writes (its cells' west and
 // south faces, and the tile's east and north edge faces).
-template <int BX = 0, int BY = 0, bool FULL = false, typename R, typename MR>
+template <int BX = 0, int BY = 0, bool FULL = false, int NT = 256, typename R, typename MR>
 __device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, const TS<R, MR>& S, const Blk& B,
                         const TM<MR>& m, const Geo& g, R dt, bool guard, R* acx, R* afx, R* acy, R* afy) {
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
@@ -873,7 +877,7 @@ __device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
   const bool xe = x1 == g.n, ye = y1 == g.n;
   bool bad = false;
   int rot = 0;
-  for2<FULL>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0, x1 + 1, y0 - 3, y1 + 3, [&](int i, int j) {
     const int l = B.L(i, j);
     // dt ut dy sin and dt ut sin / dxc with ut = (uc - cos v) / sin^2
     const auto du = dt * (uc[(long long)j * P + i] - MT(cosx, j, i) * Vs[l]);
@@ -887,7 +891,7 @@ __device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
       atomicAdd(afx + (long long)j * P + i, fx);
     }
   });
-  for2<FULL>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
+  for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0, y1 + 1, [&](int i, int j) {
     const int l = B.L(i, j);
     const auto dv = dt * (vc[(long long)j * P + i] - MT(cosy, j, i) * Us[l]);
     const R fy = dv * MT(kfy, j, i), c = dv * MT(kcy, j, i);
@@ -901,7 +905,7 @@ __device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
     }
   });
   __syncthreads();
-  inner_denominators(S, B);
+  inner_denominators<NT>(S, B);
   return bad;
 }
 
@@ -911,9 +915,16 @@ __device__ bool courant(const R* uc, const R* vc, const R* Vs, const R* Us, cons
 // FULL: every block of every member is a full BX x BY block (the tiles'
 // sizes are multiples of the block shape), so the extents of every 2-D loop
 // are compile-time constants
+// threads of a d_sw block: the plain FP64 kernel takes nine warps (two
+// blocks of 288 threads x 112 registers fill the register file, 18 warps per
+// SM to feed the FP64 pipe instead of 16), the others eight
+template <typename R, bool LEARN>
+constexpr int kDswThreads = (sizeof(R) == 8 && !LEARN) ? 288 : 256;
+
 template <typename R, int BX, int BY, bool LEARN, typename MR = R, bool FULL = false>
-__global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(MR) == 8 ? 3 : 4))
+__global__ void __launch_bounds__(kDswThreads<R, LEARN>, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(MR) == 8 ? 3 : 4))
     k_d_sw(StepArgs<R> a, int kchunk, int nwork) {
+  constexpr int NT = kDswThreads<R, LEARN>;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SX = BX + 7, SY = BY + 7, SA = SX * SY;
   R* sb = reinterpret_cast<R*>(smraw);
@@ -943,35 +954,35 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
   const int x0 = B.x0, x1 = FULL ? x0 + BX : B.x1, y0 = B.y0, y1 = FULL ? y0 + BY : B.y1;
   // read after the first barrier of the level loop; the damping weights
   // carry d4_bg da_min, the square root of the coefficient
-  stage_metric<BX, BY, FULL>(S, B, m, true, (MR)dd);
+  stage_metric<BX, BY, FULL, NT>(S, B, m, true, (MR)dd);
   for (int k = k0; k < k1; ++k) {
     const long long o = fld0(g, g.off3, g.nz, it.t, k);
     const R *u = a.u + o, *v = a.v + o, *w = a.w + o, *dp = a.delp + o, *pt = a.pt + o;
     const R *uc = a.uc + o, *vc = a.vc + o;
     int rot = 0;  // warp rotation of the loops of one barrier interval (for2)
     auto G = [&](int j, int i) { return (long long)j * P + i; };
-    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       const long long q = G(j, i);
       DP[l] = dp[q];
       PT[l] = pt[q];
       W[l] = w[q];
     });
-    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
-    for2<FULL>(rot, x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
+    for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 4, [&](int i, int j) { U[B.L(i, j)] = u[G(j, i)]; });
+    for2<FULL, NT>(rot, x0 - 3, x1 + 4, y0 - 3, y1 + 3, [&](int i, int j) { V[B.L(i, j)] = v[G(j, i)]; });
     __syncthreads();
     {
       R* const acx = a.amfx ? a.acrx + o : nullptr;
-      const bool bad = courant<BX, BY, FULL>(uc, vc, V, U, S, B, m, g, dt, a.status != nullptr, acx,
+      const bool bad = courant<BX, BY, FULL, NT>(uc, vc, V, U, S, B, m, g, dt, a.status != nullptr, acx,
                                              a.amfx ? a.axfx + o : nullptr, a.amfx ? a.acry + o : nullptr,
                                              a.amfx ? a.ayfx + o : nullptr);
       if (bad) atomicOr(a.status, ST_CFL);  // Courant-number guard on the block's own faces
     }
     // mass
-    transport<R, LEARN, BX, BY, FULL, DAMP_YES>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+    transport<R, LEARN, BX, BY, FULL, DAMP_YES, false, NT>(DP, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, MFX, MFY, a.mlp);
     R* dpo = a.delp_o + o;
-    for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1, y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       const R d = DP[l] + (MFX[l] - MFX[l + 1] + MFY[l] - MFY[l + SX]) * S.RAREA[l];
       DPN[l] = rcp(d);  // reciprocal, used by pt and w
@@ -982,10 +993,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       R* Q = fld == 0 ? PT : W;
       R* out = (fld == 0 ? a.pt_o : a.w_o) + o;
       if (LEARN && fld == 0)
-        transport<R, LEARN, BX, BY, FULL, DAMP_YES, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
+        transport<R, LEARN, BX, BY, FULL, DAMP_YES, true, NT>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO, a.mlp);
       else
-        transport<R, false, BX, BY, FULL, DAMP_YES, true>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
-      for2<FULL>(rot, x0, x1, y0, y1, [&](int i, int j) {
+        transport<R, false, BX, BY, FULL, DAMP_YES, true, NT>(Q, S, B, m, n, cc, MFX, MFY, damp, DP, FXO, FYO);
+      for2<FULL, NT>(rot, x0, x1, y0, y1, [&](int i, int j) {
         const int l = B.L(i, j);
         out[G(j, i)] =
             (Q[l] * DP[l] + (FXO[l] - FXO[l + 1] + FYO[l] - FYO[l + SX]) * S.RAREA[l]) * DPN[l];
@@ -993,12 +1004,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     }
     __syncthreads();
     // cell absolute vorticity (into PT)
-    for2<FULL>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0 - 3, x1 + 3, y0 - 3, y1 + 3, [&](int i, int j) {
       const int l = B.L(i, j);
       PT[l] = (U[l] * MT(dx, j, i) - U[l + SX] * MT(dx, j + 1, i) + V[l + 1] * MT(dy, j, i + 1) -
                V[l] * MT(dy, j, i)) * S.RAREA[l] + MT(fA, j, i);
     });
-    transport<R, false, BX, BY, FULL, DAMP_YES>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
+    transport<R, false, BX, BY, FULL, DAMP_YES, false, NT>(PT, S, B, m, n, cc, (const R*)nullptr, (const R*)nullptr, damp,
                                       (const R*)nullptr, FXO, FYO);
     // kinetic energy at corners from upwind-PPM corner winds.  FP64: the
     // edge values of u along x and of v along y once each (into the free
@@ -1006,17 +1017,17 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     // corner and wind; FP32 forms them in the corner loop (cheaper there than
     // the barrier)
     if constexpr (kStoreRD<R>) {
-      for2<FULL>(rot, x0 - 1, x1 + 2, y0, y1 + 1, [&](int i, int j) {
+      for2<FULL, NT>(rot, x0 - 1, x1 + 2, y0, y1 + 1, [&](int i, int j) {
         const int l = B.L(i, j);
         S.AL[l] = ppm_edge(U[l - 2], U[l - 1], U[l], U[l + 1]);
       });
-      for2<FULL>(rot, x0, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
+      for2<FULL, NT>(rot, x0, x1 + 1, y0 - 1, y1 + 2, [&](int i, int j) {
         const int l = B.L(i, j);
         S.QIJ[l] = ppm_edge(V[l - 2 * SX], V[l - SX], V[l], V[l + SX]);
       });
       __syncthreads();
     }
-    for2<FULL>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1 + 1, y0, y1 + 1, [&](int i, int j) {
       const int l = B.L(i, j);
       // twice the corner winds (their halvings moved into hdt and qdt)
       const R ua2 = uc[G(j - 1, i)] + uc[G(j, i)];
@@ -1037,17 +1048,17 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
     });
     __syncthreads();
     R *uo = a.u_o + o, *vo = a.v_o + o;
-    for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
       const int l = B.L(i, j);
       uo[G(j, i)] = U[l] + (FYO[l] + KE[l] - KE[l + 1]) * MT(rdx, j, i);
     });
-    for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+    for2<FULL, NT>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
       const int l = B.L(i, j);
       vo[G(j, i)] = V[l] + (-FXO[l] + KE[l] - KE[l + SX]) * MT(rdy, j, i);
     });
     if (a.xfxd) {  // the D-grid area fluxes for update_dz_d (reading R17)
-      for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
-      for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
+      for2<FULL, NT>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) { a.xfxd[o + G(j, i)] = S.XFX[B.L(i, j)]; });
+      for2<FULL, NT>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) { a.yfxd[o + G(j, i)] = S.YFX[B.L(i, j)]; });
     }
     if (a.amfx) {
       // the remapping step's sums (the Courant numbers and area fluxes were
@@ -1055,10 +1066,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 || LEARN) ? 2 : (sizeof(M
       // so an addition performed at the memory side (a reduction whose
       // result is not read back) gives the sum a load-add-store gives,
       // without the load's round trip
-      for2<FULL>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
+      for2<FULL, NT>(rot, x0, x1 + (x1 == n ? 1 : 0), y0, y1, [&](int i, int j) {
         atomicAdd(a.amfx + o + G(j, i), MFX[B.L(i, j)]);
       });
-      for2<FULL>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
+      for2<FULL, NT>(rot, x0, x1, y0, y1 + (y1 == n ? 1 : 0), [&](int i, int j) {
         atomicAdd(a.amfy + o + G(j, i), MFY[B.L(i, j)]);
       });
     }
@@ -2040,12 +2051,12 @@ bool shape_supported(int bx, int by) {
 // grid of a horizontal kernel: one CTA per work item, or (persistent mode)
 // as many CTAs as fit on the GPU at once, each striding over the work list
 template <typename K>
-static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork) {
+static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork, int threads = 256) {
   if (c.persistent <= 0) return dim3(nwork);
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const int g = sms * per_sm;
   return dim3(g < nwork ? g : nwork);
@@ -2057,7 +2068,8 @@ static dim3 work_grid(const Ctx& c, K kern, size_t smem, int nwork) {
 template <typename R, int X, int Y, bool L, typename MR, bool F = false>
 static void launch_d_sw(const Ctx& c, const StepArgs<R>& a, size_t sm, int nwork, cudaStream_t st) {
   set_smem(k_d_sw<R, X, Y, L, MR, F>, sm);
-  k_d_sw<R, X, Y, L, MR, F><<<work_grid(c, k_d_sw<R, X, Y, L, MR, F>, sm, nwork), dim3(32, 8), sm, st>>>(
+  constexpr int nt = kDswThreads<R, L>;
+  k_d_sw<R, X, Y, L, MR, F><<<work_grid(c, k_d_sw<R, X, Y, L, MR, F>, sm, nwork, nt), dim3(32, nt / 32), sm, st>>>(
       a, c.kchunk, nwork);
 }
 
